@@ -1,0 +1,315 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every expectation comes from brute force
+over all interleavings, a library routine that computes the same thing a different way
+(Python's stable sort, numpy.roll, math.gcd, finite differences), a closed form stated
+in the paper, or a hand-traced example.
+"""
+import itertools
+import math
+import random
+
+import numpy as np
+import pytest
+
+import workloads
+
+DTYPES = [np.int32, np.uint32, np.uint64, np.float32]
+
+
+def library_stable_merge(a, b):
+    """Stable merge by sorting (key, origin, index) with Python's stable sort."""
+    items = [(x, 0, i) for i, x in enumerate(a.tolist())] + \
+            [(x, 1, j) for j, x in enumerate(b.tolist())]
+    return sorted(items, key=lambda t: (t[0], t[1], t[2]))
+
+
+def interleavings(c, la):
+    """All ways to draw a sorted A of la elements from the sorted sequence c."""
+    n = len(c)
+    for pos in itertools.combinations(range(n), la):
+        s = set(pos)
+        yield c[list(pos)], c[[t for t in range(n) if t not in s]]
+
+
+def _bits(x):
+    return x.view({4: np.uint32, 8: np.uint64}[x.dtype.itemsize])
+
+
+@pytest.mark.parametrize("alphabet", [1, 2, 4, None])
+def test_merge_brute_force_all_interleavings(orc, alphabet):
+    rng = np.random.default_rng(11)
+    for n in range(0, 11):
+        hi = alphabet if alphabet else 10_000
+        c = np.sort(rng.integers(0, hi, n)).astype(np.int32)
+        for la in range(n + 1):
+            for a, b in interleavings(c, la):
+                exp = library_stable_merge(a, b)
+                got = orc.merge(a, b)
+                assert got.tolist() == [t[0] for t in exp]
+                va = np.arange(a.size, dtype=np.uint32)
+                vb = np.arange(a.size, a.size + b.size, dtype=np.uint32)
+                k, v = orc.merge_kv(a, va, b, vb)
+                assert v.tolist() == [t[2] + (a.size if t[1] else 0) for t in exp]
+                # split on every diagonal: number of A-origin items among the first d
+                d = np.arange(n + 1, dtype=np.uint64)
+                want = np.cumsum([0] + [1 - t[1] for t in exp])
+                assert orc.splits_replay(a, b, d).tolist() == want.tolist()
+                for dd in range(n + 1):
+                    assert orc.split_bsearch(a, b, dd) == want[dd]
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_merge_random_all_dtypes(orc, dt):
+    rng = random.Random(5)
+    for _ in range(60):
+        la, lb = rng.randint(0, 300), rng.randint(0, 300)
+        for dist in ("uniform", "dup16"):
+            a, b = workloads.make_pair(dist, dt, la, lb, seed=rng.randint(0, 10**6))
+            exp = library_stable_merge(a, b)
+            got = orc.merge(a, b)
+            assert got.tolist() == [t[0] for t in exp]
+
+
+def test_float_signed_zero_ties_keep_input_order(orc):
+    # -0.0 == +0.0 under "<=": stability decides, so bit patterns follow the origin
+    a = np.array([-1.0, -0.0, 0.0, 2.0], dtype=np.float32)
+    b = np.array([0.0, -0.0, 1.0], dtype=np.float32)
+    got = orc.merge(a, b)
+    want = np.array([-1.0, -0.0, 0.0, 0.0, -0.0, 1.0, 2.0], dtype=np.float32)
+    assert np.array_equal(_bits(got), _bits(want))
+
+
+def test_uint64_full_range(orc):
+    a = np.array([0, 1, 2**63 - 1, 2**63, 2**64 - 1], dtype=np.uint64)
+    b = np.array([2**63 - 2, 2**63, 2**64 - 2], dtype=np.uint64)
+    assert orc.merge(a, b).tolist() == sorted(a.tolist() + b.tolist())
+
+
+def test_split_forms_agree_and_balance(orc):
+    rng = random.Random(9)
+    for _ in range(40):
+        la, lb = rng.randint(0, 2000), rng.randint(0, 2000)
+        a, b = workloads.make_pair(rng.choice(["uniform", "dup16", "zipf"]), np.uint32, la,
+                                   lb, seed=rng.randint(0, 999))
+        P = rng.choice([1, 2, 3, 7, 16, 64])
+        d = orc.diagonals(la + lb, P)
+        rep = orc.splits_replay(a, b, d)
+        for k in range(P + 1):
+            assert orc.split_bsearch(a, b, int(d[k])) == rep[k]
+        sizes = np.diff(d.astype(np.int64))
+        n = la + lb
+        assert set(sizes.tolist()) <= {n // P, -(-n // P)}
+        # the pairs, merged one by one and concatenated, give the global merge
+        out = []
+        for k in range(P):
+            i0, i1 = int(rep[k]), int(rep[k + 1])
+            j0, j1 = int(d[k]) - i0, int(d[k + 1]) - i1
+            out.append(orc.merge(a[i0:i1], b[j0:j1]))
+        assert np.array_equal(np.concatenate(out) if out else a[:0], orc.merge(a, b))
+
+
+def test_arrange_is_pairs_back_to_back(orc):
+    a, b = workloads.make_pair("uniform", np.int32, 1000, 777, seed=1)
+    d = orc.diagonals(1777, 8)
+    i = orc.splits_replay(a, b, d)
+    arr = orc.arrange(a, b, d, i)
+    for k in range(8):
+        i0, i1, j0, j1 = int(i[k]), int(i[k + 1]), int(d[k] - i[k]), int(d[k + 1] - i[k + 1])
+        seg = arr[int(d[k]):int(d[k + 1])]
+        assert np.array_equal(seg, np.concatenate([a[i0:i1], b[j0:j1]]))
+
+
+def test_gallop_equals_bsearch_for_every_guess(orc):
+    rng = random.Random(2)
+    for _ in range(30):
+        la, lb = rng.randint(0, 70), rng.randint(0, 70)
+        a, b = workloads.make_pair(rng.choice(["uniform", "dup16"]), np.int32, la, lb,
+                                   seed=rng.randint(0, 999))
+        for d in range(la + lb + 1):
+            want = orc.split_bsearch(a, b, d)
+            for g in range(-2, la + 3):
+                i, probes = orc.gallop_split(a, b, d, max(g, 0))
+                assert i == want
+                dist = abs(want - max(0, min(g, la)))
+                # exponential bracket + bisection: O(log distance) probes
+                assert probes <= 2 * math.ceil(math.log2(dist + 1)) + 3
+
+
+def test_ls_rotate_equals_roll_and_paper_counts(orc):
+    for lx in range(0, 14):
+        for ly in range(0, 14):
+            x = np.arange(lx + ly, dtype=np.int32)
+            got, swaps = orc.ls_rotate(x, lx)
+            assert np.array_equal(got, np.roll(x, -lx))
+            if lx == ly:
+                assert swaps == lx  # Sec. 3.5: exactly L_A swaps for equal blocks
+            assert swaps <= 2 * (lx + ly)  # Sec. 3.5 bound
+    x = np.arange(10**5 + 7, dtype=np.uint64)
+    got, swaps = orc.ls_rotate(x, 7)
+    assert np.array_equal(got, np.roll(x, -7))
+
+
+def test_ls_hand_traced_example(orc):
+    # Sec. 3.4 LS on X=[0,1], Y=[2,3,4,5,6], traced by hand:
+    # swap X with Y's last 2 -> [5,6,2,3,4,0,1]; rotate [5,6|2,3,4]: swap [5,6] with
+    # [3,4] -> [3,4,2,5,6]; rotate [3,4|2]: Y smaller, swap 2 with 3 -> [2,4,3];
+    # rotate [4|3]: equal, swap -> [3,4].  6 elementary swaps.
+    got, swaps = orc.ls_rotate(np.array([0, 1, 2, 3, 4, 5, 6], dtype=np.int32), 2)
+    assert got.tolist() == [2, 3, 4, 5, 6, 0, 1]
+    assert swaps == 6
+
+
+def test_cs_rotate_gcd_cycles_and_exact_moves(orc):
+    for la in range(0, 16):
+        for lb in range(0, 16):
+            x = np.arange(la + lb, dtype=np.int32)
+            got, cycles, moves = orc.cs_rotate(x, la)
+            assert np.array_equal(got, np.roll(x, -la))
+            if la and lb:
+                assert cycles == math.gcd(la, lb)  # proof of Sec. 3.4 (GCD, not LCM)
+                assert moves == la + lb           # Sec. 3.5: exactly L_A + L_B moves
+            else:
+                assert cycles == 0 and moves == 0
+
+
+def _valid_split(a, b, pa, pb):
+    la, lb = len(a), len(b)
+    return (pa == 0 or pb == lb or a[pa - 1] <= b[pb]) and \
+        (pb == 0 or pa == la or b[pb - 1] <= a[pa])
+
+
+def test_findmedian_corner_cases(orc):
+    a = np.array([1, 2, 3], np.int32)
+    b = np.array([3, 4], np.int32)
+    assert orc.findmedian(a, b) == (3, 0)             # A <= B
+    assert orc.findmedian(b + 10, a) == (0, 3)        # A > B
+    assert orc.findmedian(a[:0], b) == (0, 0)         # |A| = 0
+    assert orc.findmedian(a, b[:0]) == (3, 0)         # |B| = 0
+
+
+def _findmedian_literal(A, B):
+    """Alg. 1 taken literally: p_A, p_B start at the middles (the text's first step),
+    the loop test uses the previous iteration's values, and the midpoints are
+    recomputed after the loop."""
+    la, lb = len(A), len(B)
+    if la == 0 or lb == 0 or A[-1] <= B[0]:
+        return la, 0
+    if not A[0] <= B[-1]:
+        return 0, lb
+    lA, limA, lB, limB = 0, la, 0, lb
+    pA, pB = la // 2, lb // 2
+    while lA < limA and lB < limB and A[pA] != B[pB]:
+        pA, pB = (limA - lA) // 2 + lA, (limB - lB) // 2 + lB
+        if A[pA] < B[pB]:
+            if pA + pB < (la - pA) + (lb - pB):
+                lA = pA + 1
+            else:
+                limB = pB
+        else:
+            if pA + pB < (la - pA) + (lb - pB):
+                lB = pB + 1
+            else:
+                limA = pA
+    return (limA - lA) // 2 + lA, (limB - lB) // 2 + lB
+
+
+def test_findmedian_reading_is_valid_where_literal_is_not(orc):
+    # The literal listing returns an invalid split here (B0 holds 4 > A1[0] = 3);
+    # the reading used by the oracle returns a valid one.
+    A = [1, 3, 3, 4, 5, 7, 7, 9]
+    B = [0, 0, 0, 1, 4, 5, 6, 7, 9]
+    assert _findmedian_literal(A, B) == (2, 5)
+    assert not _valid_split(A, B, 2, 5)
+    pa, pb = orc.findmedian(np.array(A, np.int32), np.array(B, np.int32))
+    assert _valid_split(A, B, pa, pb)
+    rng = random.Random(1)
+    for _ in range(20000):
+        la, lb, m = rng.randint(0, 12), rng.randint(0, 12), rng.choice([3, 10, 1000])
+        A = sorted(rng.randrange(m) for _ in range(la))
+        B = sorted(rng.randrange(m) for _ in range(lb))
+        pa, pb = orc.findmedian(np.array(A, np.int32), np.array(B, np.int32))
+        assert 0 <= pa <= la and 0 <= pb <= lb
+        assert _valid_split(A, B, pa, pb)
+
+
+def test_findmedian_is_not_stable_under_ties(orc):
+    # Even a valid FindMedian split can put a B key equal to A1[0] into B0, so equal
+    # keys would interleave B-then-A across pairs; the hot path uses the stable split.
+    a, b = np.array([3, 5, 5, 8], np.int32), np.array([1, 5, 5, 9], np.int32)
+    pa, pb = orc.findmedian(a, b)
+    assert (pa, pb) == (2, 2)
+    assert b[pb - 1] == a[pa]  # B0 ends with 5 == A1[0]: not the stable split
+    assert orc.split_bsearch(a, b, pa + pb) == 3
+
+
+@pytest.mark.parametrize("shift", ["ls", "cs"])
+@pytest.mark.parametrize("split", ["exact", "findmedian"])
+def test_srecpar_gives_the_merge(orc, shift, split):
+    rng = random.Random(3)
+    for _ in range(80):
+        la, lb = rng.randint(0, 400), rng.randint(0, 400)
+        a, b = workloads.make_pair(rng.choice(["uniform", "dup16", "paper"]), np.int32, la,
+                                   lb, seed=rng.randint(0, 999))
+        buf = np.concatenate([a, b])
+        depth = rng.randint(0, 5)
+        got, moved = orc.srecpar(buf, la, depth, size_limit=rng.choice([1, 16]),
+                                 split=split, shift=shift)
+        assert np.array_equal(got, orc.merge(a, b))
+
+
+def test_srecpar_exact_is_stable_with_payload_order(orc):
+    # with exact splits the division stage keeps A before B on ties: check with keys
+    # that carry their origin in the low bits
+    rng = np.random.default_rng(4)
+    k = np.sort(rng.integers(0, 8, 300)) * 1024
+    a = np.sort(k[:170] + np.arange(170)).astype(np.int32)
+    b = np.sort(k[170:] + 512 + np.arange(130)).astype(np.int32)
+    got, _ = orc.srecpar(np.concatenate([a, b]), 170, 4)
+    assert np.array_equal(got, np.sort(np.concatenate([a, b])))
+
+
+def test_mlp_forward_closed_forms(orc):
+    H = 4
+    rng = np.random.default_rng(0)
+    x = rng.random(9)
+    p = rng.normal(size=3 * H + 1)
+    p[:H] = 0.0  # w1 = 0: y = b2 + sum_h w2 tanh(b1)
+    y = orc.mlp_forward(p, H, x)
+    want = p[3 * H] + sum(p[2 * H + h] * math.tanh(p[H + h]) for h in range(H))
+    assert np.allclose(y, want, rtol=0, atol=1e-14)
+    q = np.array([0.7, -0.2, 1.5, 0.3])  # H = 1
+    y = orc.mlp_forward(q, 1, x)
+    assert np.allclose(y, [0.3 + 1.5 * math.tanh(0.7 * t - 0.2) for t in x], rtol=0,
+                       atol=1e-14)
+
+
+def test_mlp_gradient_matches_central_differences(orc):
+    H = 32
+    rng = np.random.default_rng(1)
+    x, t = rng.random(50), rng.random(50)
+    p = rng.normal(scale=0.7, size=3 * H + 1)
+    loss, g = orc.mlp_loss_grad(p, H, x, t)
+    y = orc.mlp_forward(p, H, x)
+    assert loss == pytest.approx(np.mean((y - t) ** 2), rel=1e-14)
+    h = 1e-6
+    for q in range(3 * H + 1):
+        pp, pm = p.copy(), p.copy()
+        pp[q] += h
+        pm[q] -= h
+        fd = (orc.mlp_loss_grad(pp, H, x, t)[0] - orc.mlp_loss_grad(pm, H, x, t)[0]) / (2 * h)
+        assert g[q] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+    # targets equal to the outputs: zero loss, zero gradient
+    l0, g0 = orc.mlp_loss_grad(p, H, x, y)
+    assert l0 < 1e-28 and np.abs(g0).max() < 1e-14
+
+
+def test_adam_first_step_closed_form(orc):
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 1e-3])
+    m, v = np.zeros(3), np.zeros(3)
+    lr, eps = 0.01, 1e-8
+    p0 = p.copy()
+    orc.adam_step(p, m, v, g, lr, 0.9, 0.999, eps, 1)
+    # first step: mhat = g, vhat = g^2  ->  p - lr * g / (|g| + eps)
+    assert np.allclose(p, p0 - lr * g / (np.abs(g) + eps), rtol=1e-12, atol=0)
