@@ -1,0 +1,184 @@
+/*
+ * ipmerge — GB300 (sm_103a) parallel in-place merge.
+ *
+ * C ABI of the data-parallel hot path of B. Bramas, Q. Bramas, "On the improvement of
+ * the in-place merge algorithm parallelization" (arXiv 2005.12648):
+ *
+ *   1. split      exact stable merge-path split points (the optimal split of Sec. 3.1)
+ *                 on the diagonals d_k = floor(k*n/P), k = 0..P, n = len_a + len_b;
+ *   2. rearrange  the sRecPar division stage (Alg. 3): level by level, the two middle
+ *                 blocks of every pair are exchanged in place (the partition exchange of
+ *                 Sec. 3.4), giving A_0 B_0 A_1 B_1 ... A_{P-1} B_{P-1};
+ *   3. merge      every pair (A_k, B_k) is merged stably in place (the per-thread merge
+ *                 of Alg. 2/3, here one CTA per pair, staged in shared memory).
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are plain CUDA device addresses, owned by the caller.  The
+ *     library never allocates or frees device memory; every call that needs scratch
+ *     takes a caller-owned workspace sized by the matching *_workspace_bytes query.
+ *   - Lengths and offsets count elements, not bytes.
+ *   - Keys are compared with the key type's own "<=": signed for IPM_INT32, unsigned
+ *     for IPM_UINT32 / IPM_UINT64, IEEE for IPM_FLOAT32 (NaN keys are not allowed;
+ *     -0.0 and +0.0 compare equal and keep their input order).
+ *   - The merge is stable: equal keys keep their input order, every A element before
+ *     every equal B element.  Keys (and payloads) are only moved, never computed, so
+ *     the result is bit-exact.
+ *   - Calls are asynchronous on `stream` (NULL = the legacy default stream).  Argument
+ *     errors detectable on the host return immediately and launch nothing.  Errors
+ *     found on the device (a bounded wait that expired) are recorded in the status
+ *     word at the start of the workspace, read with ipm_read_device_status.
+ *   - Preconditions that are not checked: both runs are sorted under the comparison
+ *     above, the buffer holds len_a + len_b elements, and no other work touches the
+ *     buffer or the workspace while the call runs on the stream.
+ */
+#ifndef IPMERGE_H
+#define IPMERGE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The same type as cudaStream_t. */
+typedef struct CUstream_st *ipm_stream_t;
+
+typedef enum {
+    IPM_OK = 0,
+    IPM_ERR_INVALID_ARG = 1,       /* NULL pointer, size overflow, bad option */
+    IPM_ERR_UNSUPPORTED_DTYPE = 2, /* dtype not in ipm_dtype / not allowed here */
+    IPM_ERR_ALIGNMENT = 3,         /* pointer not aligned to its element size */
+    IPM_ERR_WORKSPACE = 4,         /* workspace NULL or smaller than required */
+    IPM_ERR_CUDA = 5,              /* a CUDA runtime call or launch failed */
+    IPM_ERR_TIMEOUT = 6,           /* a bounded device-side wait expired */
+    IPM_ERR_DEVICE = 7             /* the device found an inconsistent state */
+} ipm_status;
+
+typedef enum {
+    IPM_INT32 = 0,
+    IPM_UINT32 = 1,
+    IPM_UINT64 = 2,
+    IPM_FLOAT32 = 3
+} ipm_dtype;
+
+/* Human-readable name of a status code (static string). */
+const char *ipm_status_string(ipm_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int ipm_version(void);
+
+/*
+ * Number of pairs P = 2^log2_pairs the plain merge uses for n = len_a + len_b keys of
+ * this dtype (the smallest power of two whose pairs all fit one CTA's shared-memory
+ * tile), and that tile's capacity in elements.  with_values selects the key-value
+ * tile.  Either output pointer may be NULL.
+ */
+ipm_status ipm_merge_plan(uint64_t len_a, uint64_t len_b, ipm_dtype key_dtype,
+                          int with_values, uint32_t *log2_pairs, uint64_t *tile_capacity);
+
+/*
+ * Workspace bytes for ipm_merge_inplace / _kv with this size, dtype and pair count
+ * (log2_pairs = 0 picks the automatic count of ipm_merge_plan).  The size is O(P):
+ * the split table, the per-level exchange plans and a 256-byte status block.
+ */
+ipm_status ipm_merge_workspace_bytes(uint64_t len_a, uint64_t len_b, ipm_dtype key_dtype,
+                                     int with_values, uint32_t log2_pairs, size_t *bytes);
+
+/*
+ * Stable in-place merge of the two sorted runs A = d_buf[0, len_a) and
+ * B = d_buf[len_a, len_a + len_b) into one sorted run d_buf[0, len_a + len_b)
+ * (Sec. 1 problem statement; division stage Alg. 3; exchange Sec. 3.4).
+ *   d_buf      device pointer to len_a + len_b keys of key_dtype, aligned to the key
+ *              size; overwritten with the merged run.
+ *   log2_pairs 0 = automatic; otherwise P = 2^log2_pairs pairs (every pair must fit
+ *              the tile capacity, else IPM_ERR_INVALID_ARG).
+ *   d_ws       workspace of at least ipm_merge_workspace_bytes(...) bytes, 256-byte
+ *              aligned, used for the duration of the call on `stream`.
+ * If A is empty, B is empty, or A[last] <= B[0] (the early exit of Alg. 2/3), the
+ * buffer is left as it is.
+ */
+ipm_status ipm_merge_inplace(void *d_buf, uint64_t len_a, uint64_t len_b,
+                             ipm_dtype key_dtype, uint32_t log2_pairs, void *d_ws,
+                             size_t ws_bytes, ipm_stream_t stream);
+
+/*
+ * Key-value form of ipm_merge_inplace: the 32-bit payload d_vals[t] moves with the key
+ * d_keys[t] (structure of arrays).  val_dtype must be IPM_UINT32 (any 4-byte payload
+ * can be passed as IPM_UINT32; payloads are never compared).
+ */
+ipm_status ipm_merge_inplace_kv(void *d_keys, void *d_vals, uint64_t len_a,
+                                uint64_t len_b, ipm_dtype key_dtype, ipm_dtype val_dtype,
+                                uint32_t log2_pairs, void *d_ws, size_t ws_bytes,
+                                ipm_stream_t stream);
+
+/*
+ * Step 1 alone: the exact stable split on every diagonal d_k = floor(k*n/P),
+ * k = 0..P (P = num_pairs >= 1, n = len_a + len_b, num_pairs * n < 2^64).
+ * d_split_a[k] receives i_k, the number of A elements among the first d_k keys of the
+ * stable merge; the B count is d_k - i_k.  d_split_a holds num_pairs + 1 uint64.
+ * This is the "optimal" split of Sec. 3.1 / Fig. 5, evaluated by a warp-cooperative
+ * binary search on each diagonal.  The input buffer is only read.
+ */
+ipm_status ipm_merge_splits(const void *d_buf, uint64_t len_a, uint64_t len_b,
+                            ipm_dtype key_dtype, uint64_t num_pairs, uint64_t *d_split_a,
+                            ipm_stream_t stream);
+
+/*
+ * Step 2 alone: the division stage of Alg. 3 applied to d_buf from a split table made
+ * by ipm_merge_splits with P = 2^log2_pairs.  Afterwards pair k occupies
+ * d_buf[d_k, d_{k+1}) as A[i_k, i_{k+1}) followed by B[j_k, j_{k+1}).  d_vals may be
+ * NULL (keys only) or a uint32 payload array moved with the keys.  The workspace is
+ * the one of ipm_merge_workspace_bytes for the same arguments; the split table is
+ * read from d_split_a (not from the workspace).
+ */
+ipm_status ipm_merge_rearrange(void *d_buf, void *d_vals, uint64_t len_a, uint64_t len_b,
+                               ipm_dtype key_dtype, const uint64_t *d_split_a,
+                               uint32_t log2_pairs, void *d_ws, size_t ws_bytes,
+                               ipm_stream_t stream);
+
+/*
+ * Step 3 alone: merge every pair of an arranged buffer (the layout step 2 produces)
+ * in place, one CTA per pair through shared memory.  d_split_a is the P+1 split table
+ * (P = 2^log2_pairs); every pair must fit the tile capacity.  d_vals as above.
+ */
+ipm_status ipm_merge_pairs(void *d_buf, void *d_vals, uint64_t len_a, uint64_t len_b,
+                           ipm_dtype key_dtype, const uint64_t *d_split_a,
+                           uint32_t log2_pairs, ipm_stream_t stream);
+
+/*
+ * Partition exchange alone (Sec. 3.4): d_ptr[0, len_x + len_y) = [X | Y] becomes
+ * [Y | X] in place.  elem_bytes is 4 or 8 (the bytes are moved, never compared).
+ * Same result as linear shifting; uses the workspace of ipm_rotate_workspace_bytes.
+ */
+ipm_status ipm_rotate_workspace_bytes(size_t *bytes);
+ipm_status ipm_rotate(void *d_ptr, uint64_t len_x, uint64_t len_y, uint32_t elem_bytes,
+                      void *d_ws, size_t ws_bytes, ipm_stream_t stream);
+
+/*
+ * Optional per-phase timing (for benchmarks).  When enabled on a host thread, the
+ * merge entry points called from that thread record a CUDA event pair on their stream
+ * around each launch group: phase 0 = early exit + split, 1 = exchange plan,
+ * 2 = exchange levels, 3 = pair merge.  ipm_timing_read waits for the recorded events,
+ * adds their elapsed times and kernel-launch counts into *out and forgets them.
+ * Timing adds two event records per group and changes no kernel.
+ */
+typedef struct {
+    double ms[4];
+    uint32_t launches[4];
+} ipm_timing;
+
+ipm_status ipm_timing_enable(int enable);
+ipm_status ipm_timing_read(ipm_timing *out);
+
+/*
+ * Read the device status word that the last call using this workspace left (IPM_OK,
+ * IPM_ERR_TIMEOUT or IPM_ERR_DEVICE).  Synchronises `stream`.
+ */
+ipm_status ipm_read_device_status(const void *d_ws, ipm_stream_t stream, ipm_status *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IPMERGE_H */

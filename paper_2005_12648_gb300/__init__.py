@@ -1,0 +1,264 @@
+"""Python binding of the ipmerge C ABI (``include/ipmerge.h``).
+
+GB300 (sm_103a) parallel in-place merge after Bramas & Bramas, arXiv 2005.12648.
+Every function named ``ipm_*`` here calls the C function of the same name in
+``_lib/libipmerge.so`` and only marshals arguments: tensors become device pointers,
+dtype names become ``ipm_dtype`` codes, a torch stream becomes a ``cudaStream_t``,
+and a non-OK status raises :class:`IpmError`.  Every step of the merge runs in the
+library's CUDA kernels; there is no fallback.  PyTorch provides device memory
+(workspaces come from its caching allocator) and streams only.
+
+Importing this package does not need a GPU; calling an entry point does, and fails
+loudly if the library has not been built (``build_ext.build_library()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build_ext import LIB as _LIB_PATH
+
+__all__ = [
+    "IpmError", "DTYPES", "load", "ipm_status_string", "ipm_version", "ipm_merge_plan",
+    "ipm_merge_workspace_bytes", "ipm_merge_inplace", "ipm_merge_inplace_kv",
+    "ipm_merge_splits", "ipm_merge_rearrange", "ipm_merge_pairs",
+    "ipm_rotate_workspace_bytes", "ipm_rotate", "ipm_read_device_status",
+    "ipm_timing_enable", "ipm_timing_read", "IpmTiming",
+    "workspace", "merge_inplace", "merge_inplace_kv",
+]
+
+DTYPES = {"int32": 0, "uint32": 1, "uint64": 2, "float32": 3}
+_ELEM = {0: 4, 1: 4, 2: 8, 3: 4}
+STATUS = {0: "IPM_OK", 1: "IPM_ERR_INVALID_ARG", 2: "IPM_ERR_UNSUPPORTED_DTYPE",
+          3: "IPM_ERR_ALIGNMENT", 4: "IPM_ERR_WORKSPACE", 5: "IPM_ERR_CUDA",
+          6: "IPM_ERR_TIMEOUT", 7: "IPM_ERR_DEVICE"}
+
+
+class IpmError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = int(code)
+        super().__init__(f"{where}: {STATUS.get(int(code), code)}")
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes)
+_vp, _u64, _u32, _i, _sz = (ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                            ctypes.c_size_t)
+_SIGS = {
+    "ipm_status_string": (ctypes.c_char_p, [_i]),
+    "ipm_version": (_i, []),
+    "ipm_merge_plan": (_i, [_u64, _u64, _i, _i, ctypes.POINTER(_u32),
+                            ctypes.POINTER(_u64)]),
+    "ipm_merge_workspace_bytes": (_i, [_u64, _u64, _i, _i, _u32, ctypes.POINTER(_sz)]),
+    "ipm_merge_inplace": (_i, [_vp, _u64, _u64, _i, _u32, _vp, _sz, _vp]),
+    "ipm_merge_inplace_kv": (_i, [_vp, _vp, _u64, _u64, _i, _i, _u32, _vp, _sz, _vp]),
+    "ipm_merge_splits": (_i, [_vp, _u64, _u64, _i, _u64, _vp, _vp]),
+    "ipm_merge_rearrange": (_i, [_vp, _vp, _u64, _u64, _i, _vp, _u32, _vp, _sz, _vp]),
+    "ipm_merge_pairs": (_i, [_vp, _vp, _u64, _u64, _i, _vp, _u32, _vp]),
+    "ipm_rotate_workspace_bytes": (_i, [ctypes.POINTER(_sz)]),
+    "ipm_rotate": (_i, [_vp, _u64, _u64, _u32, _vp, _sz, _vp]),
+    "ipm_read_device_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
+    "ipm_timing_enable": (_i, [_i]),
+    "ipm_timing_read": (_i, [ctypes.c_void_p]),
+}
+
+
+class IpmTiming(ctypes.Structure):
+    """Mirror of ipm_timing: per-phase milliseconds and launch counts."""
+    _fields_ = [("ms", ctypes.c_double * 4), ("launches", ctypes.c_uint32 * 4)]
+
+    PHASES = ("split", "plan", "exchange", "merge")
+
+    def as_dict(self):
+        return {p: {"ms": self.ms[i], "launches": int(self.launches[i])}
+                for i, p in enumerate(self.PHASES)}
+
+
+def exported_symbols():
+    """Names of the C entry points this binding expects the library to export."""
+    return list(_SIGS)
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libipmerge.so (once).  Raises if it is missing: there is no fallback."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or _LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"ipmerge CUDA library not built ({p}); run "
+                                   "paper_2005_12648_gb300.build_ext.build_library()")
+            L = ctypes.CDLL(p)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(code: int, where: str) -> None:
+    if code != 0:
+        raise IpmError(code, where)
+
+
+def _dt(dtype) -> int:
+    if isinstance(dtype, int):
+        if dtype not in _ELEM:
+            raise ValueError(f"bad ipm_dtype {dtype}")
+        return dtype
+    if isinstance(dtype, str):
+        return DTYPES[dtype]
+    name = str(dtype).replace("torch.", "")
+    if name in DTYPES:
+        return DTYPES[name]
+    raise ValueError(f"cannot map {dtype!r} to an ipm_dtype; pass 'int32', 'uint32', "
+                     "'uint64' or 'float32'")
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if hasattr(x, "is_cuda") and not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        return x.data_ptr()
+    raise TypeError(f"expected a tensor or an int pointer, got {type(x)}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _nbytes(x) -> int:
+    return x.numel() * x.element_size()
+
+
+# ------------------------------------------------------------------ C ABI mirrors
+
+def ipm_status_string(code: int) -> str:
+    return load().ipm_status_string(int(code)).decode()
+
+
+def ipm_version() -> int:
+    return int(load().ipm_version())
+
+
+def ipm_merge_plan(len_a: int, len_b: int, key_dtype, with_values: bool = False):
+    """Returns (log2_pairs, tile_capacity)."""
+    g, t = _u32(0), _u64(0)
+    _check(load().ipm_merge_plan(len_a, len_b, _dt(key_dtype), int(bool(with_values)),
+                                 ctypes.byref(g), ctypes.byref(t)), "ipm_merge_plan")
+    return int(g.value), int(t.value)
+
+
+def ipm_merge_workspace_bytes(len_a: int, len_b: int, key_dtype, with_values: bool = False,
+                              log2_pairs: int = 0) -> int:
+    out = _sz(0)
+    _check(load().ipm_merge_workspace_bytes(len_a, len_b, _dt(key_dtype),
+                                            int(bool(with_values)), log2_pairs,
+                                            ctypes.byref(out)), "ipm_merge_workspace_bytes")
+    return int(out.value)
+
+
+def ipm_merge_inplace(buf, len_a: int, len_b: int, key_dtype, ws, log2_pairs: int = 0,
+                      ws_bytes: int | None = None, stream=None) -> None:
+    wsb = _nbytes(ws) if ws_bytes is None else ws_bytes
+    _check(load().ipm_merge_inplace(_ptr(buf), len_a, len_b, _dt(key_dtype), log2_pairs,
+                                    _ptr(ws), wsb, _stream(stream)), "ipm_merge_inplace")
+
+
+def ipm_merge_inplace_kv(keys, vals, len_a: int, len_b: int, key_dtype, ws,
+                         val_dtype="uint32", log2_pairs: int = 0, ws_bytes: int | None = None,
+                         stream=None) -> None:
+    wsb = _nbytes(ws) if ws_bytes is None else ws_bytes
+    _check(load().ipm_merge_inplace_kv(_ptr(keys), _ptr(vals), len_a, len_b, _dt(key_dtype),
+                                       _dt(val_dtype), log2_pairs, _ptr(ws), wsb,
+                                       _stream(stream)), "ipm_merge_inplace_kv")
+
+
+def ipm_merge_splits(buf, len_a: int, len_b: int, key_dtype, num_pairs: int, split_a,
+                     stream=None) -> None:
+    _check(load().ipm_merge_splits(_ptr(buf), len_a, len_b, _dt(key_dtype), num_pairs,
+                                   _ptr(split_a), _stream(stream)), "ipm_merge_splits")
+
+
+def ipm_merge_rearrange(buf, vals, len_a: int, len_b: int, key_dtype, split_a,
+                        log2_pairs: int, ws, ws_bytes: int | None = None, stream=None):
+    wsb = _nbytes(ws) if ws_bytes is None else ws_bytes
+    _check(load().ipm_merge_rearrange(_ptr(buf), _ptr(vals), len_a, len_b, _dt(key_dtype),
+                                      _ptr(split_a), log2_pairs, _ptr(ws), wsb,
+                                      _stream(stream)), "ipm_merge_rearrange")
+
+
+def ipm_merge_pairs(buf, vals, len_a: int, len_b: int, key_dtype, split_a,
+                    log2_pairs: int, stream=None) -> None:
+    _check(load().ipm_merge_pairs(_ptr(buf), _ptr(vals), len_a, len_b, _dt(key_dtype),
+                                  _ptr(split_a), log2_pairs, _stream(stream)),
+           "ipm_merge_pairs")
+
+
+def ipm_rotate_workspace_bytes() -> int:
+    out = _sz(0)
+    _check(load().ipm_rotate_workspace_bytes(ctypes.byref(out)), "ipm_rotate_workspace_bytes")
+    return int(out.value)
+
+
+def ipm_rotate(ptr, len_x: int, len_y: int, elem_bytes: int, ws,
+               ws_bytes: int | None = None, stream=None) -> None:
+    wsb = _nbytes(ws) if ws_bytes is None else ws_bytes
+    _check(load().ipm_rotate(_ptr(ptr), len_x, len_y, elem_bytes, _ptr(ws), wsb,
+                             _stream(stream)), "ipm_rotate")
+
+
+def ipm_read_device_status(ws, stream=None) -> int:
+    out = _i(0)
+    _check(load().ipm_read_device_status(_ptr(ws), _stream(stream), ctypes.byref(out)),
+           "ipm_read_device_status")
+    return int(out.value)
+
+
+def ipm_timing_enable(enable: bool = True) -> None:
+    _check(load().ipm_timing_enable(int(bool(enable))), "ipm_timing_enable")
+
+
+def ipm_timing_read(into: "IpmTiming | None" = None) -> IpmTiming:
+    t = into if into is not None else IpmTiming()
+    _check(load().ipm_timing_read(ctypes.byref(t)), "ipm_timing_read")
+    return t
+
+
+# ------------------------------------------------------------------ conveniences
+
+def workspace(nbytes: int, device=None):
+    """A workspace from torch's caching allocator (256-byte aligned)."""
+    import torch
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8,
+                       device=device if device is not None else "cuda")
+
+
+def merge_inplace(buf, len_a: int, len_b: int, key_dtype, log2_pairs: int = 0, stream=None):
+    """Allocate the workspace and run ipm_merge_inplace on a CUDA tensor A|B."""
+    ws = workspace(ipm_merge_workspace_bytes(len_a, len_b, key_dtype, False, log2_pairs),
+                   buf.device)
+    ipm_merge_inplace(buf, len_a, len_b, key_dtype, ws, log2_pairs, stream=stream)
+    return ws
+
+
+def merge_inplace_kv(keys, vals, len_a: int, len_b: int, key_dtype, log2_pairs: int = 0,
+                     stream=None):
+    ws = workspace(ipm_merge_workspace_bytes(len_a, len_b, key_dtype, True, log2_pairs),
+                   keys.device)
+    ipm_merge_inplace_kv(keys, vals, len_a, len_b, key_dtype, ws, log2_pairs=log2_pairs,
+                         stream=stream)
+    return ws

@@ -1,0 +1,358 @@
+// The extern "C" entry points of include/ipmerge.h: argument checks, workspace layout
+// and the launch sequence of the hot path (split -> level exchanges -> pair merge).
+#include <vector>
+
+#include "ipm_internal.h"
+
+namespace ipm {
+
+int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 1;
+    }
+    if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        v <= 0) {
+        (void)cudaGetLastError();
+        v = 1;
+    }
+    if (dev >= 0 && dev < 64) cached[dev] = v;
+    return v;
+}
+
+ipm_status last_launch_status() {
+    return cudaGetLastError() == cudaSuccess ? IPM_OK : IPM_ERR_CUDA;
+}
+
+namespace {
+
+// ---- optional per-phase timing (ipm_timing_enable / ipm_timing_read), per host thread
+struct TimingRec {
+    int phase;
+    uint32_t launches;
+    cudaEvent_t a, b;
+};
+struct TimingState {
+    bool enabled = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<TimingRec> recs;
+    cudaEvent_t get() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        return e;
+    }
+};
+thread_local TimingState g_timing;
+
+// Records an event pair around one launch group when timing is enabled.
+class PhaseScope {
+  public:
+    PhaseScope(int phase, uint32_t launches, cudaStream_t s) : s_(s) {
+        if (!g_timing.enabled) return;
+        rec_.phase = phase;
+        rec_.launches = launches;
+        rec_.a = g_timing.get();
+        rec_.b = g_timing.get();
+        if (rec_.a && rec_.b && cudaEventRecord(rec_.a, s_) == cudaSuccess) on_ = true;
+    }
+    ~PhaseScope() {
+        if (!on_) return;
+        if (cudaEventRecord(rec_.b, s_) == cudaSuccess)
+            g_timing.recs.push_back(rec_);
+        else
+            (void)cudaGetLastError();
+    }
+
+  private:
+    cudaStream_t s_;
+    TimingRec rec_{};
+    bool on_ = false;
+};
+
+constexpr uint32_t kMaxLog2Pairs = 22;
+
+bool valid_key(ipm_dtype t) {
+    return t == IPM_INT32 || t == IPM_UINT32 || t == IPM_UINT64 || t == IPM_FLOAT32;
+}
+
+// Smallest G with 2^G * tile >= n.
+uint32_t auto_log2_pairs(uint64_t n, uint64_t tile) {
+    uint32_t G = 0;
+    while ((uint64_t(1) << G) * tile < n) ++G;
+    return G;
+}
+
+// Checks shared by the merge entry points; resolves G.
+ipm_status check_merge_args(uint64_t la, uint64_t lb, ipm_dtype key, bool kv,
+                            uint32_t log2_pairs, uint32_t *G_out) {
+    if (!valid_key(key)) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (la > (uint64_t(1) << 40) || lb > (uint64_t(1) << 40)) return IPM_ERR_INVALID_ARG;
+    const uint64_t n = la + lb;
+    const uint64_t tile = tile_capacity(key, kv);
+    const uint32_t G = log2_pairs ? log2_pairs : auto_log2_pairs(n, tile);
+    if (G > kMaxLog2Pairs) return IPM_ERR_INVALID_ARG;
+    // every pair must fit one tile: ceil(n / 2^G) <= tile
+    if (((n + (uint64_t(1) << G) - 1) >> G) > tile) return IPM_ERR_INVALID_ARG;
+    *G_out = G;
+    return IPM_OK;
+}
+
+struct MergeLayout {
+    size_t split_off, plan_off, total;
+};
+
+MergeLayout merge_layout(uint32_t G) {
+    MergeLayout L;
+    const uint64_t P = uint64_t(1) << G;
+    L.split_off = kStatusBytes;
+    L.plan_off = L.split_off + align_up(sizeof(uint64_t) * (P + 1), 256);
+    L.total = L.plan_off + plan_area_bytes(G);
+    return L;
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+ipm_status merge_core(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_dtype key,
+                      uint32_t log2_pairs, void *ws, size_t ws_bytes, cudaStream_t stream) {
+    const bool kv = vals != nullptr;
+    uint32_t G = 0;
+    IPM_TRY(check_merge_args(la, lb, key, kv, log2_pairs, &G));
+    if (la + lb == 0) return IPM_OK;
+    if (buf == nullptr || ws == nullptr) return buf ? IPM_ERR_WORKSPACE : IPM_ERR_INVALID_ARG;
+    if (!aligned(buf, size_t(dtype_bytes(key))) || (kv && !aligned(vals, 4)))
+        return IPM_ERR_ALIGNMENT;
+    if (!aligned(ws, 256)) return IPM_ERR_ALIGNMENT;
+    const MergeLayout L = merge_layout(G);
+    if (ws_bytes < L.total) return IPM_ERR_WORKSPACE;
+    char *w = static_cast<char *>(ws);
+    StatusBlock *sb = reinterpret_cast<StatusBlock *>(w);
+    uint64_t *split = reinterpret_cast<uint64_t *>(w + L.split_off);
+    const PlanArea pa = plan_area_at(w + L.plan_off, G);
+    const uint64_t P = uint64_t(1) << G;
+    const uint64_t n = la + lb;
+
+    {
+        PhaseScope ps(0, 2, stream);
+        // a0: early exit (A empty, B empty, or A[last] <= B[0]) -> later steps are no-ops
+        IPM_TRY(launch_early_exit(buf, la, lb, key, sb, stream));
+        // a1: exact stable splits on every diagonal
+        IPM_TRY(launch_splits(buf, la, lb, key, P, split, sb, stream));
+    }
+    // a2: division stage, one exchange level at a time
+    if (G > 0) {
+        {
+            PhaseScope ps(1, 1, stream);
+            IPM_TRY(launch_plan_levels(split, n, G, pa, sb, stream));
+        }
+        for (uint32_t l = 0; l < G; ++l) {
+            PhaseScope ps(2, 2, stream);
+            IPM_TRY(launch_level_exchange(buf, vals, dtype_bytes(key), n, l, pa, sb, stream));
+        }
+    }
+    // a3: per-pair merge
+    {
+        PhaseScope ps(3, 1, stream);
+        IPM_TRY(launch_tile_merge(buf, vals, la, lb, key, split, G, sb, stream));
+    }
+    return IPM_OK;
+}
+
+}  // namespace
+}  // namespace ipm
+
+using namespace ipm;
+
+extern "C" {
+
+const char *ipm_status_string(ipm_status s) {
+    switch (s) {
+    case IPM_OK:
+        return "IPM_OK";
+    case IPM_ERR_INVALID_ARG:
+        return "IPM_ERR_INVALID_ARG";
+    case IPM_ERR_UNSUPPORTED_DTYPE:
+        return "IPM_ERR_UNSUPPORTED_DTYPE";
+    case IPM_ERR_ALIGNMENT:
+        return "IPM_ERR_ALIGNMENT";
+    case IPM_ERR_WORKSPACE:
+        return "IPM_ERR_WORKSPACE";
+    case IPM_ERR_CUDA:
+        return "IPM_ERR_CUDA";
+    case IPM_ERR_TIMEOUT:
+        return "IPM_ERR_TIMEOUT";
+    case IPM_ERR_DEVICE:
+        return "IPM_ERR_DEVICE";
+    }
+    return "IPM_ERR_UNKNOWN";
+}
+
+int ipm_version(void) { return 100; }
+
+ipm_status ipm_merge_plan(uint64_t len_a, uint64_t len_b, ipm_dtype key_dtype,
+                          int with_values, uint32_t *log2_pairs, uint64_t *tile_cap) {
+    uint32_t G = 0;
+    IPM_TRY(check_merge_args(len_a, len_b, key_dtype, with_values != 0, 0, &G));
+    if (log2_pairs) *log2_pairs = G;
+    if (tile_cap) *tile_cap = tile_capacity(key_dtype, with_values != 0);
+    return IPM_OK;
+}
+
+ipm_status ipm_merge_workspace_bytes(uint64_t len_a, uint64_t len_b, ipm_dtype key_dtype,
+                                     int with_values, uint32_t log2_pairs, size_t *bytes) {
+    if (bytes == nullptr) return IPM_ERR_INVALID_ARG;
+    uint32_t G = 0;
+    IPM_TRY(check_merge_args(len_a, len_b, key_dtype, with_values != 0, log2_pairs, &G));
+    *bytes = merge_layout(G).total;
+    return IPM_OK;
+}
+
+ipm_status ipm_merge_inplace(void *d_buf, uint64_t len_a, uint64_t len_b,
+                             ipm_dtype key_dtype, uint32_t log2_pairs, void *d_ws,
+                             size_t ws_bytes, ipm_stream_t stream) {
+    return merge_core(d_buf, nullptr, len_a, len_b, key_dtype, log2_pairs, d_ws, ws_bytes,
+                      (cudaStream_t)stream);
+}
+
+ipm_status ipm_merge_inplace_kv(void *d_keys, void *d_vals, uint64_t len_a,
+                                uint64_t len_b, ipm_dtype key_dtype, ipm_dtype val_dtype,
+                                uint32_t log2_pairs, void *d_ws, size_t ws_bytes,
+                                ipm_stream_t stream) {
+    if (val_dtype != IPM_UINT32) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (d_vals == nullptr && len_a + len_b > 0) return IPM_ERR_INVALID_ARG;
+    if (len_a + len_b == 0) return valid_key(key_dtype) ? IPM_OK : IPM_ERR_UNSUPPORTED_DTYPE;
+    return merge_core(d_keys, static_cast<uint32_t *>(d_vals), len_a, len_b, key_dtype,
+                      log2_pairs, d_ws, ws_bytes, (cudaStream_t)stream);
+}
+
+ipm_status ipm_merge_splits(const void *d_buf, uint64_t len_a, uint64_t len_b,
+                            ipm_dtype key_dtype, uint64_t num_pairs, uint64_t *d_split_a,
+                            ipm_stream_t stream) {
+    if (!valid_key(key_dtype)) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (num_pairs == 0 || d_split_a == nullptr) return IPM_ERR_INVALID_ARG;
+    if (len_a > (uint64_t(1) << 40) || len_b > (uint64_t(1) << 40)) return IPM_ERR_INVALID_ARG;
+    const uint64_t n = len_a + len_b;
+    if (n > 0 && num_pairs > (~uint64_t(0)) / n) return IPM_ERR_INVALID_ARG;
+    if (num_pairs > (uint64_t(1) << 30)) return IPM_ERR_INVALID_ARG;
+    if (n > 0 && d_buf == nullptr) return IPM_ERR_INVALID_ARG;
+    if (!aligned(d_buf, size_t(dtype_bytes(key_dtype))) || !aligned(d_split_a, 8))
+        return IPM_ERR_ALIGNMENT;
+    return launch_splits(d_buf, len_a, len_b, key_dtype, num_pairs, d_split_a, nullptr,
+                         (cudaStream_t)stream);
+}
+
+ipm_status ipm_merge_rearrange(void *d_buf, void *d_vals, uint64_t len_a, uint64_t len_b,
+                               ipm_dtype key_dtype, const uint64_t *d_split_a,
+                               uint32_t log2_pairs, void *d_ws, size_t ws_bytes,
+                               ipm_stream_t stream) {
+    const bool kv = d_vals != nullptr;
+    if (!valid_key(key_dtype)) return IPM_ERR_UNSUPPORTED_DTYPE;
+    // the exchange levels do not depend on the tile capacity: any P = 2^G works
+    if (log2_pairs == 0 || log2_pairs > kMaxLog2Pairs) return IPM_ERR_INVALID_ARG;
+    if (len_a > (uint64_t(1) << 40) || len_b > (uint64_t(1) << 40)) return IPM_ERR_INVALID_ARG;
+    const uint32_t G = log2_pairs;
+    if (d_buf == nullptr || d_split_a == nullptr) return IPM_ERR_INVALID_ARG;
+    if (d_ws == nullptr) return IPM_ERR_WORKSPACE;
+    if (!aligned(d_buf, size_t(dtype_bytes(key_dtype))) || (kv && !aligned(d_vals, 4)) ||
+        !aligned(d_ws, 256))
+        return IPM_ERR_ALIGNMENT;
+    const MergeLayout L = merge_layout(G);
+    if (ws_bytes < L.total) return IPM_ERR_WORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = static_cast<char *>(d_ws);
+    StatusBlock *sb = reinterpret_cast<StatusBlock *>(w);
+    IPM_CUDA_TRY(cudaMemsetAsync(sb, 0, kStatusBytes, st));
+    const PlanArea pa = plan_area_at(w + L.plan_off, G);
+    IPM_TRY(launch_plan_levels(d_split_a, len_a + len_b, G, pa, sb, st));
+    for (uint32_t l = 0; l < G; ++l)
+        IPM_TRY(launch_level_exchange(d_buf, static_cast<uint32_t *>(d_vals),
+                                      dtype_bytes(key_dtype), len_a + len_b, l, pa, sb, st));
+    return IPM_OK;
+}
+
+ipm_status ipm_merge_pairs(void *d_buf, void *d_vals, uint64_t len_a, uint64_t len_b,
+                           ipm_dtype key_dtype, const uint64_t *d_split_a,
+                           uint32_t log2_pairs, ipm_stream_t stream) {
+    const bool kv = d_vals != nullptr;
+    uint32_t G = 0;
+    IPM_TRY(check_merge_args(len_a, len_b, key_dtype, kv, log2_pairs, &G));
+    if (G != log2_pairs) return IPM_ERR_INVALID_ARG;
+    if (len_a + len_b == 0) return IPM_OK;
+    if (d_buf == nullptr || d_split_a == nullptr) return IPM_ERR_INVALID_ARG;
+    if (!aligned(d_buf, size_t(dtype_bytes(key_dtype))) || (kv && !aligned(d_vals, 4)))
+        return IPM_ERR_ALIGNMENT;
+    return launch_tile_merge(d_buf, static_cast<uint32_t *>(d_vals), len_a, len_b, key_dtype,
+                             d_split_a, G, nullptr, (cudaStream_t)stream);
+}
+
+ipm_status ipm_rotate_workspace_bytes(size_t *bytes) {
+    if (bytes == nullptr) return IPM_ERR_INVALID_ARG;
+    *bytes = kStatusBytes + plan_area_bytes(1);
+    return IPM_OK;
+}
+
+ipm_status ipm_rotate(void *d_ptr, uint64_t len_x, uint64_t len_y, uint32_t elem_bytes,
+                      void *d_ws, size_t ws_bytes, ipm_stream_t stream) {
+    if (elem_bytes != 4 && elem_bytes != 8) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (len_x > (uint64_t(1) << 40) || len_y > (uint64_t(1) << 40)) return IPM_ERR_INVALID_ARG;
+    if (len_x == 0 || len_y == 0) return IPM_OK;
+    if (d_ptr == nullptr) return IPM_ERR_INVALID_ARG;
+    if (d_ws == nullptr || ws_bytes < kStatusBytes + plan_area_bytes(1))
+        return IPM_ERR_WORKSPACE;
+    if (!aligned(d_ptr, elem_bytes) || !aligned(d_ws, 256)) return IPM_ERR_ALIGNMENT;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = static_cast<char *>(d_ws);
+    StatusBlock *sb = reinterpret_cast<StatusBlock *>(w);
+    IPM_CUDA_TRY(cudaMemsetAsync(sb, 0, kStatusBytes, st));
+    const PlanArea pa = plan_area_at(w + kStatusBytes, 1);
+    IPM_TRY(launch_plan_single(len_x, len_y, pa, st));
+    return launch_level_exchange(d_ptr, nullptr, int(elem_bytes), len_x + len_y, 0, pa, sb, st);
+}
+
+ipm_status ipm_timing_enable(int enable) {
+    g_timing.enabled = enable != 0;
+    return IPM_OK;
+}
+
+ipm_status ipm_timing_read(ipm_timing *out) {
+    if (out == nullptr) return IPM_ERR_INVALID_ARG;
+    ipm_status st = IPM_OK;
+    for (const TimingRec &r : g_timing.recs) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            (void)cudaGetLastError();
+            st = IPM_ERR_CUDA;
+        } else {
+            out->ms[r.phase] += double(ms);
+            out->launches[r.phase] += r.launches;
+        }
+        g_timing.pool.push_back(r.a);
+        g_timing.pool.push_back(r.b);
+    }
+    g_timing.recs.clear();
+    return st;
+}
+
+ipm_status ipm_read_device_status(const void *d_ws, ipm_stream_t stream, ipm_status *out) {
+    if (d_ws == nullptr || out == nullptr) return IPM_ERR_INVALID_ARG;
+    unsigned int word = 0;
+    IPM_CUDA_TRY(cudaMemcpyAsync(&word, d_ws, sizeof(word), cudaMemcpyDeviceToHost,
+                                 (cudaStream_t)stream));
+    IPM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    *out = static_cast<ipm_status>(word);
+    return IPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// Shared device/host helpers of the ipmerge CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ipmerge.h"
+
+namespace ipm {
+
+// ---------------------------------------------------------------------------------
+// Key types.  Keys are compared with their own "<=" and otherwise only moved.
+// ---------------------------------------------------------------------------------
+template <typename K>
+__device__ __forceinline__ bool key_le(K x, K y) { return x <= y; }
+
+// ---------------------------------------------------------------------------------
+// Workspace status block (first 256 bytes of every workspace).
+//   word 0  device status (ipm_status), first error wins
+//   word 1  early-exit flag: nonzero when the runs are already in order (Alg. 2/3)
+//   word 2+ per-call counters used by persistent kernels
+// ---------------------------------------------------------------------------------
+struct StatusBlock {
+    unsigned int status;
+    unsigned int done;
+    unsigned int counters[62];
+};
+static_assert(sizeof(StatusBlock) == 256, "status block is 256 bytes");
+
+constexpr size_t kStatusBytes = 256;
+
+__device__ __forceinline__ void set_status(StatusBlock *sb, unsigned int code) {
+    atomicCAS(&sb->status, 0u, code);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Upper bound for every device-side wait (mbarrier, flags): 2 s of wall time.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+// ---------------------------------------------------------------------------------
+// Small host helpers.
+// ---------------------------------------------------------------------------------
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline int dtype_bytes(ipm_dtype t) {
+    switch (t) {
+    case IPM_INT32:
+    case IPM_UINT32:
+    case IPM_FLOAT32:
+        return 4;
+    case IPM_UINT64:
+        return 8;
+    }
+    return 0;
+}
+
+int num_sms();                 // cached multiprocessor count of the current device
+ipm_status last_launch_status();  // IPM_ERR_CUDA if the last launch failed
+
+}  // namespace ipm
+
+#define IPM_TRY(expr)                          \
+    do {                                       \
+        ipm_status _s = (expr);                \
+        if (_s != IPM_OK) return _s;           \
+    } while (0)
+
+#define IPM_CUDA_TRY(expr)                     \
+    do {                                       \
+        if ((expr) != cudaSuccess) {           \
+            (void)cudaGetLastError();          \
+            return IPM_ERR_CUDA;               \
+        }                                      \
+    } while (0)

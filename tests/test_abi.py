@@ -1,0 +1,92 @@
+"""The C-ABI library builds, loads without a GPU and exports every declared symbol.
+
+Only host-side paths are exercised here (queries and argument checks that return
+before any CUDA call); compute calls need a GPU and live in the gpu-marked tests.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+DECL = re.compile(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(ipm_[a-z0-9_]+)\s*\(",
+                  re.M)
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        names |= set(DECL.findall(open(h).read()))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2005_12648_gb300 import build_ext
+
+    path = build_ext.build_library()
+    import paper_2005_12648_gb300 as m
+
+    return m.load(path), m
+
+
+def test_header_declares_the_hot_path():
+    names = declared_symbols()
+    for required in ("ipm_merge_inplace", "ipm_merge_inplace_kv", "ipm_merge_splits",
+                     "ipm_merge_rearrange", "ipm_merge_pairs", "ipm_rotate",
+                     "ipm_merge_workspace_bytes", "ipm_read_device_status"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    L, m = lib
+    names = declared_symbols()
+    assert names, "no declarations parsed"
+    for n in sorted(names):
+        assert hasattr(L, n), f"{n} declared in include/ but not exported"
+    # the binding mirrors exactly the declared entry points
+    assert set(m.exported_symbols()) == names
+
+
+def test_host_queries(lib):
+    L, m = lib
+    assert m.ipm_version() >= 100
+    assert m.ipm_status_string(0) == "IPM_OK"
+    assert m.ipm_status_string(6) == "IPM_ERR_TIMEOUT"
+    G, tile = m.ipm_merge_plan(1 << 28, 1 << 28, "int32")
+    assert (1 << G) * tile >= (1 << 29) and (1 << (G - 1)) * tile < (1 << 29)
+    G0, tile0 = m.ipm_merge_plan(100, 100, "int32")
+    assert G0 == 0 and tile0 >= 200
+    Gk, tilek = m.ipm_merge_plan(1 << 26, 1 << 26, "uint32", with_values=True)
+    assert tilek < tile and (1 << Gk) * tilek >= (1 << 27)
+    ws = m.ipm_merge_workspace_bytes(1 << 28, 1 << 28, "int32")
+    # O(P): split table + plans, a few hundred bytes per pair at most
+    assert 256 < ws < 400 * (1 << G) + 4096
+    assert m.ipm_rotate_workspace_bytes() >= 256
+
+
+def test_argument_errors_return_before_any_cuda_call(lib):
+    L, m = lib
+    null = None
+    # bad dtype
+    assert L.ipm_merge_inplace(null, 10, 10, 9, 0, null, 0, null) == 2
+    # NULL buffer with data
+    assert L.ipm_merge_inplace(null, 10, 10, 0, 0, 4096, 1 << 20, null) == 1
+    # misaligned buffer
+    assert L.ipm_merge_inplace(0x1001, 10, 10, 0, 0, 4096, 1 << 20, null) == 3
+    # workspace too small
+    assert L.ipm_merge_inplace(0x1000, 10, 10, 0, 0, 4096, 16, null) == 4
+    # pairs that cannot fit one tile
+    assert L.ipm_merge_inplace(0x1000, 1 << 28, 1 << 28, 0, 1, 4096, 1 << 30, null) == 1
+    # key-value needs a uint32 payload
+    assert L.ipm_merge_inplace_kv(0x1000, 0x2000, 4, 4, 0, 3, 0, 4096, 1 << 20, null) == 2
+    # splits: zero pairs
+    assert L.ipm_merge_splits(0x1000, 4, 4, 0, 0, 0x2000, null) == 1
+    # rotate: bad element size
+    assert L.ipm_rotate(0x1000, 4, 4, 2, 0x2000, 4096, null) == 2
+    # empty inputs are a no-op that succeeds without touching the device
+    assert L.ipm_merge_inplace(null, 0, 0, 0, 0, null, 0, null) == 0
+    with pytest.raises(m.IpmError):
+        m.ipm_merge_workspace_bytes(1, 1, "int32", log2_pairs=40)

@@ -1,0 +1,180 @@
+"""GPU parity: every step of the hot path, through the C ABI, against the CPU oracle.
+
+Integer, byte and index work, so the bar is bit-exact equality everywhere.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import NAME, bits, first_diff, from_dev, to_dev
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = [np.int32, np.uint32, np.uint64, np.float32]
+
+
+def _merge_dev(ipm, dev, a, b, log2_pairs=0):
+    import torch
+
+    buf = to_dev(np.concatenate([a, b]), dev)
+    ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(a.size, b.size, NAME[a.dtype], False,
+                                                     log2_pairs), dev)
+    ipm.ipm_merge_inplace(buf, a.size, b.size, NAME[a.dtype], ws, log2_pairs)
+    torch.cuda.synchronize()
+    assert ipm.ipm_read_device_status(ws) == 0
+    return from_dev(buf, a.dtype)
+
+
+# ----------------------------------------------------------------------- step a1
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("dist", ["uniform", "dup16", "alternation", "revdisjoint"])
+def test_splits_match_oracle(ipm, dev, orc, dt, dist):
+    import torch
+
+    if dist == "alternation" and dt == np.float32:
+        pytest.skip("alternation is an integer layout")
+    for la, lb, P in [(0, 0, 1), (0, 17, 4), (17, 0, 4), (1, 1, 2), (1000, 1, 7),
+                      (70_001, 65_537, 64), (123_457, 98_765, 1000), (5000, 5000, 10_000)]:
+        if dist == "alternation" and dt == np.float32:
+            continue
+        a, b = W.make_pair(dist, dt, la, lb, seed=la + lb)
+        buf = to_dev(np.concatenate([a, b]), dev)
+        out = torch.empty(P + 1, dtype=torch.int64, device=dev)
+        ipm.ipm_merge_splits(buf, la, lb, NAME[np.dtype(dt)], P, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.uint64)
+        want = orc.splits_replay(a, b, orc.diagonals(la + lb, P))
+        assert np.array_equal(got, want), (la, lb, P)
+
+
+# ----------------------------------------------------------------------- step a2
+
+@pytest.mark.parametrize("elem", [4, 8])
+def test_rotate_matches_roll(ipm, dev, elem):
+    import torch
+
+    ws = ipm.workspace(ipm.ipm_rotate_workspace_bytes(), dev)
+    dt = np.uint32 if elem == 4 else np.uint64
+    cases = [(1, 1), (1, 2), (2, 1), (3, 5), (100, 100), (4097, 4095), (1, 100_003),
+             (100_003, 1), (65_536, 131_071), (1 << 20, (1 << 20) + 77), (999_983, 7919)]
+    for lx, ly in cases:
+        x = np.arange(lx + ly, dtype=dt) * 2654435761 % (1 << 31)
+        t = to_dev(x, dev)
+        ipm.ipm_rotate(t, lx, ly, elem, ws)
+        torch.cuda.synchronize()
+        got = from_dev(t, dt)
+        assert first_diff(got, np.roll(x, -lx)) is None, (lx, ly)
+
+
+@pytest.mark.parametrize("dt", [np.int32, np.uint64])
+@pytest.mark.parametrize("G", [1, 2, 3, 5, 8])
+def test_rearrange_matches_oracle_layout(ipm, dev, orc, dt, G):
+    import torch
+
+    for dist, la, lb in [("uniform", 50_000, 43_211), ("dup16", 30_001, 30_000),
+                         ("revdisjoint", 20_000, 20_000), ("uniform", 90_000, 77)]:
+        a, b = W.make_pair(dist, dt, la, lb, seed=G)
+        P = 1 << G
+        d = orc.diagonals(la + lb, P)
+        i = orc.splits_replay(a, b, d)
+        buf = to_dev(np.concatenate([a, b]), dev)
+        split = torch.from_numpy(i.astype(np.int64)).to(dev)
+        # workspace size grows with G; the merge query needs pairs that fit a tile
+        wsG = max(G, ipm.ipm_merge_plan(la, lb, NAME[np.dtype(dt)])[0])
+        ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, NAME[np.dtype(dt)], False,
+                                                         wsG), dev)
+        ipm.ipm_merge_rearrange(buf, None, la, lb, NAME[np.dtype(dt)], split, G, ws)
+        torch.cuda.synchronize()
+        want = orc.arrange(a, b, d, i)
+        assert first_diff(from_dev(buf, dt), want) is None, (dist, la, lb)
+
+
+# ----------------------------------------------------------------------- step a3
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_pair_merge_of_arranged_buffer(ipm, dev, orc, dt):
+    import torch
+
+    for dist, la, lb, G in [("uniform", 40_000, 39_999, 2), ("dup16", 5, 70_000, 3),
+                            ("uniform", 3, 3, 0), ("uniform", 60_000, 60_001, 4)]:
+        a, b = W.make_pair(dist, dt, la, lb, seed=11)
+        G = max(G, ipm.ipm_merge_plan(la, lb, NAME[np.dtype(dt)])[0])
+        P = 1 << G
+        d = orc.diagonals(la + lb, P)
+        i = orc.splits_replay(a, b, d)
+        buf = to_dev(orc.arrange(a, b, d, i), dev)
+        split = torch.from_numpy(i.astype(np.int64)).to(dev)
+        ipm.ipm_merge_pairs(buf, None, la, lb, NAME[np.dtype(dt)], split, G)
+        torch.cuda.synchronize()
+        assert first_diff(from_dev(buf, dt), orc.merge(a, b)) is None, (dist, la, lb)
+
+
+# ----------------------------------------------------------------------- whole path
+
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("dist", ["uniform", "dup16", "disjoint", "revdisjoint",
+                                  "alternation"])
+def test_merge_inplace_matches_oracle(ipm, dev, orc, dt, dist):
+    if dist == "alternation" and dt == np.float32:
+        pytest.skip("alternation is an integer layout")
+    _, tile = ipm.ipm_merge_plan(1, 1, NAME[np.dtype(dt)])
+    sizes = [(1, 1), (1, 0), (0, 1), (5, 3), (tile // 2, tile // 2),
+             (tile // 2 + 1, tile // 2), (int(1.7 * tile), int(2.1 * tile) + 3),
+             (3 * tile + 11, 29), (29, 3 * tile + 11), (5 * tile + 1, 4 * tile + 2)]
+    for la, lb in sizes:
+        a, b = W.make_pair(dist, dt, la, lb, seed=la * 7 + lb)
+        got = _merge_dev(ipm, dev, a, b)
+        want = orc.merge(a, b)
+        assert first_diff(got, want) is None, (dist, la, lb)
+
+
+@pytest.mark.parametrize("G", [1, 2, 4, 6, 9])
+def test_merge_inplace_forced_pair_counts(ipm, dev, orc, G):
+    for dt in (np.int32, np.uint64):
+        for dist in ("uniform", "dup16", "paper"):
+            a, b = W.make_pair(dist, dt, 20_011, 17_003, seed=G)
+            if G < ipm.ipm_merge_plan(a.size, b.size, NAME[np.dtype(dt)])[0]:
+                continue  # pairs would not fit one tile
+            got = _merge_dev(ipm, dev, a, b, log2_pairs=G)
+            assert first_diff(got, orc.merge(a, b)) is None, (dt, dist, G)
+
+
+def test_float_signed_zero_bits(ipm, dev, orc):
+    rng = np.random.default_rng(0)
+    a = np.sort(rng.choice(np.array([-1.0, -0.0, 0.0, 1.0], np.float32), 50_000))
+    b = np.sort(rng.choice(np.array([-0.0, 0.0, 2.0], np.float32), 60_000))
+    got = _merge_dev(ipm, dev, a, b)
+    assert np.array_equal(bits(got), bits(orc.merge(a, b)))
+
+
+@pytest.mark.parametrize("dt", DTYPES)
+def test_merge_inplace_kv_stable(ipm, dev, orc, dt):
+    import torch
+
+    _, tile = ipm.ipm_merge_plan(1, 1, NAME[np.dtype(dt)], with_values=True)
+    dist = "zipf" if dt != np.float32 else "dup16"
+    for la, lb in [(1, 1), (7, 0), (tile // 3, tile // 2), (3 * tile + 5, 2 * tile + 1),
+                   (4 * tile, 17)]:
+        a, b = W.make_pair(dist, dt, la, lb, seed=la + 3 * lb)
+        keys = to_dev(np.concatenate([a, b]), dev)
+        vals = torch.arange(la + lb, dtype=torch.int32, device=dev)
+        ipm.merge_inplace_kv(keys, vals, la, lb, NAME[np.dtype(dt)])
+        torch.cuda.synchronize()
+        wk, wv = orc.merge_kv(a, np.arange(la, dtype=np.uint32), b,
+                              np.arange(la, la + lb, dtype=np.uint32))
+        assert first_diff(from_dev(keys, dt), wk) is None
+        assert np.array_equal(from_dev(vals, np.uint32), wv)
+
+
+def test_async_on_a_side_stream(ipm, dev, orc):
+    import torch
+
+    a, b = W.make_pair("uniform", np.int32, 300_000, 200_000, seed=1)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        buf = to_dev(np.concatenate([a, b]), dev)
+        ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(a.size, b.size, "int32"), dev)
+        ipm.ipm_merge_inplace(buf, a.size, b.size, "int32", ws, stream=s)
+    s.synchronize()
+    assert first_diff(from_dev(buf, np.int32), orc.merge(a, b)) is None
