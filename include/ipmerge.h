@@ -156,6 +156,28 @@ ipm_status ipm_rotate(void *d_ptr, uint64_t len_x, uint64_t len_y, uint32_t elem
                       void *d_ws, size_t ws_bytes, ipm_stream_t stream);
 
 /*
+ * ipm_merge_inplace for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment variant of the same merge.
+ * Some callers cannot call cudaMalloc (another framework holds nearly all device
+ * memory in its own pool; a latency-critical path cannot afford an allocation and the
+ * synchronisation of a later cudaFree; a plain C caller has no allocator to borrow).
+ * This entry point takes no workspace: its scratch is a 4 MiB array compiled into the
+ * library, which every GPU that loads the library keeps until the process exits.
+ *   - Limit: at most 2^15 pairs, i.e. len_a + len_b <= 2^15 * tile capacity
+ *     (~1.1e9 4-byte keys, ~5.5e8 8-byte keys).  Larger inputs return
+ *     IPM_ERR_INVALID_ARG before anything is launched.  Keys only (no payload).
+ *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *   - The first call on each device looks up the array's device address (with that
+ *     device current); make that first call before any stream capture.
+ *   - Every call shares the one array.  The merge re-initialises what must start at
+ *     zero on every call, but calls that overlap on the GPU (e.g. on two streams
+ *     without ordering between them) race on it: order them.
+ * Same arguments, result and asynchrony as ipm_merge_inplace otherwise.
+ */
+ipm_status ipm_merge_inplace_noalloc(void *d_buf, uint64_t len_a, uint64_t len_b,
+                                     ipm_dtype key_dtype, ipm_stream_t stream);
+
+/*
  * Optional per-phase timing (for benchmarks).  When enabled on a host thread, the
  * merge entry points called from that thread record a CUDA event pair on their stream
  * around each launch group: phase 0 = early exit + split, 1 = exchange plan,

@@ -24,7 +24,7 @@ __all__ = [
     "ipm_merge_workspace_bytes", "ipm_merge_inplace", "ipm_merge_inplace_kv",
     "ipm_merge_splits", "ipm_merge_rearrange", "ipm_merge_pairs",
     "ipm_rotate_workspace_bytes", "ipm_rotate", "ipm_read_device_status",
-    "ipm_timing_enable", "ipm_timing_read", "IpmTiming",
+    "ipm_timing_enable", "ipm_timing_read", "IpmTiming", "ipm_merge_inplace_noalloc",
     "workspace", "merge_inplace", "merge_inplace_kv",
 ]
 
@@ -61,6 +61,7 @@ _SIGS = {
     "ipm_rotate_workspace_bytes": (_i, [ctypes.POINTER(_sz)]),
     "ipm_rotate": (_i, [_vp, _u64, _u64, _u32, _vp, _sz, _vp]),
     "ipm_read_device_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
+    "ipm_merge_inplace_noalloc": (_i, [_vp, _u64, _u64, _i, _vp]),
     "ipm_timing_enable": (_i, [_i]),
     "ipm_timing_read": (_i, [ctypes.c_void_p]),
 }
@@ -226,6 +227,14 @@ def ipm_read_device_status(ws, stream=None) -> int:
     _check(load().ipm_read_device_status(_ptr(ws), _stream(stream), ctypes.byref(out)),
            "ipm_read_device_status")
     return int(out.value)
+
+
+def ipm_merge_inplace_noalloc(buf, len_a: int, len_b: int, key_dtype, stream=None) -> None:
+    """The merge for callers that cannot allocate device memory: no workspace
+    argument; the library's own fixed 4 MiB scratch array is used instead (at most
+    2^15 pairs per call, keys only; calls that overlap on the GPU race on it)."""
+    _check(load().ipm_merge_inplace_noalloc(_ptr(buf), len_a, len_b, _dt(key_dtype),
+                                            _stream(stream)), "ipm_merge_inplace_noalloc")
 
 
 def ipm_timing_enable(enable: bool = True) -> None:
