@@ -149,11 +149,22 @@ ipm_status ipm_merge_pairs(void *d_buf, void *d_vals, uint64_t len_a, uint64_t l
 /*
  * Partition exchange alone (Sec. 3.4): d_ptr[0, len_x + len_y) = [X | Y] becomes
  * [Y | X] in place.  elem_bytes is 4 or 8 (the bytes are moved, never compared).
- * Same result as linear shifting; uses the workspace of ipm_rotate_workspace_bytes.
+ * Executed as linear shifting: LS block swaps while both the size difference and the
+ * smaller block are larger than the on-chip stash, then the remaining LS steps in
+ * closed form in one pass (every element read and written once).  The workspace size
+ * comes from ipm_rotate_workspace_bytes for the same sizes.
  */
-ipm_status ipm_rotate_workspace_bytes(size_t *bytes);
+ipm_status ipm_rotate_workspace_bytes(uint64_t len_x, uint64_t len_y, uint32_t elem_bytes,
+                                      size_t *bytes);
 ipm_status ipm_rotate(void *d_ptr, uint64_t len_x, uint64_t len_y, uint32_t elem_bytes,
                       void *d_ws, size_t ws_bytes, ipm_stream_t stream);
+
+/*
+ * Algorithmic bytes the exchange levels of the last merge (or rotate) that used this
+ * workspace moved: 2 bytes-per-element for every element of a one-pass exchange, 4 per
+ * swapped pair of an LS block swap.  Synchronises `stream`.
+ */
+ipm_status ipm_read_exchange_bytes(const void *d_ws, ipm_stream_t stream, uint64_t *out);
 
 /*
  * ipm_merge_inplace for callers that cannot allocate device memory.  The paper has no
@@ -181,7 +192,7 @@ ipm_status ipm_merge_inplace_noalloc(void *d_buf, uint64_t len_a, uint64_t len_b
  * Optional per-phase timing (for benchmarks).  When enabled on a host thread, the
  * merge entry points called from that thread record a CUDA event pair on their stream
  * around each launch group: phase 0 = early exit + split, 1 = exchange plan,
- * 2 = exchange levels, 3 = pair merge.  ipm_timing_read waits for the recorded events,
+ * 2 = exchange levels (one launch per level), 3 = pair merge.  ipm_timing_read waits for the recorded events,
  * adds their elapsed times and kernel-launch counts into *out and forgets them.
  * Timing adds two event records per group and changes no kernel.
  */

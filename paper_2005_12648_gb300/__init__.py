@@ -24,6 +24,7 @@ __all__ = [
     "ipm_merge_workspace_bytes", "ipm_merge_inplace", "ipm_merge_inplace_kv",
     "ipm_merge_splits", "ipm_merge_rearrange", "ipm_merge_pairs",
     "ipm_rotate_workspace_bytes", "ipm_rotate", "ipm_read_device_status",
+    "ipm_read_exchange_bytes",
     "ipm_timing_enable", "ipm_timing_read", "IpmTiming", "ipm_merge_inplace_noalloc",
     "workspace", "merge_inplace", "merge_inplace_kv",
 ]
@@ -58,7 +59,8 @@ _SIGS = {
     "ipm_merge_splits": (_i, [_vp, _u64, _u64, _i, _u64, _vp, _vp]),
     "ipm_merge_rearrange": (_i, [_vp, _vp, _u64, _u64, _i, _vp, _u32, _vp, _sz, _vp]),
     "ipm_merge_pairs": (_i, [_vp, _vp, _u64, _u64, _i, _vp, _u32, _vp]),
-    "ipm_rotate_workspace_bytes": (_i, [ctypes.POINTER(_sz)]),
+    "ipm_rotate_workspace_bytes": (_i, [_u64, _u64, _u32, ctypes.POINTER(_sz)]),
+    "ipm_read_exchange_bytes": (_i, [_vp, _vp, ctypes.POINTER(_u64)]),
     "ipm_rotate": (_i, [_vp, _u64, _u64, _u32, _vp, _sz, _vp]),
     "ipm_read_device_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
     "ipm_merge_inplace_noalloc": (_i, [_vp, _u64, _u64, _i, _vp]),
@@ -209,9 +211,17 @@ def ipm_merge_pairs(buf, vals, len_a: int, len_b: int, key_dtype, split_a,
            "ipm_merge_pairs")
 
 
-def ipm_rotate_workspace_bytes() -> int:
+def ipm_rotate_workspace_bytes(len_x: int, len_y: int, elem_bytes: int) -> int:
     out = _sz(0)
-    _check(load().ipm_rotate_workspace_bytes(ctypes.byref(out)), "ipm_rotate_workspace_bytes")
+    _check(load().ipm_rotate_workspace_bytes(len_x, len_y, elem_bytes, ctypes.byref(out)),
+           "ipm_rotate_workspace_bytes")
+    return int(out.value)
+
+
+def ipm_read_exchange_bytes(ws, stream=None) -> int:
+    out = _u64(0)
+    _check(load().ipm_read_exchange_bytes(_ptr(ws), _stream(stream), ctypes.byref(out)),
+           "ipm_read_exchange_bytes")
     return int(out.value)
 
 

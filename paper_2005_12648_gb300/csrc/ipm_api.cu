@@ -1,7 +1,9 @@
 // The extern "C" entry points of include/ipmerge.h: argument checks, workspace layout
 // and the launch sequence of the hot path (split -> level exchanges -> pair merge).
+#include <cstddef>
 #include <vector>
 
+#include "ipm_exchange.cuh"
 #include "ipm_internal.h"
 
 namespace ipm {
@@ -113,12 +115,12 @@ struct MergeLayout {
     size_t split_off, plan_off, total;
 };
 
-MergeLayout merge_layout(uint32_t G) {
+MergeLayout merge_layout(uint32_t G, uint64_t n, ipm_dtype key, bool kv) {
     MergeLayout L;
     const uint64_t P = uint64_t(1) << G;
     L.split_off = kStatusBytes;
     L.plan_off = L.split_off + align_up(sizeof(uint64_t) * (P + 1), 256);
-    L.total = L.plan_off + plan_area_bytes(G);
+    L.total = L.plan_off + xplan_area_bytes(G, n, key, kv);
     return L;
 }
 
@@ -134,14 +136,14 @@ ipm_status merge_core(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_d
     if (!aligned(buf, size_t(dtype_bytes(key))) || (kv && !aligned(vals, 4)))
         return IPM_ERR_ALIGNMENT;
     if (!aligned(ws, 256)) return IPM_ERR_ALIGNMENT;
-    const MergeLayout L = merge_layout(G);
+    const uint64_t n = la + lb;
+    const MergeLayout L = merge_layout(G, n, key, kv);
     if (ws_bytes < L.total) return IPM_ERR_WORKSPACE;
     char *w = static_cast<char *>(ws);
     StatusBlock *sb = reinterpret_cast<StatusBlock *>(w);
     uint64_t *split = reinterpret_cast<uint64_t *>(w + L.split_off);
-    const PlanArea pa = plan_area_at(w + L.plan_off, G);
+    const XPlanArea pa = xplan_area_at(w + L.plan_off, G, n, key, kv);
     const uint64_t P = uint64_t(1) << G;
-    const uint64_t n = la + lb;
 
     {
         PhaseScope ps(0, 2, stream);
@@ -154,11 +156,11 @@ ipm_status merge_core(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_d
     if (G > 0) {
         {
             PhaseScope ps(1, 1, stream);
-            IPM_TRY(launch_plan_levels(split, n, G, pa, sb, stream));
+            IPM_TRY(launch_xplan_levels(split, n, G, pa, key, kv, sb, stream));
         }
         for (uint32_t l = 0; l < G; ++l) {
-            PhaseScope ps(2, 2, stream);
-            IPM_TRY(launch_level_exchange(buf, vals, dtype_bytes(key), n, l, pa, sb, stream));
+            PhaseScope ps(2, 1, stream);
+            IPM_TRY(launch_exchange_level(buf, vals, key, n, l, pa, sb, stream));
         }
     }
     // a3: per-pair merge
@@ -214,7 +216,7 @@ ipm_status ipm_merge_workspace_bytes(uint64_t len_a, uint64_t len_b, ipm_dtype k
     if (bytes == nullptr) return IPM_ERR_INVALID_ARG;
     uint32_t G = 0;
     IPM_TRY(check_merge_args(len_a, len_b, key_dtype, with_values != 0, log2_pairs, &G));
-    *bytes = merge_layout(G).total;
+    *bytes = merge_layout(G, len_a + len_b, key_dtype, with_values != 0).total;
     return IPM_OK;
 }
 
@@ -267,17 +269,18 @@ ipm_status ipm_merge_rearrange(void *d_buf, void *d_vals, uint64_t len_a, uint64
     if (!aligned(d_buf, size_t(dtype_bytes(key_dtype))) || (kv && !aligned(d_vals, 4)) ||
         !aligned(d_ws, 256))
         return IPM_ERR_ALIGNMENT;
-    const MergeLayout L = merge_layout(G);
+    const uint64_t n = len_a + len_b;
+    const MergeLayout L = merge_layout(G, n, key_dtype, kv);
     if (ws_bytes < L.total) return IPM_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     char *w = static_cast<char *>(d_ws);
     StatusBlock *sb = reinterpret_cast<StatusBlock *>(w);
     IPM_CUDA_TRY(cudaMemsetAsync(sb, 0, kStatusBytes, st));
-    const PlanArea pa = plan_area_at(w + L.plan_off, G);
-    IPM_TRY(launch_plan_levels(d_split_a, len_a + len_b, G, pa, sb, st));
+    const XPlanArea pa = xplan_area_at(w + L.plan_off, G, n, key_dtype, kv);
+    IPM_TRY(launch_xplan_levels(d_split_a, n, G, pa, key_dtype, kv, sb, st));
     for (uint32_t l = 0; l < G; ++l)
-        IPM_TRY(launch_level_exchange(d_buf, static_cast<uint32_t *>(d_vals),
-                                      dtype_bytes(key_dtype), len_a + len_b, l, pa, sb, st));
+        IPM_TRY(launch_exchange_level(d_buf, static_cast<uint32_t *>(d_vals), key_dtype, n, l,
+                                      pa, sb, st));
     return IPM_OK;
 }
 
@@ -296,28 +299,45 @@ ipm_status ipm_merge_pairs(void *d_buf, void *d_vals, uint64_t len_a, uint64_t l
                              d_split_a, G, nullptr, (cudaStream_t)stream);
 }
 
-ipm_status ipm_rotate_workspace_bytes(size_t *bytes) {
+ipm_status ipm_rotate_workspace_bytes(uint64_t len_x, uint64_t len_y, uint32_t elem_bytes,
+                                      size_t *bytes) {
     if (bytes == nullptr) return IPM_ERR_INVALID_ARG;
-    *bytes = kStatusBytes + plan_area_bytes(1);
+    if (elem_bytes != 4 && elem_bytes != 8) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (len_x > (uint64_t(1) << 40) || len_y > (uint64_t(1) << 40)) return IPM_ERR_INVALID_ARG;
+    const ipm_dtype t = elem_bytes == 4 ? IPM_UINT32 : IPM_UINT64;
+    *bytes = kStatusBytes + xplan_area_bytes(1, 2 * (len_x + len_y), t, false);
     return IPM_OK;
 }
 
 ipm_status ipm_rotate(void *d_ptr, uint64_t len_x, uint64_t len_y, uint32_t elem_bytes,
                       void *d_ws, size_t ws_bytes, ipm_stream_t stream) {
-    if (elem_bytes != 4 && elem_bytes != 8) return IPM_ERR_UNSUPPORTED_DTYPE;
-    if (len_x > (uint64_t(1) << 40) || len_y > (uint64_t(1) << 40)) return IPM_ERR_INVALID_ARG;
+    size_t need = 0;
+    IPM_TRY(ipm_rotate_workspace_bytes(len_x, len_y, elem_bytes, &need));
     if (len_x == 0 || len_y == 0) return IPM_OK;
     if (d_ptr == nullptr) return IPM_ERR_INVALID_ARG;
-    if (d_ws == nullptr || ws_bytes < kStatusBytes + plan_area_bytes(1))
-        return IPM_ERR_WORKSPACE;
+    if (d_ws == nullptr || ws_bytes < need) return IPM_ERR_WORKSPACE;
     if (!aligned(d_ptr, elem_bytes) || !aligned(d_ws, 256)) return IPM_ERR_ALIGNMENT;
+    const ipm_dtype t = elem_bytes == 4 ? IPM_UINT32 : IPM_UINT64;
     cudaStream_t st = (cudaStream_t)stream;
     char *w = static_cast<char *>(d_ws);
     StatusBlock *sb = reinterpret_cast<StatusBlock *>(w);
     IPM_CUDA_TRY(cudaMemsetAsync(sb, 0, kStatusBytes, st));
-    const PlanArea pa = plan_area_at(w + kStatusBytes, 1);
-    IPM_TRY(launch_plan_single(len_x, len_y, pa, st));
-    return launch_level_exchange(d_ptr, nullptr, int(elem_bytes), len_x + len_y, 0, pa, sb, st);
+    // one exchange at offset 0: level 0 of a layout sized for 2(len_x + len_y) keys, so
+    // the flag area covers every item of this exchange
+    const XPlanArea pa = xplan_area_at(w + kStatusBytes, 1, 2 * (len_x + len_y), t, false);
+    IPM_TRY(launch_xplan_single(len_x, len_y, pa, t, st));
+    return launch_exchange_level(d_ptr, nullptr, t, len_x + len_y, 0, pa, sb, st);
+}
+
+ipm_status ipm_read_exchange_bytes(const void *d_ws, ipm_stream_t stream, uint64_t *out) {
+    if (d_ws == nullptr || out == nullptr) return IPM_ERR_INVALID_ARG;
+    unsigned long long v = 0;
+    IPM_CUDA_TRY(cudaMemcpyAsync(&v, static_cast<const char *>(d_ws) +
+                                         offsetof(StatusBlock, exchange_bytes),
+                                 sizeof(v), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    IPM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    *out = uint64_t(v);
+    return IPM_OK;
 }
 
 ipm_status ipm_timing_enable(int enable) {

@@ -16,15 +16,20 @@ __device__ __forceinline__ bool key_le(K x, K y) { return x <= y; }
 
 // ---------------------------------------------------------------------------------
 // Workspace status block (first 256 bytes of every workspace).
-//   word 0  device status (ipm_status), first error wins
-//   word 1  early-exit flag: nonzero when the runs are already in order (Alg. 2/3)
-//   word 2+ per-call counters used by persistent kernels
+//   status          device status (ipm_status), first error wins
+//   done            early-exit flag: nonzero when the runs are already in order
+//   exchange_bytes  algorithmic bytes of the exchange levels of the current call
+//   counters        per-call ticket counters of the persistent kernels
+// All of it is reset at the start of every call.
 // ---------------------------------------------------------------------------------
 struct StatusBlock {
     unsigned int status;
     unsigned int done;
-    unsigned int counters[62];
+    unsigned long long exchange_bytes;
+    unsigned int counters[60];
 };
+
+constexpr uint32_t kTicketCounter0 = 0;  // counters[l]: exchange tickets of level l
 static_assert(sizeof(StatusBlock) == 256, "status block is 256 bytes");
 
 constexpr size_t kStatusBytes = 256;

@@ -5,38 +5,21 @@
 
 namespace ipm {
 
-// One contiguous range of a reversal pass: elements [start, start + len).
-struct Seg {
-    uint64_t start;
-    uint64_t len;
+// Exchange plans of all levels in one workspace area (see ipm_exchange.cu).
+struct XPlanArea {
+    void *plans;        // RotPlan per exchange, level l at offset 2^l - 1
+    uint32_t *item_pf;  // item prefix per level, level l at offset 2^l - 1 + l
+    uint32_t *join;     // per-exchange completed-item counters, level l at 2^l - 1
+    uint32_t *flags;    // per-item "reads done" flags, shared by the levels
+    uint64_t nflags;
+    size_t zero_bytes;  // join .. end of flags, cleared on every call
 };
 
-// Reversal work is cut into units of kRevUnit element pairs.
-constexpr uint32_t kRevThreads = 256;
-constexpr uint32_t kRevItems = 8;
-constexpr uint64_t kRevUnit = uint64_t(kRevThreads) * kRevItems;
-
-// Per-level exchange plans, all levels in one area of the workspace.  Level l
-// (2^l rotations) owns
-//   seg1[2(2^l-1) .. +2^{l+1})   pass 1: X_r and Y_r of rotation r
-//   pf1 [2(2^l-1) + l .. +2^{l+1}+1)  unit prefix of pass 1
-//   seg2[(2^l-1) .. +2^l)        pass 2: the whole middle X_r|Y_r
-//   pf2 [(2^l-1) + l .. +2^l+1)  unit prefix of pass 2
-struct PlanArea {
-    Seg *seg1;
-    uint32_t *pf1;
-    Seg *seg2;
-    uint32_t *pf2;
-};
-
-inline uint64_t seg1_base(uint32_t l) { return 2ull * ((1ull << l) - 1); }
-inline uint64_t pf1_base(uint32_t l) { return 2ull * ((1ull << l) - 1) + l; }
-inline uint64_t seg2_base(uint32_t l) { return (1ull << l) - 1; }
-inline uint64_t pf2_base(uint32_t l) { return ((1ull << l) - 1) + l; }
-
-// Bytes of a PlanArea for G levels (each array 256-byte aligned).
-size_t plan_area_bytes(uint32_t G);
-PlanArea plan_area_at(void *base, uint32_t G);
+struct XParams;
+XParams exchange_params(ipm_dtype key, bool with_values);
+uint64_t max_level_items(uint32_t G, uint64_t n, const XParams &prm);
+size_t xplan_area_bytes(uint32_t G, uint64_t n, ipm_dtype key, bool with_values);
+XPlanArea xplan_area_at(void *base, uint32_t G, uint64_t n, ipm_dtype key, bool with_values);
 
 // Tile (pair) capacity of the shared-memory merge, in elements.
 uint64_t tile_capacity(ipm_dtype key, bool with_values);
@@ -53,16 +36,18 @@ ipm_status launch_splits(const void *buf, uint64_t la, uint64_t lb, ipm_dtype ke
                          uint64_t P, uint64_t *split, const StatusBlock *sb,
                          cudaStream_t stream);
 
-// Plans of all G levels from a split table with P = 2^G.
-ipm_status launch_plan_levels(const uint64_t *split, uint64_t n, uint32_t G,
-                              PlanArea pa, const StatusBlock *sb, cudaStream_t stream);
+// Plans (and zeroed flags) of all G levels from a split table with P = 2^G.
+ipm_status launch_xplan_levels(const uint64_t *split, uint64_t n, uint32_t G, XPlanArea pa,
+                               ipm_dtype key, bool with_values, StatusBlock *sb,
+                               cudaStream_t stream);
 
-// Plan of a single exchange [X|Y] at offset 0 (G = 1 layout, level 0).
-ipm_status launch_plan_single(uint64_t lx, uint64_t ly, PlanArea pa, cudaStream_t stream);
+// Plan of a single exchange [X|Y] at offset 0 (level 0 of a G = 1 layout).
+ipm_status launch_xplan_single(uint64_t lx, uint64_t ly, XPlanArea pa, ipm_dtype key,
+                               cudaStream_t stream);
 
-// The two reversal passes of level l (the exchange of every middle pair).
-ipm_status launch_level_exchange(void *buf, uint32_t *vals, int elem_bytes, uint64_t n,
-                                 uint32_t l, PlanArea pa, StatusBlock *sb,
+// The exchanges of level l, one persistent launch.
+ipm_status launch_exchange_level(void *buf, uint32_t *vals, ipm_dtype key, uint64_t n,
+                                 uint32_t l, XPlanArea pa, StatusBlock *sb,
                                  cudaStream_t stream);
 
 // Per-pair shared-memory merge of an arranged buffer.

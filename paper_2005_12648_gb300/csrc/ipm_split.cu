@@ -19,7 +19,8 @@ __global__ void early_exit_kernel(const K *buf, uint64_t la, uint64_t lb, Status
         if (!done) done = key_le(buf[la - 1], buf[la]) ? 1u : 0u;
         sb->status = 0u;
         sb->done = done;
-        for (int q = 0; q < 62; ++q) sb->counters[q] = 0u;
+        sb->exchange_bytes = 0ull;
+        for (int q = 0; q < 60; ++q) sb->counters[q] = 0u;
     }
 }
 

@@ -64,7 +64,7 @@ def test_host_queries(lib):
     ws = m.ipm_merge_workspace_bytes(1 << 28, 1 << 28, "int32")
     # O(P): split table + plans, a few hundred bytes per pair at most
     assert 256 < ws < 400 * (1 << G) + 4096
-    assert m.ipm_rotate_workspace_bytes() >= 256
+    assert m.ipm_rotate_workspace_bytes(1000, 10, 4) >= 256
 
 
 def test_argument_errors_return_before_any_cuda_call(lib):

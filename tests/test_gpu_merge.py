@@ -54,13 +54,17 @@ def test_splits_match_oracle(ipm, dev, orc, dt, dist):
 def test_rotate_matches_roll(ipm, dev, elem):
     import torch
 
-    ws = ipm.workspace(ipm.ipm_rotate_workspace_bytes(), dev)
     dt = np.uint32 if elem == 4 else np.uint64
     cases = [(1, 1), (1, 2), (2, 1), (3, 5), (100, 100), (4097, 4095), (1, 100_003),
-             (100_003, 1), (65_536, 131_071), (1 << 20, (1 << 20) + 77), (999_983, 7919)]
+             (100_003, 1), (65_536, 131_071), (1 << 20, (1 << 20) + 77), (999_983, 7919),
+             # both the size difference and the smaller block exceed the on-chip stash:
+             # linear-shifting block swaps first, then the closed-form pass
+             (3_000_017, 260_001), (260_001, 2_900_011), (1_000_003, 700_001),
+             (700_001, 1_000_003), (4_000_037, 3_700_019)]
     for lx, ly in cases:
         x = np.arange(lx + ly, dtype=dt) * 2654435761 % (1 << 31)
         t = to_dev(x, dev)
+        ws = ipm.workspace(ipm.ipm_rotate_workspace_bytes(lx, ly, elem), dev)
         ipm.ipm_rotate(t, lx, ly, elem, ws)
         torch.cuda.synchronize()
         got = from_dev(t, dt)
