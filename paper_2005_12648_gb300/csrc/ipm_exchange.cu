@@ -21,6 +21,7 @@
 // in time; on expiry the kernel records IPM_ERR_TIMEOUT and all CTAs leave.
 #include "ipm_exchange.cuh"
 #include "ipm_internal.h"
+#include "ipm_tma.cuh"
 
 namespace ipm {
 
@@ -182,215 +183,337 @@ __device__ bool wait_count(const uint32_t *ctr, uint32_t target) {
     return true;
 }
 
-template <typename K, bool KV, int THREADS, int PP>
+// ---- TMA-staged executor: one persistent 512-thread CTA per SM, two shared-memory
+// stages.  A stage holds two "slots"; an item moves at most two contiguous blocks
+// (physical ranges: a mirrored primed range is still contiguous and keeps its order),
+// each staged in one slot (a SHIFT tile, stash chunk or SINGLE exchange spans both).
+
+template <typename K, bool KV>
 struct XCfg {
-    static constexpr uint32_t kPairTile = uint32_t(THREADS) * PP;
-    static constexpr uint32_t kShiftTile = 2u * kPairTile;
-    static constexpr uint32_t kSmemBudget = 110u * 1024u;  // two CTAs per SM
-    static constexpr uint32_t kCap = kSmemBudget / (sizeof(K) + (KV ? 4u : 0u));
+    static constexpr int kThreads = 512;
+    static constexpr uint32_t kStageBytes = 104u * 1024u;
+    static constexpr uint32_t kElemBytes = uint32_t(sizeof(K)) + (KV ? 4u : 0u);
+    static constexpr uint32_t kKPad = 16u / uint32_t(sizeof(K));  // phase slack, keys
+    static constexpr uint32_t kVPad = 4u;                         // phase slack, values
+    // elements per slot, a multiple of 32
+    static constexpr uint32_t kSlot =
+        ((kStageBytes / (2u * kElemBytes)) - (kKPad > kVPad ? kKPad : kVPad) - 16u) / 32u * 32u;
+    static constexpr uint32_t kSlotK = kSlot + kKPad;  // key slot stride (elements)
+    static constexpr uint32_t kSlotV = kSlot + kVPad;  // value slot stride (elements)
+    static constexpr size_t kStageKBytes = (size_t(2) * kSlotK * sizeof(K) + 15) / 16 * 16;
+    static constexpr size_t kStageVBytes = KV ? (size_t(2) * kSlotV * 4 + 15) / 16 * 16 : 0;
+    static constexpr size_t kStageSize = kStageKBytes + kStageVBytes;
+    static constexpr size_t kSmem = 2 * kStageSize + 64;  // two stages + two mbarriers
     static constexpr uint32_t kMaxHolders = 8;
-    static constexpr size_t kSmem = size_t(kCap) * sizeof(K) + (KV ? size_t(kCap) * 4 : 0);
+    // pair tile = one slot per block; shift tile, stash chunk and SINGLE exchange = two
+    // slots (they start at slot 0 with their own phase offset < kKPad)
+    // a SINGLE exchange is staged across both stages (keys, then values)
+    static constexpr uint32_t kSingleCap =
+        uint32_t((2 * kStageSize - 64) / kElemBytes) / 32u * 32u;
     __host__ __device__ static XParams params() {
-        return XParams{kPairTile, kShiftTile, kCap, kMaxHolders};
+        return XParams{kSlot, 2 * kSlot, 2 * kSlot, kMaxHolders, kSingleCap};
     }
 };
 
-constexpr int kCopyBatch = 8;
-
-// All threads: stash[u - u0] = base[phys(off + u)] for u in [u0, u1), where
-// phys(p) = mirror ? m-1-p : p; loads issued in batches.  u1 - u0 <= stash capacity.
-template <typename K, bool KV, int THREADS>
-__device__ __noinline__ void copy_in(K *stk, uint32_t *stv, const K *base,
-                                     const uint32_t *vbase, uint32_t mirror, uint64_t m,
-                                     uint64_t off, uint64_t u0, uint64_t u1) {
-    const uint32_t cnt = uint32_t(u1 - u0);
-    const uint64_t first = off + u0;
-    for (uint32_t c = 0; c < cnt; c += uint32_t(THREADS) * kCopyBatch) {
-        K kk[kCopyBatch];
-        uint32_t vv[kCopyBatch];
-#pragma unroll
-        for (int k = 0; k < kCopyBatch; ++k) {
-            const uint32_t u = c + uint32_t(k) * THREADS + threadIdx.x;
-            if (u < cnt) {
-                const uint64_t p = mirror ? m - 1 - (first + u) : first + u;
-                kk[k] = __ldcg(base + p);
-                if (KV) vv[k] = __ldcg(vbase + p);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < kCopyBatch; ++k) {
-            const uint32_t u = c + uint32_t(k) * THREADS + threadIdx.x;
-            if (u < cnt) {
-                stk[u] = kk[k];
-                if (KV) stv[u] = vv[k];
-            }
-        }
-    }
-}
-
-// All threads: base[phys(off + u)] = stash[u - u0] for u in [u0, u1).
-template <typename K, bool KV, int THREADS>
-__device__ __noinline__ void copy_out(const K *stk, const uint32_t *stv, K *base,
-                                      uint32_t *vbase, uint32_t mirror, uint64_t m,
-                                      uint64_t off, uint64_t u0, uint64_t u1) {
-    const uint32_t cnt = uint32_t(u1 - u0);
-    const uint64_t first = off + u0;
-    for (uint32_t u = threadIdx.x; u < cnt; u += THREADS) {
-        const uint64_t p = mirror ? m - 1 - (first + u) : first + u;
-        base[p] = stk[u];
-        if (KV) vbase[p] = stv[u];
-    }
-}
-
-// Thread 0: one non-blocking pass over flags[lo..hi]; true if all reached tag.
-__device__ __forceinline__ bool flags_ready(const uint32_t *flags, uint32_t lo, uint32_t hi,
-                                            uint32_t tag) {
-    for (uint32_t q = lo; q <= hi; ++q)
-        if (ld_flag(flags + q) < tag) return false;
-    return true;
-}
-
-__device__ __forceinline__ uint32_t key_bits_lo(int32_t x) { return uint32_t(x); }
-__device__ __forceinline__ uint32_t key_bits_lo(uint32_t x) { return x; }
-__device__ __forceinline__ uint32_t key_bits_lo(float x) { return __float_as_uint(x); }
-__device__ __forceinline__ uint32_t key_bits_lo(uint64_t x) {
-    return uint32_t(x) ^ uint32_t(x >> 32);
-}
-
-// The flags a tile's writes depend on, as up to two index ranges (lo > hi: empty).
+// The flags a store depends on, as up to two index ranges (lo > hi: empty).
 struct Deps {
     uint32_t lo0, hi0, lo1, hi1;
 };
 
-struct Shared {
-    uint32_t next;
-    int abort;
-    uint32_t magic;  // runtime value the load fold is compared with
-    uint32_t sink;   // written when the comparison happens to hold; never read
+struct Move {
+    uint64_t src, dst, len;  // absolute element offsets in the buffer
 };
 
-// Move of one tile: `cnt` element pairs (PAIR, SWAP) or single elements (SHIFT).
-// Element k of this thread: source s0/s1, destination d0/d1 (physical offsets).
-template <typename K, bool KV, int THREADS, int PP>
-__device__ __noinline__ void tile_move(K *base, uint32_t *vbase, uint32_t kind,
-                                          uint32_t mirror, uint64_t m, uint64_t t0,
-                                          uint64_t t1, uint64_t rd1, uint64_t wr1,
-                                          const uint32_t *flags, uint32_t my_flag,
-                                          uint32_t tag, const Deps &dp, Shared &sh,
-                                          StatusBlock *sb) {
-    // PAIR : reads p(t), p(rd1+t); writes p(t) <- second, p(wr1+t) <- first
-    // SWAP : reads t, rd1+t;        writes t <- second, rd1+t <- first  (mirror = 0)
-    // SHIFT: reads p(rd1+t) for 2*PP elements per thread; writes p(t)
+// A decoded item.
+struct Item {
+    uint32_t r, before, nmoves;
+    bool holder, final_phase, single, flag;
+    uint32_t ticket;
+    Move mv[2];
+    uint64_t single_m, single_a;  // SINGLE: exchange size and rotation
+    Deps dp;
+};
+
+struct Shared {
+    uint32_t ticket[2];
+    int abort;
+};
+
+// Thread 0: wait until flags[lo..hi] all reach tag (empty range: true).  While
+// waiting, publish the prefetched item's flag (`my_flag`) as soon as its staging
+// mbarrier completes.  False on timeout.
+__device__ bool wait_flag_range_poll(const uint32_t *flags, uint32_t lo, uint32_t hi,
+                                     uint32_t tag, bool nxt_loaded, bool nxt_flag,
+                                     uint64_t *nbar, uint32_t nparity, uint32_t *my_flag,
+                                     bool &published) {
+    unsigned long long t0 = 0;
+    for (uint32_t q = lo; q <= hi && lo <= hi; ++q) {
+        uint32_t it = 0;
+        while (ld_flag(flags + q) < tag) {
+            if (nxt_loaded && nxt_flag && !published && mbar_try_wait(nbar, nparity)) {
+                st_flag(my_flag, tag);
+                published = true;
+            }
+            if ((++it & 63u) == 0) {
+                const unsigned long long now = globaltimer_ns();
+                if (t0 == 0)
+                    t0 = now;
+                else if (now - t0 > kWaitLimitNs)
+                    return false;
+            }
+        }
+    }
+    return true;
+}
+
+// Decode ticket t of a level plan into an item.  Every thread computes the same item.
+__device__ __forceinline__ bool decode_item(const XParams &prm, uint32_t t, uint32_t &rot_hint,
+                                            const uint32_t *pf, const RotPlan *plans,
+                                            uint32_t nrot, uint64_t n, Item &it) {
+    // the exchange holding t is the last one with pf[r] <= t; a CTA's tickets only
+    // grow, so gallop forward from the previous one
+    if (pf[rot_hint + 1] <= t) {
+        uint32_t lo = rot_hint + 1, step = 1;
+        while (lo + step < nrot && pf[lo + step] <= t) {
+            lo += step;
+            step <<= 1;
+        }
+        uint32_t hi = lo + step < nrot ? lo + step : nrot;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (pf[mid] <= t)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        rot_hint = lo;
+    }
+    const uint32_t r = rot_hint;
+    const uint32_t j = t - pf[r];
+    const RotPlan q = plans[r];
+    XPhase ph;
+    uint64_t s = q.s, a = q.a, b = q.b;
+    uint32_t before = 0;
+    bool found = false;
+    while (x_phase(prm, s, a, b, ph)) {
+        if (j < before + ph.items()) {
+            found = true;
+            break;
+        }
+        before += ph.items();
+        if (ph.final_phase) break;
+        x_after_step(ph, s, a, b);
+    }
+    const uint64_t m = ph.a + ph.b;
+    if (!found || ph.s > n || m > n - ph.s) return false;
+    const uint32_t jj = j - before;
+    const uint32_t fb = pf[r] + before;  // flag of item 0 of this phase
+    it.ticket = t;
+    it.r = r;
+    it.before = before;
+    it.final_phase = ph.final_phase;
+    it.single = ph.kind == XK_SINGLE;
+    it.holder = (ph.kind == XK_PAIR || ph.kind == XK_SHIFT) && jj < ph.holders;
+    it.flag = ph.kind == XK_PAIR || ph.kind == XK_SHIFT;
+    it.dp = Deps{1, 0, 1, 0};
+    it.single_m = 0;
+    it.single_a = 0;
+    const uint64_t base = ph.s;
+    const uint32_t mirror = ph.mirror;
+    // physical start of the primed range [x0, x0 + len)
+    auto pr = [base, mirror, m](uint64_t x0, uint64_t len) -> uint64_t {
+        return base + (mirror ? m - x0 - len : x0);
+    };
+    if (ph.kind == XK_SINGLE) {
+        it.nmoves = 1;
+        it.mv[0] = Move{base, base, m};
+        it.single_m = m;
+        it.single_a = ph.a;
+    } else if (ph.kind == XK_SWAP) {
+        const uint64_t mn = ph.a < ph.b ? ph.a : ph.b;
+        const uint64_t off2 = ph.a >= ph.b ? ph.a : ph.b;
+        const uint64_t t0 = uint64_t(jj) * prm.pair_tile;
+        const uint64_t L = (t0 + prm.pair_tile < mn ? t0 + prm.pair_tile : mn) - t0;
+        it.nmoves = 2;
+        it.mv[0] = Move{base + t0, base + off2 + t0, L};
+        it.mv[1] = Move{base + off2 + t0, base + t0, L};
+    } else if (it.holder) {
+        // PAIR: stash X'[Bp, Ap) lands at 2Bp; its landing slots hold Y'[Bp-e+u), read
+        //       by the tiles covering those offsets.
+        // SHIFT: stash X'[0, sz) lands at m-sz; the slots hold Y'[m-2sz+u).
+        const bool pair = ph.kind == XK_PAIR;
+        const uint64_t Bp = ph.a < ph.b ? ph.a : ph.b;
+        const uint64_t dlt = ph.delta;
+        const uint64_t h0 = uint64_t(jj) * prm.cap;
+        const uint64_t h1 = h0 + prm.cap < dlt ? h0 + prm.cap : dlt;
+        const uint64_t src_off = pair ? Bp : 0;
+        const uint64_t dst_off = pair ? 2 * Bp : m - dlt;
+        const uint64_t rd_off = pair ? Bp - dlt : m - 2 * dlt;
+        const uint64_t tile = pair ? prm.pair_tile : prm.shift_tile;
+        it.nmoves = 1;
+        it.mv[0] = Move{pr(src_off + h0, h1 - h0), pr(dst_off + h0, h1 - h0), h1 - h0};
+        it.dp.lo0 = fb + ph.holders + uint32_t((rd_off + h0) / tile);
+        it.dp.hi0 = fb + ph.holders + uint32_t((rd_off + h1 - 1) / tile);
+    } else {
+        const bool pair = ph.kind == XK_PAIR;
+        const uint32_t qt = jj - ph.holders;
+        const uint64_t dlt = ph.delta;
+        const uint64_t Bp = ph.a < ph.b ? ph.a : ph.b;
+        const uint64_t tile = pair ? prm.pair_tile : prm.shift_tile;
+        const uint64_t work = pair ? Bp : m - dlt;  // pairs (PAIR) or elements (SHIFT)
+        const uint64_t t0 = uint64_t(qt) * tile;
+        const uint64_t t1 = t0 + tile < work ? t0 + tile : work;
+        const uint64_t L = t1 - t0;
+        if (pair) {
+            it.nmoves = 2;
+            it.mv[0] = Move{pr(t0, L), pr(Bp + t0, L), L};      // X'[t] -> Bp + t
+            it.mv[1] = Move{pr(m - Bp + t0, L), pr(t0, L), L};  // Y'[t] -> t
+        } else {
+            it.nmoves = 1;
+            it.mv[0] = Move{pr(dlt + t0, L), pr(t0, L), L};     // Y'[t] -> t
+        }
+        // writes into the stash region wait for its holders; writes over the second
+        // block at offset t - dlt wait for the tiles that read it
+        if (t0 < dlt) {
+            it.dp.lo0 = fb + uint32_t(t0 / prm.cap);
+            it.dp.hi0 = fb + uint32_t(((t1 < dlt ? t1 : dlt) - 1) / prm.cap);
+        }
+        if (t1 > dlt) {
+            const uint32_t qlo = uint32_t(((t0 > dlt ? t0 : dlt) - dlt) / tile);
+            const uint32_t qhi = uint32_t((t1 - 1 - dlt) / tile);
+            if (qlo < qt) {
+                it.dp.lo1 = fb + ph.holders + qlo;
+                it.dp.hi1 = fb + ph.holders + (qhi < qt ? qhi : qt - 1);
+            }
+        }
+    }
+    return true;
+}
+
+// Stage the item's source blocks: TMA bulk copies for the 16-byte-aligned bodies
+// (thread 0 arms the mbarrier with their byte count and issues them), plain loads for
+// the heads and tails (all threads; the values go straight to shared memory).
+// Shared-memory layout of a stage: two key slots, then two value slots.  A SINGLE
+// exchange instead spans both stages from the base: keys, then values.
+template <typename K, bool KV>
+__device__ __forceinline__ K *stage_keys(const Item &it, unsigned char *stage,
+                                         unsigned char *base) {
+    return reinterpret_cast<K *>(it.single ? base : stage);
+}
+template <typename K, bool KV>
+__device__ __forceinline__ uint32_t *stage_vals(const Item &it, unsigned char *stage,
+                                                unsigned char *base) {
+    using C = XCfg<K, KV>;
+    return reinterpret_cast<uint32_t *>(
+        it.single ? base + (size_t(C::kSingleCap + C::kKPad) * sizeof(K) + 15) / 16 * 16
+                  : stage + C::kStageKBytes);
+}
+
+template <typename K, bool KV>
+__device__ __forceinline__ void stage_load(const Item &it, const K *buf, const uint32_t *vals,
+                                           unsigned char *stage, unsigned char *base,
+                                           uint64_t *bar) {
+    using C = XCfg<K, KV>;
+    K *sk = stage_keys<K, KV>(it, stage, base);
+    uint32_t *sv = stage_vals<K, KV>(it, stage, base);
     const uint32_t tid = threadIdx.x;
-    auto phys = [&](uint64_t x) -> uint64_t { return mirror ? m - 1 - x : x; };
-    constexpr int NE = 2 * PP;  // registers per thread
-    // zero-initialised: the fold below must read only defined values, or the compiler
-    // could drop it (and with it the wait for the loads)
-    K r[NE];
-    uint32_t rv[KV ? NE : 1];
-#pragma unroll
-    for (int k = 0; k < NE; ++k) {
-        r[k] = K(0);
-        if (KV) rv[KV ? k : 0] = 0u;
-    }
-    if (kind == XK_SHIFT) {
-#pragma unroll
-        for (int k = 0; k < NE; ++k) {
-            const uint64_t t = t0 + uint64_t(k) * THREADS + tid;
-            if (t < t1) {
-                const uint64_t p = phys(rd1 + t);
-                r[k] = __ldcg(base + p);
-                if (KV) rv[KV ? k : 0] = __ldcg(vbase + p);
-            }
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < PP; ++k) {
-            const uint64_t t = t0 + uint64_t(k) * THREADS + tid;
-            if (t < t1) {
-                const uint64_t p0 = phys(t), p1 = phys(rd1 + t);
-                r[2 * k] = __ldcg(base + p0);
-                r[2 * k + 1] = __ldcg(base + p1);
-                if (KV) {
-                    rv[KV ? 2 * k : 0] = __ldcg(vbase + p0);
-                    rv[KV ? 2 * k + 1 : 0] = __ldcg(vbase + p1);
-                }
-            }
-        }
-    }
-    // while the loads are in flight, thread 0 checks whether the dependencies are met
-    bool ready = true;
     if (tid == 0) {
-        if (dp.lo0 <= dp.hi0) ready = flags_ready(flags, dp.lo0, dp.hi0, tag);
-        if (ready && dp.lo1 <= dp.hi1) ready = flags_ready(flags, dp.lo1, dp.hi1, tag);
-    }
-    // A warp can reach a barrier with its loads still in flight: only reading the
-    // destination registers waits for them.  Every loaded value is folded into one
-    // word that is the operand of the barrier itself (a barrier reduction must have
-    // its operand), so each warp's loads have returned before it arrives and the
-    // "reads done" flag below is true.  (An operand of an empty asm would not do:
-    // the assembler drops computations that no instruction consumes.)
-    uint32_t fold = 0;
-#pragma unroll
-    for (int k = 0; k < NE; ++k) {
-        fold ^= key_bits_lo(r[k]);
-        if (KV) fold ^= rv[KV ? k : 0];
-    }
-    if (__syncthreads_or(fold == sh.magic)) sh.sink = fold;  // rarely taken, harmless
-    if (tid == 0) {
-        if (flags != nullptr) st_flag(const_cast<uint32_t *>(flags) + my_flag, tag);
-        if (!ready) {
-            bool ok = true;
-            if (dp.lo0 <= dp.hi0) ok = wait_flags(flags, dp.lo0, dp.hi0, tag);
-            if (ok && dp.lo1 <= dp.hi1) ok = wait_flags(flags, dp.lo1, dp.hi1, tag);
-            if (!ok) {
-                set_status(sb, IPM_ERR_TIMEOUT);
-                sh.abort = 1;
+        uint32_t tx = 0;
+        for (uint32_t i = 0; i < it.nmoves; ++i) {
+            const Geo<int(sizeof(K))> gk(buf + it.mv[i].src, uint32_t(it.mv[i].len));
+            tx += gk.body * uint32_t(sizeof(K));
+            if (KV) {
+                const Geo<4> gv(vals + it.mv[i].src, uint32_t(it.mv[i].len));
+                tx += gv.body * 4u;
             }
         }
+        mbar_arrive_expect_tx(bar, tx);
     }
-    if (!(dp.lo0 > dp.hi0 && dp.lo1 > dp.hi1)) {
-        __syncthreads();  // dependencies met (or abort) before any write
-        if (sh.abort) return;
-    }
-    if (kind == XK_SHIFT) {
-#pragma unroll
-        for (int k = 0; k < NE; ++k) {
-            const uint64_t t = t0 + uint64_t(k) * THREADS + tid;
-            if (t < t1) {
-                const uint64_t p = phys(t);
-                base[p] = r[k];
-                if (KV) vbase[p] = rv[KV ? k : 0];
-            }
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < PP; ++k) {
-            const uint64_t t = t0 + uint64_t(k) * THREADS + tid;
-            if (t < t1) {
-                const uint64_t p0 = phys(t), p1 = phys(wr1 + t);
-                base[p0] = r[2 * k + 1];
-                base[p1] = r[2 * k];
-                if (KV) {
-                    vbase[p0] = rv[KV ? 2 * k + 1 : 0];
-                    vbase[p1] = rv[KV ? 2 * k : 0];
-                }
-            }
+    for (uint32_t i = 0; i < it.nmoves; ++i) {
+        const Move &mv = it.mv[i];
+        const uint32_t len = uint32_t(mv.len);
+        const K *g = buf + mv.src;
+        const Geo<int(sizeof(K))> gk(g, len);
+        K *dk = sk + i * C::kSlotK + gk.off;
+        if (tid == 0 && gk.body)
+            bulk_load(dk + gk.head, g + gk.head, gk.body * uint32_t(sizeof(K)), bar);
+        for (uint32_t j = tid; j < gk.head; j += C::kThreads) dk[j] = __ldcg(g + j);
+        for (uint32_t j = gk.tail_start + tid; j < len; j += C::kThreads) dk[j] = __ldcg(g + j);
+        if (KV) {
+            const uint32_t *gv = vals + mv.src;
+            const Geo<4> gvv(gv, len);
+            uint32_t *dv = sv + i * C::kSlotV + gvv.off;
+            if (tid == 0 && gvv.body)
+                bulk_load(dv + gvv.head, gv + gvv.head, gvv.body * 4u, bar);
+            for (uint32_t j = tid; j < gvv.head; j += C::kThreads) dv[j] = __ldcg(gv + j);
+            for (uint32_t j = gvv.tail_start + tid; j < len; j += C::kThreads)
+                dv[j] = __ldcg(gv + j);
         }
     }
 }
 
-template <typename K, bool KV, int THREADS, int PP>
-__global__ void __launch_bounds__(THREADS, 2)
+// Write the staged blocks to their destinations (coalesced stores from shared memory).
+template <typename K, bool KV>
+__device__ __forceinline__ void stage_store(const Item &it, K *buf, uint32_t *vals,
+                                            unsigned char *stage, unsigned char *base) {
+    using C = XCfg<K, KV>;
+    const K *sk = stage_keys<K, KV>(it, stage, base);
+    const uint32_t *sv = stage_vals<K, KV>(it, stage, base);
+    const uint32_t tid = threadIdx.x;
+    if (it.single) {  // the whole exchange [X|Y] is staged; write it rotated by |X|
+        const Move &mv = it.mv[0];
+        const Geo<int(sizeof(K))> gk(buf + mv.src, uint32_t(mv.len));
+        const uint32_t m = uint32_t(it.single_m), a = uint32_t(it.single_a);
+        const K *k0 = sk + gk.off;
+        K *dst = buf + mv.dst;
+        for (uint32_t t = tid; t < m; t += C::kThreads) {
+            uint32_t src = t + a;
+            if (src >= m) src -= m;
+            dst[t] = k0[src];
+        }
+        if (KV) {
+            const Geo<4> gv(vals + mv.src, uint32_t(mv.len));
+            const uint32_t *v0 = sv + gv.off;
+            uint32_t *vd = vals + mv.dst;
+            for (uint32_t t = tid; t < m; t += C::kThreads) {
+                uint32_t src = t + a;
+                if (src >= m) src -= m;
+                vd[t] = v0[src];
+            }
+        }
+        return;
+    }
+    for (uint32_t i = 0; i < it.nmoves; ++i) {
+        const Move &mv = it.mv[i];
+        const uint32_t len = uint32_t(mv.len);
+        const Geo<int(sizeof(K))> gk(buf + mv.src, len);
+        const K *k0 = sk + i * C::kSlotK + gk.off;
+        K *dst = buf + mv.dst;
+        for (uint32_t j = tid; j < len; j += C::kThreads) dst[j] = k0[j];
+        if (KV) {
+            const Geo<4> gv(vals + mv.src, len);
+            const uint32_t *v0 = sv + i * C::kSlotV + gv.off;
+            uint32_t *vd = vals + mv.dst;
+            for (uint32_t j = tid; j < len; j += C::kThreads) vd[j] = v0[j];
+        }
+    }
+}
+
+// One level: items in ticket order.  Per item: stage its blocks (TMA), publish "reads
+// done" once the data has landed, wait for the flags its stores depend on, store.  The
+// next item's blocks are staged into the other stage while the current one completes,
+// unless the current item is a stash holder (it waits on later tickets, which must
+// stay available to other CTAs) or the next item must first wait for an LS step.
+template <typename K, bool KV>
+__global__ void __launch_bounds__(512, 1)
     exchange_level_kernel(K *__restrict__ buf, uint32_t *__restrict__ vals, uint64_t n,
                           const RotPlan *__restrict__ plans, const uint32_t *__restrict__ pf,
                           uint32_t nrot, uint32_t *__restrict__ flags,
                           uint32_t *__restrict__ join, uint32_t tag, uint32_t ctr_index,
                           StatusBlock *sb) {
-    using C = XCfg<K, KV, THREADS, PP>;
-    extern __shared__ __align__(16) unsigned char xsmem[];
-    K *stk = reinterpret_cast<K *>(xsmem);
-    uint32_t *stv = reinterpret_cast<uint32_t *>(xsmem + size_t(C::kCap) * sizeof(K));
+    using C = XCfg<K, KV>;
+    extern __shared__ __align__(128) unsigned char xsmem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(xsmem + 2 * C::kStageSize);
     __shared__ Shared sh;
     if (sb != nullptr && *((volatile unsigned int *)&sb->done)) return;
     const XParams prm = C::params();
@@ -398,196 +521,125 @@ __global__ void __launch_bounds__(THREADS, 2)
     const uint32_t total = pf[nrot];
     uint32_t *ctr = &sb->counters[ctr_index];
     if (tid == 0) {
-        sh.next = atomicAdd(ctr, 1u);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+        sh.ticket[0] = atomicAdd(ctr, 1u);
         sh.abort = 0;
-        sh.magic = tag * 0x9e3779b9u + blockIdx.x;
-        sh.sink = 0;
     }
     __syncthreads();
-    uint32_t rot = 0;  // search hint: a CTA's tickets only grow
-    for (;;) {
-        const uint32_t ticket = sh.next;
-        const int aborted = sh.abort;
-        __syncthreads();  // everyone has read the ticket before thread 0 replaces it
-        if (ticket >= total || aborted) break;
-        // ---- decode: the exchange r holding the ticket is the last one with
-        // pf[r] <= ticket.  Tickets of a CTA only grow, so the block probes the THREADS
-        // exchanges after the previous one in one coalesced round; a binary search
-        // covers longer jumps.
-        if (pf[rot + 1] <= ticket) {
-            const uint32_t cand = rot + 1 + tid;
-            const bool le = cand <= nrot && pf[cand] <= ticket;
-            const int cnt = __syncthreads_count(le);  // pf non-decreasing: a prefix
-            if (cnt < THREADS) {
-                rot = rot + uint32_t(cnt);
-            } else {
-                uint32_t lo = rot + THREADS, hi = nrot;
-                while (hi - lo > 1) {
-                    const uint32_t mid = (lo + hi) >> 1;
-                    if (pf[mid] <= ticket)
-                        lo = mid;
-                    else
-                        hi = mid;
-                }
-                rot = lo;
-            }
-        }
-        const uint32_t r = rot;
-        const uint32_t j = ticket - pf[r];
-        const RotPlan q = plans[r];
-        XPhase ph;
-        uint64_t s = q.s, a = q.a, b = q.b;
-        uint32_t before = 0;
-        bool found = false;
-        while (x_phase(prm, s, a, b, ph)) {
-            if (j < before + ph.items()) {
-                found = true;
-                break;
-            }
-            before += ph.items();
-            if (ph.final_phase) break;
-            x_after_step(ph, s, a, b);
-        }
-        const uint64_t m = ph.a + ph.b;
-        if (!found || ph.s > n || m > n - ph.s) {  // inconsistent plan or split table
-            if (tid == 0) set_status(sb, IPM_ERR_DEVICE);
-            break;
-        }
-        const uint32_t jj = j - before;
-        const bool holder = (ph.kind == XK_PAIR || ph.kind == XK_SHIFT) && jj < ph.holders;
-        uint32_t nxt = 0;
-        if (tid == 0 && !holder) nxt = atomicAdd(ctr, 1u);  // result used at the end
-        if (before > 0) {  // an earlier LS step of this exchange must be complete
-            if (tid == 0 && !wait_count(join + r, before)) {
-                set_status(sb, IPM_ERR_TIMEOUT);
-                sh.abort = 1;
-            }
-            __syncthreads();
-            if (sh.abort) break;
-        }
-        const uint32_t fb = pf[r] + before;  // flag of item 0 of this phase
-        K *base = buf + ph.s;
-        uint32_t *vbase = KV ? vals + ph.s : nullptr;
-        const Deps none{1, 0, 1, 0};
-
-        if (ph.kind == XK_SINGLE) {
-            copy_in<K, KV, THREADS>(stk, stv, base, vbase, 0u, m, 0, 0, m);
-            __syncthreads();
-            const uint32_t mm = uint32_t(m), aa = uint32_t(ph.a);
-            for (uint32_t t = tid; t < mm; t += THREADS) {
-                uint32_t src = t + aa;
-                if (src >= mm) src -= mm;
-                base[t] = stk[src];
-                if (KV) vbase[t] = stv[src];
-            }
-        } else if (ph.kind == XK_SWAP) {
-            const uint64_t mn = ph.a < ph.b ? ph.a : ph.b;
-            const uint64_t off2 = ph.a >= ph.b ? ph.a : ph.b;
-            const uint64_t t0 = uint64_t(jj) * C::kPairTile;
-            const uint64_t t1 = t0 + C::kPairTile < mn ? t0 + C::kPairTile : mn;
-            tile_move<K, KV, THREADS, PP>(base, vbase, XK_SWAP, 0u, m, t0, t1, off2, off2,
-                                          nullptr, 0, tag, none, sh, sb);
-        } else if (holder) {
-            // PAIR: stash = X'[Bp, Ap) -> X'2 lands at 2Bp; readers of the landing
-            //       slots: tiles covering offsets [Bp-e+u).
-            // SHIFT: stash = X'[0, sz) lands at rest; readers: tiles covering
-            //       offsets [rest-sz+u).
-            const bool pair = ph.kind == XK_PAIR;
-            const uint64_t Bp = ph.a < ph.b ? ph.a : ph.b;
-            const uint64_t dlt = ph.delta;
-            const uint64_t h0 = uint64_t(jj) * prm.cap;
-            const uint64_t h1 = h0 + prm.cap < dlt ? h0 + prm.cap : dlt;
-            const uint64_t src_off = pair ? Bp : 0;
-            const uint64_t dst_off = pair ? 2 * Bp : m - dlt;
-            const uint64_t rd_off = pair ? Bp - dlt : m - 2 * dlt;
-            const uint32_t tile = pair ? C::kPairTile : C::kShiftTile;
-            copy_in<K, KV, THREADS>(stk, stv, base, vbase, ph.mirror, m, src_off, h0, h1);
-            __syncthreads();
-            if (tid == 0) {
-                st_flag(flags + fb + jj, tag);
-                const uint32_t qlo = uint32_t((rd_off + h0) / tile);
-                const uint32_t qhi = uint32_t((rd_off + h1 - 1) / tile);
-                if (!wait_flags(flags + fb + ph.holders, qlo, qhi, tag)) {
+    uint32_t parity0 = 0, parity1 = 0;
+    uint32_t rot = 0;
+    int cs = 0;  // stage of the current item
+    Item cur;
+    bool cur_loaded = false;
+    uint32_t cur_t = sh.ticket[0];
+    if (cur_t < total && !decode_item(prm, cur_t, rot, pf, plans, nrot, n, cur)) {
+        if (tid == 0) set_status(sb, IPM_ERR_DEVICE);
+        return;
+    }
+    uint32_t it_no = 0;
+    bool cur_flag_done = false;  // thread 0: the current item's flag is published
+    while (cur_t < total) {
+        bool nxt_flag_done = false;
+        unsigned char *st_cur = xsmem + (cs ? C::kStageSize : 0);
+        unsigned char *st_nxt = xsmem + (cs ? 0 : C::kStageSize);
+        // ---- the current item's earlier LS steps must be complete before it loads
+        if (!cur_loaded) {
+            if (cur.before > 0) {
+                if (tid == 0 && !wait_count(join + cur.r, cur.before)) {
                     set_status(sb, IPM_ERR_TIMEOUT);
                     sh.abort = 1;
                 }
+                __syncthreads();
+                if (sh.abort) break;
             }
+            stage_load<K, KV>(cur, buf, vals, st_cur, xsmem, &bar[cs]);
+        }
+        // ---- reserve and decode the next ticket (alternating slots: no extra barrier).
+        // A stash holder reserves it only once it is done: it waits on later tickets of
+        // its own exchange, and one of them must never be parked behind it.
+        uint32_t nxt_t = total;
+        Item nxt;
+        bool nxt_loaded = false;
+        if (!cur.holder) {
+            if (tid == 0) sh.ticket[(it_no + 1) & 1] = atomicAdd(ctr, 1u);
             __syncthreads();
-            if (sh.abort) break;
-            copy_out<K, KV, THREADS>(stk, stv, base, vbase, ph.mirror, m, dst_off, h0, h1);
-        } else {
-            const bool pair = ph.kind == XK_PAIR;
-            const uint32_t qt = jj - ph.holders;
-            const uint64_t dlt = ph.delta;
-            const uint64_t Bp = ph.a < ph.b ? ph.a : ph.b;
-            const uint64_t tile = pair ? C::kPairTile : C::kShiftTile;
-            const uint64_t work = pair ? Bp : m - dlt;  // pairs (PAIR) or elements (SHIFT)
-            const uint64_t t0 = uint64_t(qt) * tile;
-            const uint64_t t1 = t0 + tile < work ? t0 + tile : work;
-            // Writes that land in the stash region wait for its holders; writes over
-            // the second block at offset t - dlt wait for the tiles that read it.
-            Deps dp{1, 0, 1, 0};
-            if (t0 < dlt) {
-                dp.lo0 = fb + uint32_t(t0 / prm.cap);
-                dp.hi0 = fb + uint32_t(((t1 < dlt ? t1 : dlt) - 1) / prm.cap);
+            nxt_t = sh.ticket[(it_no + 1) & 1];
+            if (nxt_t < total && !decode_item(prm, nxt_t, rot, pf, plans, nrot, n, nxt)) {
+                if (tid == 0) set_status(sb, IPM_ERR_DEVICE);
+                break;
             }
-            if (t1 > dlt) {
-                const uint32_t qlo = uint32_t(((t0 > dlt ? t0 : dlt) - dlt) / tile);
-                const uint32_t qhi = uint32_t((t1 - 1 - dlt) / tile);
-                if (qlo < qt) {
-                    dp.lo1 = fb + ph.holders + qlo;
-                    dp.hi1 = fb + ph.holders + (qhi < qt ? qhi : qt - 1);
-                }
+            // a SINGLE exchange needs both stages: it neither prefetches nor is prefetched
+            if (nxt_t < total && nxt.before == 0 && !nxt.single && !cur.single) {
+                stage_load<K, KV>(nxt, buf, vals, st_nxt, xsmem, &bar[cs ^ 1]);
+                nxt_loaded = true;
             }
-            if (pair)
-                tile_move<K, KV, THREADS, PP>(base, vbase, XK_PAIR, ph.mirror, m, t0, t1,
-                                              m - Bp, Bp, flags, fb + jj, tag, dp, sh, sb);
-            else
-                tile_move<K, KV, THREADS, PP>(base, vbase, XK_SHIFT, ph.mirror, m, t0, t1,
-                                              dlt, 0, flags, fb + jj, tag, dp, sh, sb);
-            if (sh.abort) break;
         }
-        // ---- item complete.  Only an LS step is waited for (by the next phase of its
-        // exchange): every thread makes its own writes visible device-wide before the
-        // barrier after which the step is counted.
-        if (!ph.final_phase) __threadfence();
-        __syncthreads();
+        // ---- current item: staged -> reads done -> dependencies -> stores
+        if (tid == 0 && !mbar_wait_bounded(&bar[cs], cs ? parity1 : parity0)) {
+            set_status(sb, IPM_ERR_TIMEOUT);
+            sh.abort = 1;
+        }
+        if (cs)
+            parity1 ^= 1u;
+        else
+            parity0 ^= 1u;
+        __syncthreads();  // bulk data landed; heads and tails are in shared memory
+        if (sh.abort) break;
         if (tid == 0) {
-            if (!ph.final_phase) atomicAdd(join + r, 1u);
-            if (holder) nxt = atomicAdd(ctr, 1u);
-            sh.next = nxt;
+            if (cur.flag && !cur_flag_done) st_flag(flags + cur.ticket, tag);
+            // The prefetched item's "reads done" is published as soon as its data has
+            // landed (its heads and tails were loaded before the barrier above), not
+            // when it becomes current: the tiles after it in the chain wait for it.
+            const uint32_t np = cs ? parity0 : parity1;
+            bool ok = wait_flag_range_poll(flags, cur.dp.lo0, cur.dp.hi0, tag, nxt_loaded,
+                                           nxt.flag, &bar[cs ^ 1], np, flags + nxt_t,
+                                           nxt_flag_done);
+            if (ok)
+                ok = wait_flag_range_poll(flags, cur.dp.lo1, cur.dp.hi1, tag, nxt_loaded,
+                                          nxt.flag, &bar[cs ^ 1], np, flags + nxt_t,
+                                          nxt_flag_done);
+            if (!ok) {
+                set_status(sb, IPM_ERR_TIMEOUT);
+                sh.abort = 1;
+            }
         }
         __syncthreads();
+        if (sh.abort) break;
+        stage_store<K, KV>(cur, buf, vals, st_cur, xsmem);
+        if (tid == 0 && nxt_loaded && nxt.flag && !nxt_flag_done &&
+            mbar_try_wait(&bar[cs ^ 1], cs ? parity0 : parity1)) {
+            st_flag(flags + nxt_t, tag);
+            nxt_flag_done = true;
+        }
+        if (!cur.final_phase) __threadfence();  // an LS step: writes visible device-wide
+        fence_proxy_async_smem();  // our reads of the stage precede the next bulk copy into it
+        __syncthreads();           // stage free again
+        if (tid == 0 && !cur.final_phase) atomicAdd(join + cur.r, 1u);
+        if (cur.holder) {  // now reserve the next ticket
+            if (tid == 0) sh.ticket[(it_no + 1) & 1] = atomicAdd(ctr, 1u);
+            __syncthreads();
+            nxt_t = sh.ticket[(it_no + 1) & 1];
+            if (nxt_t < total && !decode_item(prm, nxt_t, rot, pf, plans, nrot, n, nxt)) {
+                if (tid == 0) set_status(sb, IPM_ERR_DEVICE);
+                break;
+            }
+        }
+        cur = nxt;
+        cur_t = nxt_t;
+        cur_loaded = nxt_loaded;
+        cur_flag_done = nxt_flag_done;
+        cs ^= 1;
+        ++it_no;
     }
 }
-
-template <typename K, bool KV>
-struct XShape;
-template <>
-struct XShape<int32_t, false> { static constexpr int T = 256, PP = 16; };
-template <>
-struct XShape<uint32_t, false> { static constexpr int T = 256, PP = 16; };
-template <>
-struct XShape<float, false> { static constexpr int T = 256, PP = 16; };
-template <>
-struct XShape<uint64_t, false> { static constexpr int T = 256, PP = 8; };
-template <>
-struct XShape<int32_t, true> { static constexpr int T = 256, PP = 8; };
-template <>
-struct XShape<uint32_t, true> { static constexpr int T = 256, PP = 8; };
-template <>
-struct XShape<float, true> { static constexpr int T = 256, PP = 8; };
-template <>
-struct XShape<uint64_t, true> { static constexpr int T = 256, PP = 4; };
-
-template <typename E, bool KV>
-using XCfgOf = XCfg<E, KV, XShape<E, KV>::T, XShape<E, KV>::PP>;
 
 template <typename E, bool KV>
 ipm_status exchange_level_t(void *buf, uint32_t *vals, uint64_t n, uint32_t l,
                             XPlanArea pa, StatusBlock *sb, cudaStream_t stream) {
-    using C = XCfgOf<E, KV>;
-    auto kern = exchange_level_kernel<E, KV, XShape<E, KV>::T, XShape<E, KV>::PP>;
+    using C = XCfg<E, KV>;
+    auto kern = exchange_level_kernel<E, KV>;
     static int grid = 0;
     if (grid == 0) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -596,7 +648,7 @@ ipm_status exchange_level_t(void *buf, uint32_t *vals, uint64_t n, uint32_t l,
             return IPM_ERR_CUDA;
         }
         int per_sm = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, XShape<E, KV>::T,
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, C::kThreads,
                                                           C::kSmem) != cudaSuccess) {
             (void)cudaGetLastError();
             return IPM_ERR_CUDA;
@@ -607,9 +659,9 @@ ipm_status exchange_level_t(void *buf, uint32_t *vals, uint64_t n, uint32_t l,
     const uint64_t R = 1ull << l;
     const RotPlan *plans = reinterpret_cast<const RotPlan *>(pa.plans) + (R - 1);
     const uint32_t *pf = pa.item_pf + (R - 1) + l;
-    kern<<<grid, XShape<E, KV>::T, C::kSmem, stream>>>(
-        (E *)buf, vals, n, plans, pf, uint32_t(R), pa.flags, pa.join + (R - 1), l + 1,
-        kTicketCounter0 + l, sb);
+    kern<<<grid, C::kThreads, C::kSmem, stream>>>((E *)buf, vals, n, plans, pf, uint32_t(R),
+                                                  pa.flags, pa.join + (R - 1), l + 1,
+                                                  kTicketCounter0 + l, sb);
     return last_launch_status();
 }
 
@@ -620,12 +672,11 @@ XParams exchange_params(ipm_dtype key, bool with_values) {
     case IPM_INT32:
     case IPM_UINT32:
     case IPM_FLOAT32:
-        return with_values ? XCfgOf<int32_t, true>::params() : XCfgOf<int32_t, false>::params();
+        return with_values ? XCfg<int32_t, true>::params() : XCfg<int32_t, false>::params();
     case IPM_UINT64:
-        return with_values ? XCfgOf<uint64_t, true>::params()
-                           : XCfgOf<uint64_t, false>::params();
+        return with_values ? XCfg<uint64_t, true>::params() : XCfg<uint64_t, false>::params();
     }
-    return XParams{1, 2, 1, 1};
+    return XParams{1, 2, 1, 1, 1};
 }
 
 size_t xplan_area_bytes(uint32_t G, uint64_t n, ipm_dtype key, bool with_values) {

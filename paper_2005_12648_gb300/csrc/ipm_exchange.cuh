@@ -31,8 +31,9 @@ enum : uint32_t { XK_NONE = 0, XK_SWAP = 1, XK_SINGLE = 2, XK_PAIR = 3, XK_SHIFT
 struct XParams {
     uint32_t pair_tile;    // pairs per PAIR / SWAP tile
     uint32_t shift_tile;   // elements per SHIFT tile
-    uint32_t cap;          // stash / SINGLE capacity of one CTA, in elements
+    uint32_t cap;          // stash capacity of one CTA, in elements
     uint32_t max_holders;  // stash CTAs per exchange (must stay below the resident CTAs)
+    uint32_t single_cap;   // largest exchange one CTA stages whole (SINGLE)
 };
 
 // One phase of an exchange.  (s, a, b): the exchange [X|Y] the phase works on.
@@ -66,7 +67,7 @@ __host__ __device__ inline bool x_phase(const XParams &P, uint64_t s, uint64_t a
     ph.final_phase = true;
     const uint64_t mn = a < b ? a : b;
     const uint64_t e = a > b ? a - b : b - a;
-    if (m <= P.cap) {
+    if (m <= P.single_cap) {
         ph.kind = XK_SINGLE;
         ph.tiles = 0;
         return true;

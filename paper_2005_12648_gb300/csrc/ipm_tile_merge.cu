@@ -14,100 +14,11 @@
 // The kernel is persistent (one CTA per SM, grid-stride over pairs); a pair never
 // straddles two CTAs, so the in-place write-back touches only the CTA's own range.
 #include "ipm_internal.h"
+#include "ipm_tma.cuh"
 
 namespace ipm {
 
 namespace {
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Wait for the mbarrier phase with the given parity; false after kWaitLimitNs.
-__device__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    unsigned long long t0 = 0;
-    for (uint32_t it = 0;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 0) {
-            const unsigned long long now = globaltimer_ns();
-            if (t0 == 0)
-                t0 = now;
-            else if (now - t0 > kWaitLimitNs)
-                return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void bulk_load(void *smem_dst, const void *gsrc, uint32_t bytes,
-                                          uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-        "[%3];" ::"r"(smem_u32(smem_dst)),
-        "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void bulk_store(void *gdst, const void *smem_src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
-                 "r"(smem_u32(smem_src)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() {
-    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_read0() {
-    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-}
-__device__ __forceinline__ void bulk_wait_all0() {
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-}
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Split of a global range of `count` elements of size W into an unaligned head, a
-// 16-byte-aligned body and a tail.  The staged copy keeps the address's phase mod 16:
-// element j lives at smem[off + j].
-template <int W>
-struct Geo {
-    uint32_t off, head, body, tail_start;
-    __device__ Geo(const void *g, uint32_t count) {
-        const uint32_t mis = uint32_t(reinterpret_cast<uintptr_t>(g) & 15u);
-        off = mis / W;
-        uint32_t h = ((16u - mis) & 15u) / W;
-        head = h < count ? h : count;
-        body = ((count - head) * W / 16u) * 16u / W;
-        tail_start = head + body;
-    }
-};
 
 template <typename K, bool KV, int THREADS, int E>
 struct TileShape {
