@@ -270,23 +270,25 @@ __device__ bool wait_flag_range_poll(const uint32_t *flags, uint32_t lo, uint32_
 __device__ __forceinline__ bool decode_item(const XParams &prm, uint32_t t, uint32_t &rot_hint,
                                             const uint32_t *pf, const RotPlan *plans,
                                             uint32_t nrot, uint64_t n, Item &it) {
-    // the exchange holding t is the last one with pf[r] <= t; a CTA's tickets only
-    // grow, so gallop forward from the previous one
+    // the exchange holding t is the last one with pf[r] <= t.  A CTA's tickets only
+    // grow: the block probes the 512 exchanges after the previous one in one coalesced
+    // round (pf is non-decreasing, so the hits form a prefix); longer jumps bisect.
     if (pf[rot_hint + 1] <= t) {
-        uint32_t lo = rot_hint + 1, step = 1;
-        while (lo + step < nrot && pf[lo + step] <= t) {
-            lo += step;
-            step <<= 1;
+        const uint32_t cand = rot_hint + 1 + threadIdx.x;
+        const int cnt = __syncthreads_count(cand <= nrot && pf[cand] <= t);
+        if (cnt < int(blockDim.x)) {
+            rot_hint += uint32_t(cnt);
+        } else {
+            uint32_t lo = rot_hint + blockDim.x, hi = nrot;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (pf[mid] <= t)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            rot_hint = lo;
         }
-        uint32_t hi = lo + step < nrot ? lo + step : nrot;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (pf[mid] <= t)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        rot_hint = lo;
     }
     const uint32_t r = rot_hint;
     const uint32_t j = t - pf[r];
@@ -390,9 +392,6 @@ __device__ __forceinline__ bool decode_item(const XParams &prm, uint32_t t, uint
     return true;
 }
 
-// Stage the item's source blocks: TMA bulk copies for the 16-byte-aligned bodies
-// (thread 0 arms the mbarrier with their byte count and issues them), plain loads for
-// the heads and tails (all threads; the values go straight to shared memory).
 // Shared-memory layout of a stage: two key slots, then two value slots.  A SINGLE
 // exchange instead spans both stages from the base: keys, then values.
 template <typename K, bool KV>
@@ -409,14 +408,29 @@ __device__ __forceinline__ uint32_t *stage_vals(const Item &it, unsigned char *s
                   : stage + C::kStageKBytes);
 }
 
+// Unaligned head/tail elements of a staged item, loaded into registers by threads
+// 0..31 (keys) and 32..63 (values) and written to shared memory only later
+// (flush_pending), so their load latency does not stall the CTA.  A thread holds at most
+// one element per stage.
+template <typename K>
+struct Pending {
+    K key;
+    uint32_t val;
+    uint32_t slot;  // element index from the shared-memory base, or ~0u if none
+};
+
+// Stage the item's source blocks: TMA bulk copies for the 16-byte-aligned bodies
+// (thread 0 arms the mbarrier with their byte count and issues them); the heads and
+// tails (under 16 bytes per end) go to `pd` and reach shared memory in flush_pending.
 template <typename K, bool KV>
 __device__ __forceinline__ void stage_load(const Item &it, const K *buf, const uint32_t *vals,
                                            unsigned char *stage, unsigned char *base,
-                                           uint64_t *bar) {
+                                           uint64_t *bar, Pending<K> &pd) {
     using C = XCfg<K, KV>;
     K *sk = stage_keys<K, KV>(it, stage, base);
     uint32_t *sv = stage_vals<K, KV>(it, stage, base);
     const uint32_t tid = threadIdx.x;
+    pd.slot = ~0u;
     if (tid == 0) {
         uint32_t tx = 0;
         for (uint32_t i = 0; i < it.nmoves; ++i) {
@@ -429,27 +443,82 @@ __device__ __forceinline__ void stage_load(const Item &it, const K *buf, const u
         }
         mbar_arrive_expect_tx(bar, tx);
     }
+    const uint32_t kofs = uint32_t((reinterpret_cast<unsigned char *>(sk) - base) / sizeof(K));
+    const uint32_t vofs = uint32_t((reinterpret_cast<unsigned char *>(sv) - base) / 4);
     for (uint32_t i = 0; i < it.nmoves; ++i) {
         const Move &mv = it.mv[i];
         const uint32_t len = uint32_t(mv.len);
         const K *g = buf + mv.src;
         const Geo<int(sizeof(K))> gk(g, len);
-        K *dk = sk + i * C::kSlotK + gk.off;
         if (tid == 0 && gk.body)
-            bulk_load(dk + gk.head, g + gk.head, gk.body * uint32_t(sizeof(K)), bar);
-        for (uint32_t j = tid; j < gk.head; j += C::kThreads) dk[j] = __ldcg(g + j);
-        for (uint32_t j = gk.tail_start + tid; j < len; j += C::kThreads) dk[j] = __ldcg(g + j);
+            bulk_load(sk + i * C::kSlotK + gk.off + gk.head, g + gk.head,
+                      gk.body * uint32_t(sizeof(K)), bar);
+        // move i: lanes 8i .. 8i+7 of warp 0; lane e < 4 takes head element e, lane
+        // e >= 4 tail element e-4 (at most 3 of each for 4-byte keys, 1 for 8-byte)
+        if (tid >= 8 * i && tid < 8 * i + 8) {
+            const uint32_t e = tid - 8 * i;
+            const uint32_t ntail = len - gk.tail_start;
+            uint32_t j = ~0u;
+            if (e < 4 && e < gk.head)
+                j = e;
+            else if (e >= 4 && e - 4 < ntail)
+                j = gk.tail_start + (e - 4);
+            if (j != ~0u) {
+                pd.key = __ldcg(g + j);
+                pd.slot = kofs + i * C::kSlotK + gk.off + j;
+            }
+        }
         if (KV) {
             const uint32_t *gv = vals + mv.src;
             const Geo<4> gvv(gv, len);
-            uint32_t *dv = sv + i * C::kSlotV + gvv.off;
             if (tid == 0 && gvv.body)
-                bulk_load(dv + gvv.head, gv + gvv.head, gvv.body * 4u, bar);
-            for (uint32_t j = tid; j < gvv.head; j += C::kThreads) dv[j] = __ldcg(gv + j);
-            for (uint32_t j = gvv.tail_start + tid; j < len; j += C::kThreads)
-                dv[j] = __ldcg(gv + j);
+                bulk_load(sv + i * C::kSlotV + gvv.off + gvv.head, gv + gvv.head, gvv.body * 4u,
+                          bar);
+            if (tid >= 32 + 8 * i && tid < 40 + 8 * i) {
+                const uint32_t e = tid - 32 - 8 * i;
+                const uint32_t ntail = len - gvv.tail_start;
+                uint32_t j = ~0u;
+                if (e < 4 && e < gvv.head)
+                    j = e;
+                else if (e >= 4 && e - 4 < ntail)
+                    j = gvv.tail_start + (e - 4);
+                if (j != ~0u) {
+                    pd.val = __ldcg(gv + j);
+                    pd.slot = vofs + i * C::kSlotV + gvv.off + j;
+                }
+            }
         }
     }
+}
+
+// Write a pending head/tail element to shared memory (keys from threads 0..31, values
+// from threads 32..63).  The caller's next barrier makes it visible to the CTA.
+template <typename K>
+__device__ __forceinline__ void flush_pending(Pending<K> &pd, unsigned char *base) {
+    if (pd.slot != ~0u) {
+        if (threadIdx.x < 32)
+            reinterpret_cast<K *>(base)[pd.slot] = pd.key;
+        else
+            reinterpret_cast<uint32_t *>(base)[pd.slot] = pd.val;
+        pd.slot = ~0u;
+    }
+}
+
+// dst[0, len) = src[0, len) (src in shared memory): 8 independent shared loads per
+// thread ahead of their 8 coalesced global stores, so the loop is not latency-bound.
+template <typename T, int THREADS>
+__device__ __forceinline__ void copy_out_unrolled(const T *src, T *dst, uint32_t len) {
+    constexpr uint32_t U = 8;
+    const uint32_t tid = threadIdx.x;
+    uint32_t j0 = 0;
+    for (; j0 + U * THREADS <= len; j0 += U * THREADS) {
+        T v[U];
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) v[u] = src[j0 + u * THREADS + tid];
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) dst[j0 + u * THREADS + tid] = v[u];
+    }
+    for (uint32_t j = j0 + tid; j < len; j += THREADS) dst[j] = src[j];
 }
 
 // Write the staged blocks to their destinations (coalesced stores from shared memory).
@@ -487,14 +556,11 @@ __device__ __forceinline__ void stage_store(const Item &it, K *buf, uint32_t *va
         const Move &mv = it.mv[i];
         const uint32_t len = uint32_t(mv.len);
         const Geo<int(sizeof(K))> gk(buf + mv.src, len);
-        const K *k0 = sk + i * C::kSlotK + gk.off;
-        K *dst = buf + mv.dst;
-        for (uint32_t j = tid; j < len; j += C::kThreads) dst[j] = k0[j];
+        copy_out_unrolled<K, C::kThreads>(sk + i * C::kSlotK + gk.off, buf + mv.dst, len);
         if (KV) {
             const Geo<4> gv(vals + mv.src, len);
-            const uint32_t *v0 = sv + i * C::kSlotV + gv.off;
-            uint32_t *vd = vals + mv.dst;
-            for (uint32_t j = tid; j < len; j += C::kThreads) vd[j] = v0[j];
+            copy_out_unrolled<uint32_t, C::kThreads>(sv + i * C::kSlotV + gv.off, vals + mv.dst,
+                                                     len);
         }
     }
 }
@@ -540,6 +606,9 @@ __global__ void __launch_bounds__(512, 1)
     }
     uint32_t it_no = 0;
     bool cur_flag_done = false;  // thread 0: the current item's flag is published
+    Pending<K> pd_cur, pd_nxt;   // head/tail elements staged by this thread
+    pd_cur.slot = ~0u;
+    pd_nxt.slot = ~0u;
     while (cur_t < total) {
         bool nxt_flag_done = false;
         unsigned char *st_cur = xsmem + (cs ? C::kStageSize : 0);
@@ -554,7 +623,7 @@ __global__ void __launch_bounds__(512, 1)
                 __syncthreads();
                 if (sh.abort) break;
             }
-            stage_load<K, KV>(cur, buf, vals, st_cur, xsmem, &bar[cs]);
+            stage_load<K, KV>(cur, buf, vals, st_cur, xsmem, &bar[cs], pd_cur);
         }
         // ---- reserve and decode the next ticket (alternating slots: no extra barrier).
         // A stash holder reserves it only once it is done: it waits on later tickets of
@@ -572,7 +641,7 @@ __global__ void __launch_bounds__(512, 1)
             }
             // a SINGLE exchange needs both stages: it neither prefetches nor is prefetched
             if (nxt_t < total && nxt.before == 0 && !nxt.single && !cur.single) {
-                stage_load<K, KV>(nxt, buf, vals, st_nxt, xsmem, &bar[cs ^ 1]);
+                stage_load<K, KV>(nxt, buf, vals, st_nxt, xsmem, &bar[cs ^ 1], pd_nxt);
                 nxt_loaded = true;
             }
         }
@@ -585,6 +654,8 @@ __global__ void __launch_bounds__(512, 1)
             parity1 ^= 1u;
         else
             parity0 ^= 1u;
+        flush_pending<K>(pd_cur, xsmem);
+        flush_pending<K>(pd_nxt, xsmem);  // the next item's reads are over once it lands
         __syncthreads();  // bulk data landed; heads and tails are in shared memory
         if (sh.abort) break;
         if (tid == 0) {
@@ -630,6 +701,8 @@ __global__ void __launch_bounds__(512, 1)
         cur_t = nxt_t;
         cur_loaded = nxt_loaded;
         cur_flag_done = nxt_flag_done;
+        pd_cur = pd_nxt;
+        pd_nxt.slot = ~0u;
         cs ^= 1;
         ++it_no;
     }
