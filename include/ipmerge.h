@@ -167,6 +167,84 @@ ipm_status ipm_rotate(void *d_ptr, uint64_t len_x, uint64_t len_y, uint32_t elem
 ipm_status ipm_read_exchange_bytes(const void *d_ws, ipm_stream_t stream, uint64_t *out);
 
 /*
+ * Batched segmented merge: many independent in-place merges in one call.
+ * Segment t of the table is the problem of Sec. 1 on its own slice of the buffer:
+ * A = d_buf[offset, offset + len_a) and B = d_buf[offset + len_a, offset + len_a +
+ * len_b), both sorted, merged stably in place.  Offsets and lengths count elements.
+ */
+typedef struct {
+    uint64_t offset;
+    uint64_t len_a;
+    uint64_t len_b;
+} ipm_segment;
+
+/*
+ * Launch options of ipm_merge_batched (a NULL options pointer = all zero):
+ *   tile         0 = library default (2), 1 = wide tile (the plain merge's tile, one
+ *                CTA per SM), 2 = narrow tile (half of it, two CTAs per SM),
+ *                3 = quarter tile (four CTAs per SM);
+ *   ctas_per_sm  0 = as many as fit, else at most this many resident CTAs per SM;
+ *   order        0 = work queue in segment-size order, largest first; 1 = table order;
+ *   reserved     must be 0.
+ * Every option changes only the speed, never the result.
+ */
+typedef struct {
+    uint32_t tile;
+    uint32_t ctas_per_sm;
+    uint32_t order;
+    uint32_t reserved;
+} ipm_batched_options;
+
+/*
+ * Workspace bytes of ipm_merge_batched for a buffer of buf_len elements, a table of
+ * nseg segments, this dtype, payload choice and options: O(nseg + buf_len / tile) (the
+ * queue and the split tables of the segments longer than one tile).
+ */
+ipm_status ipm_merge_batched_workspace_bytes(uint64_t buf_len, uint32_t nseg,
+                                            ipm_dtype key_dtype, int with_values,
+                                            const ipm_batched_options *opt, size_t *bytes);
+
+/*
+ * Longest segment (len_a + len_b, elements) ipm_merge_batched accepts for this dtype,
+ * payload choice and options: 512 tiles of the chosen tile size.  Longer segments are skipped on the device
+ * (status IPM_ERR_INVALID_ARG); merge them with ipm_merge_inplace instead.
+ */
+ipm_status ipm_merge_batched_max_segment(ipm_dtype key_dtype, int with_values,
+                                         const ipm_batched_options *opt, uint64_t *elems);
+
+/*
+ * Merge every segment of d_segs (nseg entries, device memory) in place.
+ *   d_buf     device keys, buf_len elements, aligned to the key size.
+ *   d_vals    NULL, or a uint32 payload array of buf_len elements moved with the keys
+ *             (val_dtype IPM_UINT32; ignored when d_vals is NULL).
+ *   d_segs    device array of nseg ipm_segment, 8-byte aligned; the segments must not
+ *             overlap (overlapping segments give an unspecified result, but every
+ *             access stays inside [0, buf_len)).
+ *   d_ws      workspace of ipm_merge_batched_workspace_bytes(buf_len, nseg, ...) bytes
+ *             (same dtype, payload choice and options), 256-byte aligned.
+ * Every segment is handled by one CTA at a time: the early exit of Alg. 2/3, then (when
+ * it is longer than one tile) its exact splits and its sRecPar exchange levels
+ * (Alg. 3, Sec. 3.4) in a first persistent launch, and its pair merges in a second;
+ * a segment that fits one tile is merged directly.  CTAs take segments from atomic
+ * work queues.  A segment that leaves the buffer or is longer than
+ * ipm_merge_batched_max_segment is left untouched and the device status becomes
+ * IPM_ERR_INVALID_ARG (ipm_read_device_status).  The call launches three kernels
+ * (queue preparation, levels, merge), performs no host synchronisation and no
+ * allocation, so it can be captured in a CUDA graph.
+ */
+ipm_status ipm_merge_batched(void *d_buf, void *d_vals, uint64_t buf_len,
+                             const ipm_segment *d_segs, uint32_t nseg, ipm_dtype key_dtype,
+                             ipm_dtype val_dtype, const ipm_batched_options *opt,
+                             void *d_ws, size_t ws_bytes, ipm_stream_t stream);
+
+/*
+ * Algorithmic bytes the pair merges of the last batched call that used this workspace
+ * moved: 2 bytes-per-element for every element of a segment that was merged (segments
+ * that took the early exit move nothing).  Synchronises `stream`.
+ */
+ipm_status ipm_read_merge_bytes(const void *d_ws, ipm_stream_t stream, uint64_t *out);
+
+/*
  * ipm_merge_inplace for callers that cannot allocate device memory.  The paper has no
  * counterpart: this is a deployment variant of the same merge.
  * Some callers cannot call cudaMalloc (another framework holds nearly all device
@@ -192,13 +270,16 @@ ipm_status ipm_merge_inplace_noalloc(void *d_buf, uint64_t len_a, uint64_t len_b
  * Optional per-phase timing (for benchmarks).  When enabled on a host thread, the
  * merge entry points called from that thread record a CUDA event pair on their stream
  * around each launch group: phase 0 = early exit + split, 1 = exchange plan,
- * 2 = exchange levels (one launch per level), 3 = pair merge.  ipm_timing_read waits for the recorded events,
- * adds their elapsed times and kernel-launch counts into *out and forgets them.
- * Timing adds two event records per group and changes no kernel.
+ * 2 = exchange levels (one launch per level), 3 = pair merge, 4 = batched merge
+ * (queue order + persistent kernel), 5 = split-model training, 6 = learned splits.
+ * ipm_timing_read waits for the recorded events, adds their elapsed times and
+ * kernel-launch counts into *out and forgets them.  Timing adds two event records per
+ * group and changes no kernel.
  */
+#define IPM_TIMING_PHASES 8
 typedef struct {
-    double ms[4];
-    uint32_t launches[4];
+    double ms[IPM_TIMING_PHASES];
+    uint32_t launches[IPM_TIMING_PHASES];
 } ipm_timing;
 
 ipm_status ipm_timing_enable(int enable);

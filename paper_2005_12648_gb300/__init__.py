@@ -27,6 +27,8 @@ __all__ = [
     "ipm_read_exchange_bytes",
     "ipm_timing_enable", "ipm_timing_read", "IpmTiming", "ipm_merge_inplace_noalloc",
     "workspace", "merge_inplace", "merge_inplace_kv",
+    "IpmBatchedOptions", "ipm_merge_batched_workspace_bytes", "ipm_merge_batched_max_segment",
+    "ipm_merge_batched", "ipm_read_merge_bytes", "segment_table", "merge_batched",
 ]
 
 DTYPES = {"int32": 0, "uint32": 1, "uint64": 2, "float32": 3}
@@ -66,14 +68,23 @@ _SIGS = {
     "ipm_merge_inplace_noalloc": (_i, [_vp, _u64, _u64, _i, _vp]),
     "ipm_timing_enable": (_i, [_i]),
     "ipm_timing_read": (_i, [ctypes.c_void_p]),
+    "ipm_merge_batched_workspace_bytes": (_i, [_u64, _u32, _i, _i, _vp, ctypes.POINTER(_sz)]),
+    "ipm_merge_batched_max_segment": (_i, [_i, _i, _vp, ctypes.POINTER(_u64)]),
+    "ipm_merge_batched": (_i, [_vp, _vp, _u64, _vp, _u32, _i, _i, _vp, _vp, _sz, _vp]),
+    "ipm_read_merge_bytes": (_i, [_vp, _vp, ctypes.POINTER(_u64)]),
 }
+
+
+TIMING_PHASES = 8
 
 
 class IpmTiming(ctypes.Structure):
     """Mirror of ipm_timing: per-phase milliseconds and launch counts."""
-    _fields_ = [("ms", ctypes.c_double * 4), ("launches", ctypes.c_uint32 * 4)]
+    _fields_ = [("ms", ctypes.c_double * TIMING_PHASES),
+                ("launches", ctypes.c_uint32 * TIMING_PHASES)]
 
-    PHASES = ("split", "plan", "exchange", "merge")
+    PHASES = ("split", "plan", "exchange", "merge", "batched", "train", "learned_split",
+              "reserved")
 
     def as_dict(self):
         return {p: {"ms": self.ms[i], "launches": int(self.launches[i])}
@@ -257,6 +268,66 @@ def ipm_timing_read(into: "IpmTiming | None" = None) -> IpmTiming:
     return t
 
 
+class IpmBatchedOptions(ctypes.Structure):
+    """Mirror of ipm_batched_options (tile 0 = default, 1 wide, 2 narrow, 3 quarter;
+    order 0 = largest segment first, 1 = table order; ctas_per_sm 0 = as many as fit)."""
+    _fields_ = [("tile", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("order", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {"tile": int(self.tile), "ctas_per_sm": int(self.ctas_per_sm),
+                "order": int(self.order)}
+
+
+def _opts(options) -> "IpmBatchedOptions | None":
+    if options is None or isinstance(options, IpmBatchedOptions):
+        return options
+    return IpmBatchedOptions(int(options.get("tile", 0)), int(options.get("ctas_per_sm", 0)),
+                             int(options.get("order", 0)), 0)
+
+
+def ipm_merge_batched_workspace_bytes(buf_len: int, nseg: int, key_dtype,
+                                      with_values: bool = False, options=None) -> int:
+    out = _sz(0)
+    o = _opts(options)
+    _check(load().ipm_merge_batched_workspace_bytes(buf_len, nseg, _dt(key_dtype),
+                                                    int(bool(with_values)),
+                                                    ctypes.byref(o) if o is not None else None,
+                                                    ctypes.byref(out)),
+           "ipm_merge_batched_workspace_bytes")
+    return int(out.value)
+
+
+def ipm_merge_batched_max_segment(key_dtype, with_values: bool = False, options=None) -> int:
+    out = _u64(0)
+    o = _opts(options)
+    _check(load().ipm_merge_batched_max_segment(_dt(key_dtype), int(bool(with_values)),
+                                                ctypes.byref(o) if o is not None else None,
+                                                ctypes.byref(out)),
+           "ipm_merge_batched_max_segment")
+    return int(out.value)
+
+
+def ipm_merge_batched(buf, vals, buf_len: int, segs, nseg: int, key_dtype, ws,
+                      val_dtype="uint32", options=None, ws_bytes: int | None = None,
+                      stream=None) -> None:
+    """segs: device array of nseg {offset, len_a, len_b} uint64 triples (e.g. an
+    int64 tensor of shape [nseg, 3])."""
+    wsb = _nbytes(ws) if ws_bytes is None else ws_bytes
+    o = _opts(options)
+    _check(load().ipm_merge_batched(_ptr(buf), _ptr(vals), buf_len, _ptr(segs), nseg,
+                                    _dt(key_dtype), _dt(val_dtype),
+                                    ctypes.byref(o) if o is not None else None, _ptr(ws), wsb,
+                                    _stream(stream)), "ipm_merge_batched")
+
+
+def ipm_read_merge_bytes(ws, stream=None) -> int:
+    out = _u64(0)
+    _check(load().ipm_read_merge_bytes(_ptr(ws), _stream(stream), ctypes.byref(out)),
+           "ipm_read_merge_bytes")
+    return int(out.value)
+
+
 # ------------------------------------------------------------------ conveniences
 
 def workspace(nbytes: int, device=None):
@@ -280,4 +351,23 @@ def merge_inplace_kv(keys, vals, len_a: int, len_b: int, key_dtype, log2_pairs: 
                    keys.device)
     ipm_merge_inplace_kv(keys, vals, len_a, len_b, key_dtype, ws, log2_pairs=log2_pairs,
                          stream=stream)
+    return ws
+
+
+def segment_table(offsets, len_a, len_b, device=None):
+    """A device segment table (int64 [nseg, 3]: offset, len_a, len_b) from host lists."""
+    import torch
+    t = torch.stack([torch.as_tensor(offsets, dtype=torch.int64),
+                     torch.as_tensor(len_a, dtype=torch.int64),
+                     torch.as_tensor(len_b, dtype=torch.int64)], dim=1).contiguous()
+    return t.to(device if device is not None else "cuda")
+
+
+def merge_batched(buf, segs, key_dtype, vals=None, options=None, stream=None):
+    """Allocate the workspace and run ipm_merge_batched over a device segment table."""
+    nseg = int(segs.shape[0])
+    ws = workspace(ipm_merge_batched_workspace_bytes(buf.numel(), nseg, key_dtype,
+                                                     vals is not None, options), buf.device)
+    ipm_merge_batched(buf, vals, buf.numel(), segs, nseg, key_dtype, ws, options=options,
+                      stream=stream)
     return ws

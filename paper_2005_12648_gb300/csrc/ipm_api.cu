@@ -111,6 +111,19 @@ ipm_status check_merge_args(uint64_t la, uint64_t lb, ipm_dtype key, bool kv,
     return IPM_OK;
 }
 
+// Kernel variant of a batched options struct (NULL = defaults): 0 wide, 1 narrow,
+// 2 quarter tile.
+constexpr uint32_t kDefaultBatchedVariant = 1;
+
+ipm_status batched_variant(const ipm_batched_options *opt, uint32_t *variant) {
+    *variant = kDefaultBatchedVariant;
+    if (opt == nullptr) return IPM_OK;
+    if (opt->tile > 3 || opt->order > 1 || opt->reserved != 0 || opt->ctas_per_sm > 64)
+        return IPM_ERR_INVALID_ARG;
+    *variant = opt->tile == 0 ? kDefaultBatchedVariant : opt->tile - 1;
+    return IPM_OK;
+}
+
 struct MergeLayout {
     size_t split_off, plan_off, total;
 };
@@ -338,6 +351,66 @@ ipm_status ipm_read_exchange_bytes(const void *d_ws, ipm_stream_t stream, uint64
     IPM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     *out = uint64_t(v);
     return IPM_OK;
+}
+
+ipm_status ipm_read_merge_bytes(const void *d_ws, ipm_stream_t stream, uint64_t *out) {
+    if (d_ws == nullptr || out == nullptr) return IPM_ERR_INVALID_ARG;
+    unsigned long long v = 0;
+    IPM_CUDA_TRY(cudaMemcpyAsync(&v, static_cast<const char *>(d_ws) +
+                                         offsetof(StatusBlock, merge_bytes),
+                                 sizeof(v), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    IPM_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    *out = uint64_t(v);
+    return IPM_OK;
+}
+
+ipm_status ipm_merge_batched_workspace_bytes(uint64_t buf_len, uint32_t nseg,
+                                            ipm_dtype key_dtype, int with_values,
+                                            const ipm_batched_options *opt, size_t *bytes) {
+    uint32_t variant = 0;
+    IPM_TRY(batched_variant(opt, &variant));
+    if (!valid_key(key_dtype)) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (bytes == nullptr || buf_len > (uint64_t(1) << 40)) return IPM_ERR_INVALID_ARG;
+    *bytes = batched_layout(buf_len, nseg, batched_tile(key_dtype, with_values != 0, variant))
+                 .total;
+    return IPM_OK;
+}
+
+ipm_status ipm_merge_batched_max_segment(ipm_dtype key_dtype, int with_values,
+                                         const ipm_batched_options *opt, uint64_t *elems) {
+    uint32_t variant = 0;
+    IPM_TRY(batched_variant(opt, &variant));
+    if (!valid_key(key_dtype)) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (elems == nullptr) return IPM_ERR_INVALID_ARG;
+    *elems = batched_max_segment(key_dtype, with_values != 0, variant);
+    return IPM_OK;
+}
+
+ipm_status ipm_merge_batched(void *d_buf, void *d_vals, uint64_t buf_len,
+                             const ipm_segment *d_segs, uint32_t nseg, ipm_dtype key_dtype,
+                             ipm_dtype val_dtype, const ipm_batched_options *opt,
+                             void *d_ws, size_t ws_bytes, ipm_stream_t stream) {
+    uint32_t variant = 0;
+    IPM_TRY(batched_variant(opt, &variant));
+    if (!valid_key(key_dtype)) return IPM_ERR_UNSUPPORTED_DTYPE;
+    const bool kv = d_vals != nullptr;
+    if (kv && val_dtype != IPM_UINT32) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (buf_len > (uint64_t(1) << 40)) return IPM_ERR_INVALID_ARG;
+    if (nseg > 0 && d_segs == nullptr) return IPM_ERR_INVALID_ARG;
+    if (buf_len > 0 && d_buf == nullptr) return IPM_ERR_INVALID_ARG;
+    if (d_ws == nullptr) return IPM_ERR_WORKSPACE;
+    const BatchedLayout L =
+        batched_layout(buf_len, nseg, batched_tile(key_dtype, kv, variant));
+    if (ws_bytes < L.total) return IPM_ERR_WORKSPACE;
+    if (!aligned(d_buf, size_t(dtype_bytes(key_dtype))) || (kv && !aligned(d_vals, 4)) ||
+        !aligned(d_segs, 8) || !aligned(d_ws, 256))
+        return IPM_ERR_ALIGNMENT;
+    cudaStream_t st = (cudaStream_t)stream;
+    const uint32_t by_size = (opt == nullptr || opt->order == 0) ? 1u : 0u;
+    const uint32_t per_sm = opt ? opt->ctas_per_sm : 0u;
+    PhaseScope ps(4, 3, st);
+    return launch_batched(d_buf, static_cast<uint32_t *>(d_vals), buf_len, key_dtype, d_segs,
+                          nseg, d_ws, L, by_size, variant, per_sm, st);
 }
 
 ipm_status ipm_timing_enable(int enable) {

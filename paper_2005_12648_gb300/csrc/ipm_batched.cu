@@ -1,0 +1,248 @@
+// Batched segmented merge: the queue-preparation kernel, the workspace layout and the
+// dispatch to the per-key-type kernels (ipm_batched.cuh, ipm_batched_<key>.cu).
+#include "ipm_batched.cuh"
+
+namespace ipm {
+
+ipm_status batched_launch_i32(void *, uint32_t *, uint64_t, batched::QueueArea, uint32_t,
+                              uint32_t, uint32_t, StatusBlock *, cudaStream_t);
+ipm_status batched_launch_u32(void *, uint32_t *, uint64_t, batched::QueueArea, uint32_t,
+                              uint32_t, uint32_t, StatusBlock *, cudaStream_t);
+ipm_status batched_launch_u64(void *, uint32_t *, uint64_t, batched::QueueArea, uint32_t,
+                              uint32_t, uint32_t, StatusBlock *, cudaStream_t);
+ipm_status batched_launch_f32(void *, uint32_t *, uint64_t, batched::QueueArea, uint32_t,
+                              uint32_t, uint32_t, StatusBlock *, cudaStream_t);
+
+namespace {
+
+using namespace batched;
+
+constexpr uint32_t kPrepThreads = 1024;
+constexpr uint32_t kOrderBuckets = 256;  // 4 per octave of the segment length
+
+// Bucket of a segment of n >= 1 elements: 4 * floor(log2 n) + the next two bits.
+__device__ __forceinline__ uint32_t size_bucket(uint64_t n) {
+    const uint32_t lg = 63u - uint32_t(__clzll(n));
+    const uint32_t frac = lg >= 2 ? uint32_t(n >> (lg - 2)) & 3u : uint32_t(n << (2 - lg)) & 3u;
+    return (lg << 2) | frac;
+}
+
+constexpr uint32_t kPrepBatch = 8;  // descriptors in flight per thread
+constexpr uint32_t kPrepWarps = kPrepThreads / 32;
+
+// Appends `q` to list[*ctr] for the active lanes: one atomic per warp.
+__device__ __forceinline__ void warp_append(uint32_t *ctr, uint32_t *list, uint32_t q,
+                                            bool active) {
+    const uint32_t act = __ballot_sync(0xffffffffu, active);
+    if (act == 0) return;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t leader = __ffs(act) - 1u;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(ctr, uint32_t(__popc(act)));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (active) list[base + uint32_t(__popc(act & ((1u << lane) - 1u)))] = q;
+}
+
+// One CTA: resets the status block, writes the queue of descriptors (largest segment
+// first when by_size, else table order) and lists the multi-tile segments in queue
+// order; segments that leave the buffer or exceed the per-segment limit set
+// IPM_ERR_INVALID_ARG.  The size order is a counting sort over 256 length buckets
+// with one private histogram per warp (no contention between warps); every pass
+// loads kPrepBatch descriptors per thread before using any of them.
+__global__ void __launch_bounds__(kPrepThreads)
+    batched_prep_kernel(const ipm_segment *__restrict__ segs, uint32_t nseg, uint32_t by_size,
+                        uint64_t buf_len, uint64_t tile, uint64_t max_seg, QueueArea qa,
+                        StatusBlock *sb) {
+    __shared__ uint32_t hist[kPrepWarps][kOrderBuckets];  // per warp: count, then cursor
+    __shared__ uint32_t total[kOrderBuckets];
+    __shared__ uint32_t nmulti;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        sb->status = 0u;
+        sb->done = 0u;
+        sb->exchange_bytes = 0ull;
+        sb->merge_bytes = 0ull;
+        for (int q = 0; q < kNumCounters; ++q) sb->counters[q] = 0u;
+        nmulti = 0;
+    }
+    constexpr uint32_t kStride = kPrepThreads * kPrepBatch;
+    if (by_size) {
+        for (uint32_t q = tid; q < kPrepWarps * kOrderBuckets; q += kPrepThreads)
+            (&hist[0][0])[q] = 0u;
+        __syncthreads();
+        for (uint32_t t0 = 0; t0 < nseg; t0 += kStride) {
+            uint64_t n[kPrepBatch];
+#pragma unroll
+            for (uint32_t j = 0; j < kPrepBatch; ++j) {
+                const uint32_t t = t0 + j * kPrepThreads + tid;
+                n[j] = t < nseg ? segs[t].len_a + segs[t].len_b : 0;
+            }
+#pragma unroll
+            for (uint32_t j = 0; j < kPrepBatch; ++j)
+                if (t0 + j * kPrepThreads + tid < nseg)
+                    atomicAdd(&hist[warp][n[j] ? size_bucket(n[j]) : 0u], 1u);
+        }
+        __syncthreads();
+        // bucket totals, then their exclusive scan from the largest bucket down
+        for (uint32_t q = tid; q < kOrderBuckets; q += kPrepThreads) {
+            uint32_t sum = 0;
+            for (uint32_t w = 0; w < kPrepWarps; ++w) sum += hist[w][q];
+            total[q] = sum;
+        }
+        __syncthreads();
+        if (tid < 32) {
+            uint32_t carry = 0;
+            for (int base = int(kOrderBuckets) - 32; base >= 0; base -= 32) {
+                const uint32_t q = uint32_t(base) + 31u - tid;  // descending in the chunk
+                const uint32_t v = total[q];
+                uint32_t x = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (int(tid) >= o) x += y;
+                }
+                total[q] = carry + x - v;
+                carry += __shfl_sync(0xffffffffu, x, 31);
+            }
+        }
+        __syncthreads();
+        // per-warp cursors: bucket start + the counts of the lower warps
+        for (uint32_t q = tid; q < kOrderBuckets; q += kPrepThreads) {
+            uint32_t run = total[q];
+            for (uint32_t w = 0; w < kPrepWarps; ++w) {
+                const uint32_t c = hist[w][q];
+                hist[w][q] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+    }
+    // scatter into queue order (by_size) or copy (table order, listing the multi-tile
+    // segments on the way)
+    for (uint32_t t0 = 0; t0 < nseg; t0 += kStride) {
+        ipm_segment sg[kPrepBatch];
+#pragma unroll
+        for (uint32_t j = 0; j < kPrepBatch; ++j) {
+            const uint32_t t = t0 + j * kPrepThreads + tid;
+            if (t < nseg) sg[j] = segs[t];
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < kPrepBatch; ++j) {
+            const uint32_t t = t0 + j * kPrepThreads + tid;
+            uint32_t cls = kSegTrivial;
+            if (t < nseg) {
+                const uint64_t n = sg[j].len_a + sg[j].len_b;
+                const uint32_t q =
+                    by_size ? atomicAdd(&hist[warp][n ? size_bucket(n) : 0u], 1u) : t;
+                qa.queue[q] = sg[j];
+                cls = seg_class(sg[j], buf_len, tile, max_seg);
+                if (cls == kSegInvalid) set_status(sb, IPM_ERR_INVALID_ARG);  // untouched
+            }
+            if (!by_size) warp_append(&nmulti, qa.multi, t, cls == kSegMulti);
+        }
+    }
+    if (by_size) {
+        // list the multi-tile segments in queue order (largest first): they lead the
+        // queue, so it is read back only until a bucket entirely below the tile shows
+        __syncthreads();  // the queue is written (global writes of this CTA)
+        __shared__ uint32_t done;
+        if (tid == 0) done = 0;
+        __syncthreads();
+        const uint32_t first_multi_bucket = size_bucket(tile + 1);
+        for (uint32_t t0 = 0; t0 < nseg && !done; t0 += kStride) {
+            ipm_segment sg[kPrepBatch];
+#pragma unroll
+            for (uint32_t j = 0; j < kPrepBatch; ++j) {
+                const uint32_t q = t0 + j * kPrepThreads + tid;
+                if (q < nseg) sg[j] = qa.queue[q];
+            }
+            uint32_t below = 0;
+#pragma unroll
+            for (uint32_t j = 0; j < kPrepBatch; ++j) {
+                const uint32_t q = t0 + j * kPrepThreads + tid;
+                uint32_t cls = kSegTrivial;
+                if (q < nseg) {
+                    cls = seg_class(sg[j], buf_len, tile, max_seg);
+                    const uint64_t n = sg[j].len_a + sg[j].len_b;
+                    below |= (n == 0 || size_bucket(n) < first_multi_bucket) ? 1u : 0u;
+                }
+                warp_append(&nmulti, qa.multi, q, cls == kSegMulti);
+            }
+            // the queue is in descending bucket order: every segment after one whose
+            // bucket lies below the first multi-tile bucket fits one tile
+            if (__syncthreads_or(below) && tid == 0) done = 1;
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    if (tid == 0) sb->counters[kMultiCount] = nmulti;
+}
+
+}  // namespace
+
+uint64_t batched_tile(ipm_dtype key, bool with_values, uint32_t variant) {
+    switch (key) {
+    case IPM_INT32:
+    case IPM_UINT32:
+    case IPM_FLOAT32:
+        return with_values ? tile_t<int32_t, true>(variant) : tile_t<int32_t, false>(variant);
+    case IPM_UINT64:
+        return with_values ? tile_t<uint64_t, true>(variant)
+                           : tile_t<uint64_t, false>(variant);
+    }
+    return 0;
+}
+
+uint64_t batched_max_segment(ipm_dtype key, bool with_values, uint32_t variant) {
+    return uint64_t(kMaxPairs) * batched_tile(key, with_values, variant);
+}
+
+// Workspace layout: status block | queue | multi | soff | split pool.  The pool holds
+// every multi-tile segment's P + 1 splits; P < 2 n / tile, so for segments that do not
+// overlap 2 (buf_len / tile + 1) + nseg entries suffice.
+BatchedLayout batched_layout(uint64_t buf_len, uint32_t nseg, uint64_t tile) {
+    BatchedLayout L;
+    L.queue_off = kStatusBytes;
+    L.multi_off = L.queue_off + align_up(sizeof(ipm_segment) * size_t(nseg), 256);
+    L.soff_off = L.multi_off + align_up(sizeof(uint32_t) * size_t(nseg), 256);
+    L.pool_off = L.soff_off + align_up(sizeof(uint32_t) * size_t(nseg), 256);
+    L.pool_cap = 2 * (buf_len / tile + 1) + uint64_t(nseg);
+    L.total = L.pool_off + align_up(sizeof(uint64_t) * size_t(L.pool_cap), 256);
+    return L;
+}
+
+ipm_status launch_batched(void *buf, uint32_t *vals, uint64_t buf_len, ipm_dtype key,
+                          const ipm_segment *segs, uint32_t nseg, void *ws,
+                          const BatchedLayout &L, uint32_t by_size, uint32_t variant,
+                          uint32_t ctas_per_sm, cudaStream_t stream) {
+    char *w = static_cast<char *>(ws);
+    StatusBlock *sb = reinterpret_cast<StatusBlock *>(w);
+    QueueArea qa;
+    qa.queue = reinterpret_cast<ipm_segment *>(w + L.queue_off);
+    qa.multi = reinterpret_cast<uint32_t *>(w + L.multi_off);
+    qa.soff = reinterpret_cast<uint32_t *>(w + L.soff_off);
+    qa.pool = reinterpret_cast<uint64_t *>(w + L.pool_off);
+    qa.pool_cap = L.pool_cap;
+    const uint64_t tile = batched_tile(key, vals != nullptr, variant);
+    batched_prep_kernel<<<1, kPrepThreads, 0, stream>>>(
+        segs, nseg, by_size, buf_len, tile, batched_max_segment(key, vals != nullptr, variant),
+        qa, sb);
+    IPM_TRY(last_launch_status());
+    switch (key) {
+    case IPM_INT32:
+        return batched_launch_i32(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm, sb,
+                                  stream);
+    case IPM_UINT32:
+        return batched_launch_u32(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm, sb,
+                                  stream);
+    case IPM_UINT64:
+        return batched_launch_u64(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm, sb,
+                                  stream);
+    case IPM_FLOAT32:
+        return batched_launch_f32(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm, sb,
+                                  stream);
+    }
+    return IPM_ERR_UNSUPPORTED_DTYPE;
+}
+
+}  // namespace ipm

@@ -19,14 +19,18 @@ __device__ __forceinline__ bool key_le(K x, K y) { return x <= y; }
 //   status          device status (ipm_status), first error wins
 //   done            early-exit flag: nonzero when the runs are already in order
 //   exchange_bytes  algorithmic bytes of the exchange levels of the current call
+//   merge_bytes     algorithmic bytes of the pair merges (batched calls only)
 //   counters        per-call ticket counters of the persistent kernels
 // All of it is reset at the start of every call.
 // ---------------------------------------------------------------------------------
+constexpr int kNumCounters = 58;
+
 struct StatusBlock {
     unsigned int status;
     unsigned int done;
     unsigned long long exchange_bytes;
-    unsigned int counters[60];
+    unsigned long long merge_bytes;
+    unsigned int counters[kNumCounters];
 };
 
 constexpr uint32_t kTicketCounter0 = 0;  // counters[l]: exchange tickets of level l

@@ -1,12 +1,8 @@
-// Split step: early-exit test (Alg. 2/3) and exact stable merge-path splits (Sec. 3.1).
-//
-// For a diagonal d (an output count), the stable split i is the number of A elements
-// among the first d keys of the stable merge; A[m] is among them exactly when
-// A[m] <= B[d-1-m].  That predicate is true for m < i and false for m >= i, so one
-// warp brackets i with 32 evenly spaced probes per step: the ballot of the probes is
-// a prefix of ones, its popcount locates the bracket, and the range shrinks ~33x per
-// step (log_33 of the run length dependent steps instead of log_2).
+// Split step: early-exit test (Alg. 2/3) and the exact stable merge-path splits
+// (Sec. 3.1) of every diagonal d_k = floor(k*n/P), one warp per diagonal
+// (warp_split, ipm_split.cuh).
 #include "ipm_internal.h"
+#include "ipm_split.cuh"
 
 namespace ipm {
 
@@ -20,7 +16,8 @@ __global__ void early_exit_kernel(const K *buf, uint64_t la, uint64_t lb, Status
         sb->status = 0u;
         sb->done = done;
         sb->exchange_bytes = 0ull;
-        for (int q = 0; q < 60; ++q) sb->counters[q] = 0u;
+        sb->merge_bytes = 0ull;
+        for (int q = 0; q < kNumCounters; ++q) sb->counters[q] = 0u;
     }
 }
 
@@ -35,29 +32,8 @@ __global__ void __launch_bounds__(256) split_kernel(const K *__restrict__ A, uin
     if (k > P) return;  // whole warp exits together
     const uint64_t n = la + lb;
     const uint64_t d = (k * n) / P;
-    uint64_t lo = d > lb ? d - lb : 0;
-    uint64_t hi = d < la ? d : la;
-    while (hi - lo > 32) {
-        const uint64_t R = hi - lo;
-        const uint64_t m = lo + (R * (lane + 1)) / 33;  // strictly increasing, in [lo,hi)
-        const bool p = key_le(__ldg(A + m), __ldg(B + (d - 1 - m)));
-        const unsigned bal = __ballot_sync(0xffffffffu, p);
-        const int c = __popc(bal);
-        const uint64_t m_lo = __shfl_sync(0xffffffffu, m, c > 0 ? c - 1 : 0);
-        const uint64_t m_hi = __shfl_sync(0xffffffffu, m, c < 32 ? c : 31);
-        const uint64_t nlo = c > 0 ? m_lo + 1 : lo;
-        const uint64_t nhi = c < 32 ? m_hi : hi;
-        lo = nlo;
-        hi = nhi;
-    }
-    const uint64_t R = hi - lo;
-    bool p = false;
-    if (lane < R) {
-        const uint64_t m = lo + lane;
-        p = key_le(__ldg(A + m), __ldg(B + (d - 1 - m)));
-    }
-    const int c = __popc(__ballot_sync(0xffffffffu, p));
-    if (lane == 0) out[k] = lo + uint64_t(c);
+    const uint64_t i = warp_split<true>(A, la, B, lb, d);
+    if (lane == 0) out[k] = i;
 }
 
 template <typename K>

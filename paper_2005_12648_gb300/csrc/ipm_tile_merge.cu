@@ -1,33 +1,16 @@
 // Merge step: every pair (A_k, B_k) of the arranged buffer is merged stably in place by
 // one CTA (the per-thread std::inplace_merge of Alg. 2/3, here per CTA).
 //
-// Pair k occupies [d_k, d_{k+1}) as A[i_k, i_{k+1}) | B[j_k, j_{k+1}).  The CTA
-//   1. stages the pair in shared memory: the 16-byte-aligned body with one TMA bulk
-//      copy (cp.async.bulk, completion on an mbarrier), the unaligned head and tail
-//      (< 16 bytes each) with plain loads;
-//   2. gives each thread E consecutive outputs: a binary search on its diagonal of
-//      the pair's merge path (stable predicate A[m] <= B[d-1-m]), then E sequential
-//      merge steps into registers;
-//   3. writes the registers back over the staged pair (E odd keeps the blocked
-//      writes conflict-free across banks) and stores the body with one TMA bulk store,
-//      head and tail with plain stores.
-// The kernel is persistent (one CTA per SM, grid-stride over pairs); a pair never
-// straddles two CTAs, so the in-place write-back touches only the CTA's own range.
+// Pair k occupies [d_k, d_{k+1}) as A[i_k, i_{k+1}) | B[j_k, j_{k+1}); the shared-memory
+// merge of one pair is merge_pair_smem (ipm_tile_merge.cuh).  The kernel is persistent
+// (one CTA per SM, grid-stride over pairs); a pair never straddles two CTAs, so the
+// in-place write-back touches only the CTA's own range.
 #include "ipm_internal.h"
-#include "ipm_tma.cuh"
+#include "ipm_tile_merge.cuh"
 
 namespace ipm {
 
 namespace {
-
-template <typename K, bool KV, int THREADS, int E>
-struct TileShape {
-    static constexpr int kTile = THREADS * E;
-    static constexpr int kKeyPad = 16 / int(sizeof(K));
-    static constexpr size_t kKeyBytes = ((size_t(kTile + kKeyPad) * sizeof(K)) + 15) / 16 * 16;
-    static constexpr size_t kValBytes = KV ? ((size_t(kTile + 4) * 4 + 15) / 16 * 16) : 0;
-    static constexpr size_t kSmem = 128 + kKeyBytes + kValBytes;
-};
 
 template <typename K, bool KV, int THREADS, int E>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -62,110 +45,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (tid == 0 && sb != nullptr) set_status(sb, IPM_ERR_DEVICE);
             continue;
         }
-        const uint32_t b = c - a;
-        K *g = buf + d0;
-        uint32_t *gv = KV ? vals + d0 : nullptr;
-        const Geo<int(sizeof(K))> gk(g, c);
-        const Geo<4> gvv(KV ? (const void *)gv : (const void *)g, KV ? c : 0u);
-        K *tk = skeys + gk.off;          // staged keys: tk[0, c)
-        uint32_t *tv = svals + gvv.off;  // staged values: tv[0, c)
-
-        // ---- 1. stage
-        if (tid == 0) {
-            const uint32_t kb = gk.body * uint32_t(sizeof(K));
-            const uint32_t vb = KV ? gvv.body * 4u : 0u;
-            mbar_arrive_expect_tx(mbar, kb + vb);
-            if (kb) bulk_load(tk + gk.head, g + gk.head, kb, mbar);
-            if (KV && vb) bulk_load(tv + gvv.head, gv + gvv.head, vb, mbar);
-        }
-        for (uint32_t j = tid; j < gk.head; j += THREADS) tk[j] = g[j];
-        for (uint32_t j = gk.tail_start + tid; j < c; j += THREADS) tk[j] = g[j];
-        if (KV) {
-            for (uint32_t j = tid; j < gvv.head; j += THREADS) tv[j] = gv[j];
-            for (uint32_t j = gvv.tail_start + tid; j < c; j += THREADS) tv[j] = gv[j];
-        }
-        if (!mbar_wait_bounded(mbar, parity)) atomicOr(&abort_flag, 1);
-        parity ^= 1u;
-        __syncthreads();
-        if (abort_flag) {
-            if (tid == 0 && sb != nullptr) set_status(sb, IPM_ERR_TIMEOUT);
+        if (merge_pair_smem<K, KV, THREADS, E>(buf + d0, KV ? vals + d0 : nullptr, a, c, skeys,
+                                               svals, mbar, parity, abort_flag,
+                                               sb) == kPairAbort)
             break;
-        }
-
-        // ---- 2. merge path split of this thread's diagonal, then E merge steps
-        const K *sA = tk;
-        const K *sB = tk + a;
-        const uint32_t dt = tid * uint32_t(E);
-        K ok[E];
-        uint32_t oi[KV ? E : 1];
-        if (dt < c) {
-            uint32_t lo = dt > b ? dt - b : 0u;
-            uint32_t hi = dt < a ? dt : a;
-            while (lo < hi) {
-                const uint32_t m = (lo + hi) >> 1;
-                if (key_le(sA[m], sB[dt - 1 - m]))
-                    lo = m + 1;
-                else
-                    hi = m;
-            }
-            uint32_t ia = lo, ib = dt - lo;
-            K va = ia < a ? sA[ia] : K(0);
-            K vb = ib < b ? sB[ib] : K(0);
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const bool takeA = (ib >= b) || (ia < a && key_le(va, vb));
-                if (KV)
-                    oi[KV ? e : 0] = takeA ? ia : a + ib;
-                else
-                    ok[e] = takeA ? va : vb;
-                if (takeA) {
-                    ++ia;
-                    if (ia < a) va = sA[ia];
-                } else {
-                    ++ib;
-                    if (ib < b) vb = sB[ib];
-                }
-            }
-        }
-        uint32_t ov[KV ? E : 1];
-        if (KV && dt < c) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const uint32_t src = (dt + e < c) ? oi[KV ? e : 0] : 0u;
-                ok[e] = tk[src];
-                ov[KV ? e : 0] = tv[src];
-            }
-        }
-        __syncthreads();
-
-        // ---- 3. write back in place, then store
-        if (dt < c) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                if (dt + e < c) {
-                    tk[dt + e] = ok[e];
-                    if (KV) tv[dt + e] = ov[KV ? e : 0];
-                }
-            }
-        }
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            const uint32_t kb = gk.body * uint32_t(sizeof(K));
-            const uint32_t vb = KV ? gvv.body * 4u : 0u;
-            if (kb) bulk_store(g + gk.head, tk + gk.head, kb);
-            if (KV && vb) bulk_store(gv + gvv.head, tv + gvv.head, vb);
-            bulk_commit();
-        }
-        for (uint32_t j = tid; j < gk.head; j += THREADS) g[j] = tk[j];
-        for (uint32_t j = gk.tail_start + tid; j < c; j += THREADS) g[j] = tk[j];
-        if (KV) {
-            for (uint32_t j = tid; j < gvv.head; j += THREADS) gv[j] = tv[j];
-            for (uint32_t j = gvv.tail_start + tid; j < c; j += THREADS) gv[j] = tv[j];
-        }
-        if (tid == 0) bulk_wait_read0();
-        fence_proxy_async_smem();
-        __syncthreads();
     }
     if (tid == 0) bulk_wait_all0();
 }

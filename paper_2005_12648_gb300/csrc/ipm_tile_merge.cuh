@@ -1,0 +1,182 @@
+// Shared-memory merge of one pair (A_k, B_k) in place: the per-thread
+// std::inplace_merge of Alg. 2/3, done here by one CTA.  Used by the per-pair merge
+// kernel of the plain path and by the batched kernel.
+//
+// The pair [A (a) | B (c - a)] starting at g is
+//   1. staged in shared memory: the 16-byte-aligned body with one TMA bulk copy
+//      (cp.async.bulk, completion on an mbarrier), the unaligned head and tail
+//      (< 16 bytes each) with plain loads;
+//   2. merged (merge_staged): each thread owns E consecutive outputs, finds its diagonal
+//      of the pair's merge path by binary search, takes E sequential merge steps into
+//      registers and writes them back over the staged copy;
+//   3. stored: the body with one TMA bulk store, head and tail with plain stores.
+#pragma once
+
+#include "ipm_common.cuh"
+#include "ipm_tma.cuh"
+
+namespace ipm {
+
+template <typename K, bool KV, int THREADS, int E>
+struct TileShape {
+    static constexpr int kTile = THREADS * E;
+    static constexpr int kKeyPad = 16 / int(sizeof(K));
+    static constexpr size_t kKeyBytes = ((size_t(kTile + kKeyPad) * sizeof(K)) + 15) / 16 * 16;
+    static constexpr size_t kValBytes = KV ? ((size_t(kTile + 4) * 4 + 15) / 16 * 16) : 0;
+    static constexpr size_t kSmem = 128 + kKeyBytes + kValBytes;
+};
+
+enum : int { kPairAbort = 0, kPairMerged = 1, kPairInOrder = 2, kPairTrivial = 3 };
+
+// Step 2 of merge_pair_smem with EC outputs per thread (EC odd, THREADS * EC >= c):
+// each thread finds its diagonal of the pair's merge path by binary search (stable
+// predicate A[m] <= B[d-1-m]), takes EC branch-free merge steps into registers, and,
+// after a barrier, writes them back over the staged copy (EC odd keeps the blocked
+// writes conflict-free across banks).
+template <typename K, bool KV, int THREADS, int EC>
+__device__ __forceinline__ void merge_staged(K *tk, uint32_t *tv, uint32_t a, uint32_t c) {
+    const uint32_t tid = threadIdx.x;
+    const uint32_t b = c - a;
+    const K *sA = tk;
+    const K *sB = tk + a;
+    const uint32_t dt = tid * uint32_t(EC);
+    K ok[EC];
+    uint32_t oi[KV ? EC : 1];
+    if (dt < c) {
+        uint32_t lo = dt > b ? dt - b : 0u;
+        uint32_t hi = dt < a ? dt : a;
+        while (lo < hi) {
+            const uint32_t m = (lo + hi) >> 1;
+            if (key_le(sA[m], sB[dt - 1 - m]))
+                lo = m + 1;
+            else
+                hi = m;
+        }
+        // Branch-free steps (a, b >= 1 here).  Each run keeps its current key and the two
+        // after it in registers (indices clamped to the run); the taken side shifts its
+        // window and loads the key three ahead, which is needed two steps later at the
+        // earliest, so the shared-memory latency stays off the compare chain.  An
+        // exhausted side is never taken again, so its stale keys do not matter.
+        uint32_t ia = lo, ib = dt - lo;
+        const uint32_t la1 = a - 1, lb1 = b - 1;
+        K va0 = sA[ia < la1 ? ia : la1], va1 = sA[ia + 1 < la1 ? ia + 1 : la1];
+        K va2 = sA[ia + 2 < la1 ? ia + 2 : la1];
+        K vb0 = sB[ib < lb1 ? ib : lb1], vb1 = sB[ib + 1 < lb1 ? ib + 1 : lb1];
+        K vb2 = sB[ib + 2 < lb1 ? ib + 2 : lb1];
+#pragma unroll
+        for (int e = 0; e < EC; ++e) {
+            const bool takeA = (ib >= b) || (ia < a && key_le(va0, vb0));
+            if (KV)
+                oi[KV ? e : 0] = takeA ? ia : a + ib;
+            else
+                ok[e] = takeA ? va0 : vb0;
+            const uint32_t src = takeA ? (ia + 3 < la1 ? ia + 3 : la1)
+                                       : a + (ib + 3 < lb1 ? ib + 3 : lb1);
+            const K nv = tk[src];
+            ia += takeA ? 1u : 0u;
+            ib += takeA ? 0u : 1u;
+            va0 = takeA ? va1 : va0;
+            va1 = takeA ? va2 : va1;
+            va2 = takeA ? nv : va2;
+            vb0 = takeA ? vb0 : vb1;
+            vb1 = takeA ? vb1 : vb2;
+            vb2 = takeA ? vb2 : nv;
+        }
+    }
+    uint32_t ov[KV ? EC : 1];
+    if (KV && dt < c) {
+#pragma unroll
+        for (int e = 0; e < EC; ++e) {
+            const uint32_t src = (dt + e < c) ? oi[KV ? e : 0] : 0u;
+            ok[e] = tk[src];
+            ov[KV ? e : 0] = tv[src];
+        }
+    }
+    __syncthreads();
+    if (dt < c) {
+#pragma unroll
+        for (int e = 0; e < EC; ++e) {
+            if (dt + e < c) {
+                tk[dt + e] = ok[e];
+                if (KV) tv[dt + e] = ov[KV ? e : 0];
+            }
+        }
+    }
+}
+
+
+// Merges the pair at g (payload at gv when KV) through skeys/svals.  All THREADS
+// threads of the CTA call it together.  c <= THREADS * E, a <= c.  Returns
+//   kPairTrivial  one run is empty: nothing to move, nothing read;
+//   kPairInOrder  A[last] <= B[0] on the staged copy (the early exit of Alg. 2/3):
+//                 read, nothing written;
+//   kPairMerged   merged and written back;
+//   kPairAbort    the staging copy did not complete within the wait limit (status set
+//                 to IPM_ERR_TIMEOUT); the pair is left untouched.
+// On return the shared buffers are free again (the bulk store has finished reading
+// them).
+template <typename K, bool KV, int THREADS, int E>
+__device__ __forceinline__ int merge_pair_smem(K *g, uint32_t *gv, uint32_t a, uint32_t c,
+                                               K *skeys, uint32_t *svals, uint64_t *mbar,
+                                               uint32_t &parity, int &abort_flag,
+                                               StatusBlock *sb) {
+    const uint32_t tid = threadIdx.x;
+    const uint32_t b = c - a;
+    if (a == 0 || b == 0) return kPairTrivial;
+    const Geo<int(sizeof(K))> gk(g, c);
+    const Geo<4> gvv(KV ? (const void *)gv : (const void *)g, KV ? c : 0u);
+    K *tk = skeys + gk.off;          // staged keys: tk[0, c)
+    uint32_t *tv = svals + gvv.off;  // staged values: tv[0, c)
+
+    // ---- 1. stage
+    if (tid == 0) {
+        const uint32_t kb = gk.body * uint32_t(sizeof(K));
+        const uint32_t vb = KV ? gvv.body * 4u : 0u;
+        mbar_arrive_expect_tx(mbar, kb + vb);
+        if (kb) bulk_load(tk + gk.head, g + gk.head, kb, mbar);
+        if (KV && vb) bulk_load(tv + gvv.head, gv + gvv.head, vb, mbar);
+    }
+    for (uint32_t j = tid; j < gk.head; j += THREADS) tk[j] = g[j];
+    for (uint32_t j = gk.tail_start + tid; j < c; j += THREADS) tk[j] = g[j];
+    if (KV) {
+        for (uint32_t j = tid; j < gvv.head; j += THREADS) tv[j] = gv[j];
+        for (uint32_t j = gvv.tail_start + tid; j < c; j += THREADS) tv[j] = gv[j];
+    }
+    if (!mbar_wait_bounded(mbar, parity)) atomicOr(&abort_flag, 1);
+    parity ^= 1u;
+    __syncthreads();
+    if (abort_flag) {
+        if (tid == 0 && sb != nullptr) set_status(sb, IPM_ERR_TIMEOUT);
+        return kPairAbort;
+    }
+    if (key_le(tk[a - 1], tk[a])) {  // already in order: nothing to write
+        __syncthreads();             // every thread has read tk before it is reused
+        return kPairInOrder;
+    }
+
+    // ---- 2. merge in shared memory
+    merge_staged<K, KV, THREADS, E>(tk, tv, a, c);
+
+    // ---- 3. store the merged copy
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+        const uint32_t kb = gk.body * uint32_t(sizeof(K));
+        const uint32_t vb = KV ? gvv.body * 4u : 0u;
+        if (kb) bulk_store(g + gk.head, tk + gk.head, kb);
+        if (KV && vb) bulk_store(gv + gvv.head, tv + gvv.head, vb);
+        bulk_commit();
+    }
+    for (uint32_t j = tid; j < gk.head; j += THREADS) g[j] = tk[j];
+    for (uint32_t j = gk.tail_start + tid; j < c; j += THREADS) g[j] = tk[j];
+    if (KV) {
+        for (uint32_t j = tid; j < gvv.head; j += THREADS) gv[j] = tv[j];
+        for (uint32_t j = gvv.tail_start + tid; j < c; j += THREADS) gv[j] = tv[j];
+    }
+    if (tid == 0) bulk_wait_read0();
+    fence_proxy_async_smem();
+    __syncthreads();
+    return kPairMerged;
+}
+
+}  // namespace ipm
