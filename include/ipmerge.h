@@ -245,6 +245,97 @@ ipm_status ipm_merge_batched(void *d_buf, void *d_vals, uint64_t buf_len,
 ipm_status ipm_read_merge_bytes(const void *d_ws, ipm_stream_t stream, uint64_t *out);
 
 /*
+ * Learned split proposer.  The paper has no counterpart: it extends the split step
+ * (Sec. 3.1), whose cost is the chain of dependent probes of each diagonal's search.
+ * A small model predicts the split of a diagonal from its position; a warp then
+ * corrects the proposal to the exact split with one round of exponentially spaced
+ * probes around it (galloping) followed by the bracket search of ipm_merge_splits, so
+ * the result is always the exact split, only the number of dependent probe rounds
+ * changes.
+ *
+ * Model: y(x) = b2 + sum_h w2[h] * tanh(w1[h] * x + b1[h]), h < 32, FP32, with input
+ * x = d / n (the diagonal's relative position) and target y = i / len_a (the split's
+ * relative position in A); the proposal for diagonal d is round(y * len_a) clamped to
+ * the diagonal's range.  The struct lives in DEVICE memory, owned by the caller.
+ */
+#define IPM_SPLIT_MODEL_HIDDEN 32
+typedef struct {
+    float w1[IPM_SPLIT_MODEL_HIDDEN];
+    float b1[IPM_SPLIT_MODEL_HIDDEN];
+    float w2[IPM_SPLIT_MODEL_HIDDEN];
+    float b2;
+    float loss;      /* mean squared error on the training samples after training */
+    uint32_t steps;  /* Adam steps taken by the last ipm_split_model_train */
+    uint32_t reserved;
+} ipm_split_model;
+
+/* Adam hyper-parameters of ipm_split_model_train (Kingma & Ba). */
+typedef struct {
+    uint32_t steps;  /* full-batch Adam steps */
+    float lr;        /* learning rate */
+    float beta1, beta2, eps;
+} ipm_split_train_options;
+
+/* Device counters of a learned (or plain) split pass, accumulated by ipm_merge_splits_learned. */
+typedef struct {
+    uint64_t diagonals;    /* diagonals searched */
+    uint64_t rounds;       /* dependent probe rounds, summed over diagonals */
+    uint64_t probes;       /* predicate evaluations, summed over diagonals */
+    uint64_t abs_err_sum;  /* sum of |proposal - exact split| (0 without a model) */
+    uint64_t abs_err_max;  /* max of |proposal - exact split| */
+} ipm_split_stats;
+
+/* Workspace bytes of ipm_split_model_train for nsamples training diagonals. */
+ipm_status ipm_split_model_train_workspace_bytes(uint32_t nsamples, size_t *bytes);
+
+/*
+ * Train d_model in place on the runs A = d_buf[0, len_a), B = d_buf[len_a, len_a +
+ * len_b): the exact split of each of the nsamples diagonals d_diags[s] (uint64, device,
+ * 0 <= d <= len_a + len_b) is computed on the device (as ipm_merge_splits does) and
+ * becomes the target t_s = i_s / len_a for the input x_s = d_s / n; then opt->steps
+ * full-batch Adam steps minimise the mean squared error, starting from the parameters
+ * d_model holds on entry (Adam moments start at zero).  One CTA runs every step, so the
+ * call is a fixed number of launches.  len_a >= 1, 1 <= nsamples <= 2^20.
+ */
+ipm_status ipm_split_model_train(const void *d_buf, uint64_t len_a, uint64_t len_b,
+                                 ipm_dtype key_dtype, const uint64_t *d_diags,
+                                 uint32_t nsamples, const ipm_split_train_options *opt,
+                                 ipm_split_model *d_model, void *d_ws, size_t ws_bytes,
+                                 ipm_stream_t stream);
+
+/*
+ * The model's FP32 forward pass (d_y[s] = y(d_x[s])) and its mean-squared-error loss
+ * and gradient on (d_x, d_t): d_grad receives the 97 gradient entries in the order
+ * w1, b1, w2, b2, then the loss (98 floats).  These are the device functions the
+ * training uses, exposed for checking.  All arrays are device float arrays of n.
+ */
+ipm_status ipm_split_model_forward(const ipm_split_model *d_model, const float *d_x,
+                                   uint32_t n, float *d_y, ipm_stream_t stream);
+ipm_status ipm_split_model_loss_grad(const ipm_split_model *d_model, const float *d_x,
+                                     const float *d_t, uint32_t n, float *d_grad,
+                                     ipm_stream_t stream);
+
+/*
+ * ipm_merge_splits with proposals: the same exact splits d_split_a[k] on the diagonals
+ * d_k = floor(k*n/P), k = 0..P, found by galloping from the model's proposal.
+ * d_model may be NULL (no proposal: the plain bracket search, for comparison).
+ * d_stats (nullable, device, zeroed by the caller) accumulates the probe counts.
+ */
+ipm_status ipm_merge_splits_learned(const void *d_buf, uint64_t len_a, uint64_t len_b,
+                                    ipm_dtype key_dtype, uint64_t num_pairs,
+                                    const ipm_split_model *d_model, uint64_t *d_split_a,
+                                    ipm_split_stats *d_stats, ipm_stream_t stream);
+
+/*
+ * ipm_merge_inplace with the split step of ipm_merge_splits_learned (same workspace,
+ * same result, bit for bit).
+ */
+ipm_status ipm_merge_inplace_learned(void *d_buf, uint64_t len_a, uint64_t len_b,
+                                     ipm_dtype key_dtype, uint32_t log2_pairs,
+                                     const ipm_split_model *d_model, void *d_ws,
+                                     size_t ws_bytes, ipm_stream_t stream);
+
+/*
  * ipm_merge_inplace for callers that cannot allocate device memory.  The paper has no
  * counterpart: this is a deployment variant of the same merge.
  * Some callers cannot call cudaMalloc (another framework holds nearly all device

@@ -29,6 +29,11 @@ __all__ = [
     "workspace", "merge_inplace", "merge_inplace_kv",
     "IpmBatchedOptions", "ipm_merge_batched_workspace_bytes", "ipm_merge_batched_max_segment",
     "ipm_merge_batched", "ipm_read_merge_bytes", "segment_table", "merge_batched",
+    "IpmSplitModel", "IpmSplitTrainOptions", "IpmSplitStats", "SPLIT_MODEL_HIDDEN",
+    "ipm_split_model_train_workspace_bytes", "ipm_split_model_train", "ipm_split_model_forward",
+    "ipm_split_model_loss_grad", "ipm_merge_splits_learned", "ipm_merge_inplace_learned",
+    "split_model_initial_params", "split_model_to_device", "split_model_from_device",
+    "train_split_model",
 ]
 
 DTYPES = {"int32": 0, "uint32": 1, "uint64": 2, "float32": 3}
@@ -72,6 +77,12 @@ _SIGS = {
     "ipm_merge_batched_max_segment": (_i, [_i, _i, _vp, ctypes.POINTER(_u64)]),
     "ipm_merge_batched": (_i, [_vp, _vp, _u64, _vp, _u32, _i, _i, _vp, _vp, _sz, _vp]),
     "ipm_read_merge_bytes": (_i, [_vp, _vp, ctypes.POINTER(_u64)]),
+    "ipm_split_model_train_workspace_bytes": (_i, [_u32, ctypes.POINTER(_sz)]),
+    "ipm_split_model_train": (_i, [_vp, _u64, _u64, _i, _vp, _u32, _vp, _vp, _vp, _sz, _vp]),
+    "ipm_split_model_forward": (_i, [_vp, _vp, _u32, _vp, _vp]),
+    "ipm_split_model_loss_grad": (_i, [_vp, _vp, _vp, _u32, _vp, _vp]),
+    "ipm_merge_splits_learned": (_i, [_vp, _u64, _u64, _i, _u64, _vp, _vp, _vp, _vp]),
+    "ipm_merge_inplace_learned": (_i, [_vp, _u64, _u64, _i, _u32, _vp, _vp, _sz, _vp]),
 }
 
 
@@ -328,6 +339,75 @@ def ipm_read_merge_bytes(ws, stream=None) -> int:
     return int(out.value)
 
 
+SPLIT_MODEL_HIDDEN = 32
+
+
+class IpmSplitModel(ctypes.Structure):
+    """Mirror of ipm_split_model (the struct itself lives in device memory)."""
+    _fields_ = [("w1", ctypes.c_float * SPLIT_MODEL_HIDDEN),
+                ("b1", ctypes.c_float * SPLIT_MODEL_HIDDEN),
+                ("w2", ctypes.c_float * SPLIT_MODEL_HIDDEN), ("b2", ctypes.c_float),
+                ("loss", ctypes.c_float), ("steps", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class IpmSplitTrainOptions(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint32), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
+
+
+class IpmSplitStats(ctypes.Structure):
+    _fields_ = [("diagonals", ctypes.c_uint64), ("rounds", ctypes.c_uint64),
+                ("probes", ctypes.c_uint64), ("abs_err_sum", ctypes.c_uint64),
+                ("abs_err_max", ctypes.c_uint64)]
+
+
+def ipm_split_model_train_workspace_bytes(nsamples: int) -> int:
+    out = _sz(0)
+    _check(load().ipm_split_model_train_workspace_bytes(nsamples, ctypes.byref(out)),
+           "ipm_split_model_train_workspace_bytes")
+    return int(out.value)
+
+
+def ipm_split_model_train(buf, len_a: int, len_b: int, key_dtype, diags, nsamples: int,
+                          model, ws, steps: int = 300, lr: float = 1e-2, beta1: float = 0.9,
+                          beta2: float = 0.999, eps: float = 1e-8,
+                          ws_bytes: int | None = None, stream=None) -> None:
+    """model: device buffer of sizeof(IpmSplitModel) bytes holding the initial
+    parameters; trained in place.  diags: device uint64 (int64) array of diagonals."""
+    wsb = _nbytes(ws) if ws_bytes is None else ws_bytes
+    opt = IpmSplitTrainOptions(int(steps), float(lr), float(beta1), float(beta2), float(eps))
+    _check(load().ipm_split_model_train(_ptr(buf), len_a, len_b, _dt(key_dtype), _ptr(diags),
+                                        nsamples, ctypes.byref(opt), _ptr(model), _ptr(ws),
+                                        wsb, _stream(stream)), "ipm_split_model_train")
+
+
+def ipm_split_model_forward(model, x, n: int, y, stream=None) -> None:
+    _check(load().ipm_split_model_forward(_ptr(model), _ptr(x), n, _ptr(y), _stream(stream)),
+           "ipm_split_model_forward")
+
+
+def ipm_split_model_loss_grad(model, x, t, n: int, grad, stream=None) -> None:
+    _check(load().ipm_split_model_loss_grad(_ptr(model), _ptr(x), _ptr(t), n, _ptr(grad),
+                                            _stream(stream)), "ipm_split_model_loss_grad")
+
+
+def ipm_merge_splits_learned(buf, len_a: int, len_b: int, key_dtype, num_pairs: int, model,
+                             split_a, stats=None, stream=None) -> None:
+    _check(load().ipm_merge_splits_learned(_ptr(buf), len_a, len_b, _dt(key_dtype), num_pairs,
+                                           _ptr(model), _ptr(split_a), _ptr(stats),
+                                           _stream(stream)), "ipm_merge_splits_learned")
+
+
+def ipm_merge_inplace_learned(buf, len_a: int, len_b: int, key_dtype, model, ws,
+                              log2_pairs: int = 0, ws_bytes: int | None = None,
+                              stream=None) -> None:
+    wsb = _nbytes(ws) if ws_bytes is None else ws_bytes
+    _check(load().ipm_merge_inplace_learned(_ptr(buf), len_a, len_b, _dt(key_dtype),
+                                            log2_pairs, _ptr(model), _ptr(ws), wsb,
+                                            _stream(stream)), "ipm_merge_inplace_learned")
+
+
 # ------------------------------------------------------------------ conveniences
 
 def workspace(nbytes: int, device=None):
@@ -371,3 +451,57 @@ def merge_batched(buf, segs, key_dtype, vals=None, options=None, stream=None):
     ipm_merge_batched(buf, vals, buf.numel(), segs, nseg, key_dtype, ws, options=options,
                       stream=stream)
     return ws
+
+
+def split_model_initial_params():
+    """Deterministic starting point for training (float32, 97 values w1|b1|w2|b2): the
+    hidden units are steps at evenly spaced centres c_h = (h + 1/2)/32 of the input
+    range, w1 = 16, b1 = -16 c_h, w2 = 1/64, b2 = 1/2, so y(x) starts as a smooth
+    staircase close to y = x (the split of two runs drawn from one distribution)."""
+    import numpy as np
+
+    H = SPLIT_MODEL_HIDDEN
+    c = (np.arange(H, dtype=np.float64) + 0.5) / H
+    p = np.concatenate([np.full(H, 16.0), -16.0 * c, np.full(H, 1.0 / 64), [0.5]])
+    return p.astype(np.float32)
+
+
+def split_model_to_device(params, device=None):
+    """A device ipm_split_model (uint8 tensor of its size) holding the 97 parameters."""
+    import numpy as np
+    import torch
+
+    m = IpmSplitModel()
+    p = np.asarray(params, dtype=np.float32)
+    H = SPLIT_MODEL_HIDDEN
+    m.w1[:] = p[:H].tolist()
+    m.b1[:] = p[H:2 * H].tolist()
+    m.w2[:] = p[2 * H:3 * H].tolist()
+    m.b2 = float(p[3 * H])
+    raw = np.frombuffer(bytes(m), dtype=np.uint8).copy()
+    return torch.from_numpy(raw).to(device if device is not None else "cuda")
+
+
+def split_model_from_device(t):
+    """(params float32[97], loss, steps) of a device ipm_split_model."""
+    import numpy as np
+
+    raw = t.cpu().numpy().tobytes()
+    m = IpmSplitModel.from_buffer_copy(raw)
+    H = SPLIT_MODEL_HIDDEN
+    p = np.concatenate([np.array(m.w1[:], np.float32), np.array(m.b1[:], np.float32),
+                        np.array(m.w2[:], np.float32), np.array([m.b2], np.float32)])
+    return p, float(m.loss), int(m.steps)
+
+
+def train_split_model(buf, len_a: int, len_b: int, key_dtype, diags, steps: int = 300,
+                      lr: float = 1e-2, params=None, stream=None):
+    """Train a device model from the given (or the default initial) parameters on the
+    device diagonals `diags`; returns the device model tensor."""
+    model = split_model_to_device(split_model_initial_params() if params is None else params,
+                                  buf.device)
+    n = int(diags.numel())
+    ws = workspace(ipm_split_model_train_workspace_bytes(n), buf.device)
+    ipm_split_model_train(buf, len_a, len_b, key_dtype, diags, n, model, ws, steps=steps,
+                          lr=lr, stream=stream)
+    return model

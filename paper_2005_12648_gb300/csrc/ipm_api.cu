@@ -140,7 +140,8 @@ MergeLayout merge_layout(uint32_t G, uint64_t n, ipm_dtype key, bool kv) {
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 ipm_status merge_core(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_dtype key,
-                      uint32_t log2_pairs, void *ws, size_t ws_bytes, cudaStream_t stream) {
+                      uint32_t log2_pairs, void *ws, size_t ws_bytes, cudaStream_t stream,
+                      const ipm_split_model *model = nullptr) {
     const bool kv = vals != nullptr;
     uint32_t G = 0;
     IPM_TRY(check_merge_args(la, lb, key, kv, log2_pairs, &G));
@@ -159,11 +160,16 @@ ipm_status merge_core(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_d
     const uint64_t P = uint64_t(1) << G;
 
     {
-        PhaseScope ps(0, 2, stream);
+        PhaseScope ps(model ? 6 : 0, 2, stream);
         // a0: early exit (A empty, B empty, or A[last] <= B[0]) -> later steps are no-ops
         IPM_TRY(launch_early_exit(buf, la, lb, key, sb, stream));
-        // a1: exact stable splits on every diagonal
-        IPM_TRY(launch_splits(buf, la, lb, key, P, split, sb, stream));
+        // a1: exact stable splits on every diagonal (from the model's proposals when one
+        // is given: the same splits)
+        if (model != nullptr)
+            IPM_TRY(launch_learned_splits(buf, la, lb, key, P, model, split, nullptr, sb,
+                                          stream));
+        else
+            IPM_TRY(launch_splits(buf, la, lb, key, P, split, sb, stream));
     }
     // a2: division stage, one exchange level at a time
     if (G > 0) {
@@ -411,6 +417,86 @@ ipm_status ipm_merge_batched(void *d_buf, void *d_vals, uint64_t buf_len,
     PhaseScope ps(4, 3, st);
     return launch_batched(d_buf, static_cast<uint32_t *>(d_vals), buf_len, key_dtype, d_segs,
                           nseg, d_ws, L, by_size, variant, per_sm, st);
+}
+
+ipm_status ipm_split_model_train_workspace_bytes(uint32_t nsamples, size_t *bytes) {
+    if (bytes == nullptr || nsamples == 0 || nsamples > (1u << 20)) return IPM_ERR_INVALID_ARG;
+    *bytes = split_model_train_ws_bytes(nsamples);
+    return IPM_OK;
+}
+
+ipm_status ipm_split_model_train(const void *d_buf, uint64_t len_a, uint64_t len_b,
+                                 ipm_dtype key_dtype, const uint64_t *d_diags,
+                                 uint32_t nsamples, const ipm_split_train_options *opt,
+                                 ipm_split_model *d_model, void *d_ws, size_t ws_bytes,
+                                 ipm_stream_t stream) {
+    if (!valid_key(key_dtype)) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (opt == nullptr || d_model == nullptr || d_diags == nullptr || d_buf == nullptr)
+        return IPM_ERR_INVALID_ARG;
+    if (len_a == 0 || len_a > (uint64_t(1) << 40) || len_b > (uint64_t(1) << 40))
+        return IPM_ERR_INVALID_ARG;
+    if (nsamples == 0 || nsamples > (1u << 20) || opt->steps > 1000000u) return IPM_ERR_INVALID_ARG;
+    if (!(opt->lr > 0.f) || !(opt->beta1 >= 0.f && opt->beta1 < 1.f) ||
+        !(opt->beta2 >= 0.f && opt->beta2 < 1.f) || !(opt->eps > 0.f))
+        return IPM_ERR_INVALID_ARG;
+    if (d_ws == nullptr || ws_bytes < split_model_train_ws_bytes(nsamples))
+        return IPM_ERR_WORKSPACE;
+    if (!aligned(d_buf, size_t(dtype_bytes(key_dtype))) || !aligned(d_diags, 8) ||
+        !aligned(d_model, 4) || !aligned(d_ws, 256))
+        return IPM_ERR_ALIGNMENT;
+    cudaStream_t st = (cudaStream_t)stream;
+    PhaseScope ps(5, 3, st);
+    return launch_split_model_train(d_buf, len_a, len_b, key_dtype, d_diags, nsamples, *opt,
+                                    d_model, d_ws, st);
+}
+
+ipm_status ipm_split_model_forward(const ipm_split_model *d_model, const float *d_x,
+                                   uint32_t n, float *d_y, ipm_stream_t stream) {
+    if (n > 0 && (d_model == nullptr || d_x == nullptr || d_y == nullptr))
+        return IPM_ERR_INVALID_ARG;
+    if (!aligned(d_model, 4) || !aligned(d_x, 4) || !aligned(d_y, 4)) return IPM_ERR_ALIGNMENT;
+    return launch_split_model_forward(d_model, d_x, n, d_y, (cudaStream_t)stream);
+}
+
+ipm_status ipm_split_model_loss_grad(const ipm_split_model *d_model, const float *d_x,
+                                     const float *d_t, uint32_t n, float *d_grad,
+                                     ipm_stream_t stream) {
+    if (d_model == nullptr || d_x == nullptr || d_t == nullptr || d_grad == nullptr ||
+        n == 0 || n > (1u << 20))
+        return IPM_ERR_INVALID_ARG;
+    if (!aligned(d_model, 4) || !aligned(d_x, 4) || !aligned(d_t, 4) || !aligned(d_grad, 4))
+        return IPM_ERR_ALIGNMENT;
+    return launch_split_model_loss_grad(d_model, d_x, d_t, n, d_grad, (cudaStream_t)stream);
+}
+
+ipm_status ipm_merge_splits_learned(const void *d_buf, uint64_t len_a, uint64_t len_b,
+                                    ipm_dtype key_dtype, uint64_t num_pairs,
+                                    const ipm_split_model *d_model, uint64_t *d_split_a,
+                                    ipm_split_stats *d_stats, ipm_stream_t stream) {
+    if (!valid_key(key_dtype)) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (num_pairs == 0 || d_split_a == nullptr) return IPM_ERR_INVALID_ARG;
+    if (len_a > (uint64_t(1) << 40) || len_b > (uint64_t(1) << 40)) return IPM_ERR_INVALID_ARG;
+    const uint64_t n = len_a + len_b;
+    if (n > 0 && num_pairs > (~uint64_t(0)) / n) return IPM_ERR_INVALID_ARG;
+    if (num_pairs > (uint64_t(1) << 30)) return IPM_ERR_INVALID_ARG;
+    if (n > 0 && d_buf == nullptr) return IPM_ERR_INVALID_ARG;
+    if (!aligned(d_buf, size_t(dtype_bytes(key_dtype))) || !aligned(d_split_a, 8) ||
+        !aligned(d_model, 4) || !aligned(d_stats, 8))
+        return IPM_ERR_ALIGNMENT;
+    cudaStream_t st = (cudaStream_t)stream;
+    PhaseScope ps(6, 1, st);
+    return launch_learned_splits(d_buf, len_a, len_b, key_dtype, num_pairs, d_model, d_split_a,
+                                 d_stats, nullptr, st);
+}
+
+ipm_status ipm_merge_inplace_learned(void *d_buf, uint64_t len_a, uint64_t len_b,
+                                     ipm_dtype key_dtype, uint32_t log2_pairs,
+                                     const ipm_split_model *d_model, void *d_ws,
+                                     size_t ws_bytes, ipm_stream_t stream) {
+    if (d_model == nullptr) return IPM_ERR_INVALID_ARG;
+    if (!aligned(d_model, 4)) return IPM_ERR_ALIGNMENT;
+    return merge_core(d_buf, nullptr, len_a, len_b, key_dtype, log2_pairs, d_ws, ws_bytes,
+                      (cudaStream_t)stream, d_model);
 }
 
 ipm_status ipm_timing_enable(int enable) {

@@ -69,4 +69,20 @@ ipm_status launch_batched(void *buf, uint32_t *vals, uint64_t buf_len, ipm_dtype
                           const BatchedLayout &L, uint32_t by_size, uint32_t variant,
                           uint32_t ctas_per_sm, cudaStream_t stream);
 
+// Learned split proposer (ipm_learned.cu).
+ipm_status launch_learned_splits(const void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
+                                 uint64_t P, const ipm_split_model *model, uint64_t *split,
+                                 ipm_split_stats *stats, const StatusBlock *sb,
+                                 cudaStream_t stream);
+size_t split_model_train_ws_bytes(uint32_t nsamples);
+ipm_status launch_split_model_train(const void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
+                                    const uint64_t *diags, uint32_t n,
+                                    const ipm_split_train_options &opt,
+                                    ipm_split_model *model, void *ws, cudaStream_t stream);
+ipm_status launch_split_model_forward(const ipm_split_model *model, const float *x, uint32_t n,
+                                      float *y, cudaStream_t stream);
+ipm_status launch_split_model_loss_grad(const ipm_split_model *model, const float *x,
+                                        const float *t, uint32_t n, float *grad,
+                                        cudaStream_t stream);
+
 }  // namespace ipm

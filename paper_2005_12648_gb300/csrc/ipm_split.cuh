@@ -22,11 +22,16 @@ __device__ __forceinline__ K split_load(const K *p) {
 
 // The split i on diagonal d, 0 <= d <= la + lb; every lane of the (full) warp calls it
 // with the same arguments and receives the same i.  lo/hi may narrow the search when a
-// bracket is already known (lo <= i <= hi); pass the trivial bracket otherwise.
-template <bool NC, typename K>
+// bracket is already known (lo <= i <= hi); pass the trivial bracket otherwise.  With
+// COUNT, *rounds and *probes receive the dependent probe rounds and the predicate
+// evaluations the search made.
+template <bool NC, bool COUNT = false, typename K>
 __device__ __forceinline__ uint64_t warp_split_bracket(const K *A, const K *B, uint64_t d,
-                                                       uint64_t lo, uint64_t hi) {
+                                                       uint64_t lo, uint64_t hi,
+                                                       uint32_t *rounds = nullptr,
+                                                       uint32_t *probes = nullptr) {
     const unsigned lane = threadIdx.x & 31u;
+    uint32_t nr = 0, np = 0;
     while (hi - lo > 32) {
         const uint64_t R = hi - lo;
         const uint64_t m = lo + (R * (lane + 1)) / 33;  // strictly increasing, in [lo,hi)
@@ -39,6 +44,10 @@ __device__ __forceinline__ uint64_t warp_split_bracket(const K *A, const K *B, u
         const uint64_t nhi = c < 32 ? m_hi : hi;
         lo = nlo;
         hi = nhi;
+        if (COUNT) {
+            ++nr;
+            np += 32;
+        }
     }
     const uint64_t R = hi - lo;
     bool p = false;
@@ -47,6 +56,12 @@ __device__ __forceinline__ uint64_t warp_split_bracket(const K *A, const K *B, u
         p = key_le(split_load<NC>(A + m), split_load<NC>(B + (d - 1 - m)));
     }
     const int c = __popc(__ballot_sync(0xffffffffu, p));
+    if (COUNT) {
+        nr += R > 0 ? 1u : 0u;
+        np += uint32_t(R);
+        *rounds = nr;
+        *probes = np;
+    }
     return lo + uint64_t(c);
 }
 

@@ -57,3 +57,15 @@ def test_batched_lengths_fit_the_cap():
     torch = pytest.importorskip("torch")
     tb, toffs = W.batched_buffer_torch(torch, small_a, small_b, 2, "cpu")
     assert np.array_equal(tb.numpy(), buf) and np.array_equal(toffs, offs)
+
+
+def test_split_training_diagonals():
+    n = (1 << 29) + 12345
+    d = W.split_training_diagonals(n, 4096, seed=0)
+    assert d.dtype == np.uint64 and d.size == 4096
+    assert np.all(np.diff(d.astype(np.int64)) >= 0) and int(d[-1]) <= n
+    assert np.array_equal(d, W.split_training_diagonals(n, 4096, seed=0))
+    # the stratified half covers every slice of the range
+    hist = np.histogram(d.astype(np.float64), bins=64, range=(0, n))[0]
+    assert hist.min() >= 4096 // 2 // 64
+    assert W.split_training_diagonals(10, 7, seed=1).max() <= 10

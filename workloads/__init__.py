@@ -290,3 +290,18 @@ def batched_buffer_torch(torch, len_a, len_b, seed: int, device):
     buf = (key & 0xFFFFFFFF).to(torch.int32)
     offs = np.concatenate([[0], np.cumsum(la + lb)[:-1]]).astype(np.uint64)
     return buf, offs
+
+
+# ----------------------------------------------------------------------------------
+# Training diagonals of the learned split proposer.
+# ----------------------------------------------------------------------------------
+
+def split_training_diagonals(n: int, nsamples: int = 4096, seed: int = 0) -> np.ndarray:
+    """Diagonals in [0, n] for training: half uniform draws (SplitMix64 stream 900),
+    half stratified (the centre of each of nsamples/2 equal slices), sorted, uint64."""
+    half = nsamples // 2
+    u = unit_np(raw_np(seed, 900, nsamples - half))
+    uni = np.floor(u * (n + 1)).astype(np.uint64)
+    strat = np.floor((np.arange(half, dtype=np.float64) + 0.5) * (n / max(half, 1))).astype(np.uint64)
+    d = np.concatenate([uni, strat])
+    return np.sort(np.minimum(d, np.uint64(n)))
