@@ -9,7 +9,16 @@ pristine device copy outside the timed interval; each step is timed with CUDA ev
 the launching stream and the K step times are summed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload c2-int32-uniform|c2-int32-dup16|...]
+                  [--workload c2-int32-uniform|c2-int32-dup16|...|c4-int32-batched|
+                              c5-float32-learned] [--no-forms]
+
+The line also carries "forms": the other two forms of the metric measured in the same
+run on their own workloads -- "batched" (20,000 int32 segments, log-uniform lengths,
+2^28 keys in all, one ipm_merge_batched call per step, against a loop of
+ipm_merge_inplace calls) and "learned" (float32 Gaussian-mixture runs of 2^28 each:
+the split step with model proposals against the plain split, P = 2^16, and the whole
+merge with each).  --workload c4-int32-batched / c5-float32-learned makes that form
+the headline instead.
 
 N > 1 (torchrun): the merge does not shard (a single merge needs an all-to-all that
 would defeat "in place"), so every rank merges its own replica; value = all ranks' keys
@@ -52,7 +61,16 @@ WORKLOADS = {
                          "int32 L_A=L_B=2^20, uniform (L2-resident, 8 MiB)"),
     "c2s-int32-uniform": ("uniform", "int32", 1 << 25, 1 << 25,
                           "int32 L_A=L_B=2^25, uniform (reduced c2 for profiling; 256 MiB)"),
+    "c4-int32-batched": ("uniform", "int32", 1 << 27, 1 << 27,
+                         "batched: 20,000 int32 segments back to back, per-side lengths "
+                         "log-uniform on [2^4, 2^e_max] with e_max set so the total is "
+                         "<= 2^28 keys, uniform values; one ipm_merge_batched call"),
+    "c5-float32-learned": ("gmm", "float32", 1 << 28, 1 << 28,
+                           "learned split: float32 keys from an 8-component Gaussian "
+                           "mixture, L_A=L_B=2^28, model trained on 4,096 diagonals "
+                           "(300 Adam steps); ipm_merge_inplace_learned"),
 }
+FORM = {"c4-int32-batched": "batched", "c5-float32-learned": "learned"}
 NP_DT = {"int32": np.int32, "uint32": np.uint32, "uint64": np.uint64, "float32": np.float32}
 
 
@@ -65,6 +83,8 @@ def parse():
     p.add_argument("--workload", default="c2-int32-uniform", choices=sorted(WORKLOADS))
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-forms", action="store_true",
+                   help="skip the batched / learned side measurements")
     return p.parse_args()
 
 
@@ -157,9 +177,38 @@ def method_bytes(n: int, w: int) -> dict:
 def cpu_oracle_timing(wl, budget_s: float = 10.0, steps: int | None = None,
                       warmup: int = 0):
     """The oracle's plain sequential merge on a 2^24+2^24-key sample of the workload
-    (same generator), single thread.  Returns (GKeys/s, sample description, reps)."""
+    (same generator), single thread; for the batched workload, the oracle merging the
+    first 1/16 of the segments one by one.  Returns (GKeys/s, sample description,
+    reps, seconds)."""
     import oracle
     import workloads
+
+    if wl is WORKLOADS["c4-int32-batched"]:
+        la, lb, _ = workloads.batched_lengths()
+        k = la.size // 16
+        buf, offs = workloads.batched_buffer(la[:k], lb[:k], seed=0)
+        segs = [(int(o), int(x), int(y)) for o, x, y in zip(offs, la[:k], lb[:k])]
+        keys = int(buf.size)
+
+        def once():
+            for o, x, y in segs:
+                oracle.merge(buf[o:o + x], buf[o + x:o + x + y])
+
+        once()
+        times = []
+        t_end = time.perf_counter() + budget_s
+        while True:
+            t0 = time.perf_counter()
+            once()
+            times.append(time.perf_counter() - t0)
+            if (steps is not None and len(times) >= steps) or \
+                    (steps is None and time.perf_counter() > t_end):
+                break
+        tot = sum(times)
+        sample = (f"oracle two-pointer merge of the first {k} of the {la.size} segments "
+                  f"({keys} keys, 1/16 of the segments), one by one, {len(times)} reps, "
+                  f"1 thread")
+        return keys * len(times) / tot / 1e9, sample, len(times), tot
 
     dist, dt, la, lb, _ = wl
     scale = max(1, (la + lb) // (1 << 25))
@@ -207,6 +256,192 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------------ our arm
 
+def timed_steps(torch, stream, steps, prep, call):
+    """CUDA-event time (ms) of `call` per step, with `prep` (the input restore) run
+    before each step outside the timed interval."""
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for s, e in evs:
+        prep()
+        s.record(stream)
+        call()
+        e.record(stream)
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in evs]
+
+
+def measure_batched(torch, ipm, workloads, dev, stream, steps, warmup, options=None,
+                    loop_segments=500):
+    """The batched form: 20,000 int32 segments (2^28 keys) merged by one
+    ipm_merge_batched call per step; also replayed as a captured CUDA graph, and
+    compared with a loop of ipm_merge_inplace calls over the first loop_segments
+    segments."""
+    la, lb, emax = workloads.batched_lengths()
+    pristine, offs = workloads.batched_buffer_torch(torch, la, lb, 0, dev)
+    n = pristine.numel()
+    buf = torch.empty_like(pristine)
+    segs = ipm.segment_table(offs.astype(np.int64), la, lb, dev)
+    ws = ipm.workspace(ipm.ipm_merge_batched_workspace_bytes(n, la.size, "int32", False,
+                                                             options), dev)
+
+    def prep():
+        buf.copy_(pristine)
+
+    def call():
+        ipm.ipm_merge_batched(buf, None, n, segs, la.size, "int32", ws, options=options)
+
+    for _ in range(max(1, warmup)):
+        prep()
+        call()
+    torch.cuda.synchronize()
+    if ipm.ipm_read_device_status(ws) != 0:
+        raise RuntimeError("batched: device status not OK")
+    ipm.ipm_timing_read()
+    ipm.ipm_timing_enable(True)
+    times = timed_steps(torch, stream, steps, prep, call)
+    ipm.ipm_timing_enable(False)
+    ph = ipm.ipm_timing_read().as_dict()["batched"]
+    if ipm.ipm_read_device_status(ws) != 0:
+        raise RuntimeError("batched: device status not OK")
+    merge_b, exch_b = ipm.ipm_read_merge_bytes(ws), ipm.ipm_read_exchange_bytes(ws)
+    ms = statistics.median(times)
+
+    # the same call captured in a CUDA graph
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        prep()
+        ipm.ipm_merge_batched(buf, None, n, segs, la.size, "int32", ws, options=options,
+                              stream=side)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        ipm.ipm_merge_batched(buf, None, n, segs, la.size, "int32", ws, options=options,
+                              stream=side)
+    gtimes = timed_steps(torch, stream, steps, prep, g.replay)
+    if ipm.ipm_read_device_status(ws) != 0:
+        raise RuntimeError("batched graph: device status not OK")
+    ok_sorted = bool(all((buf[o + 1:o + x + y] >= buf[o:o + x + y - 1]).all().item()
+                         for o, x, y in zip(offs[:64].tolist(), la[:64].tolist(),
+                                            lb[:64].tolist())))
+
+    # baseline: one ipm_merge_inplace call per segment, on the first segments
+    K = min(loop_segments, la.size)
+    kkeys = int((la[:K] + lb[:K]).sum())
+    wsp = ipm.workspace(ipm.ipm_merge_workspace_bytes(int(la[:K].max()), int(lb[:K].max()),
+                                                      "int32"), dev)
+
+    def loop():
+        for o, x, y in zip(offs[:K].tolist(), la[:K].tolist(), lb[:K].tolist()):
+            ipm.ipm_merge_inplace(buf[o:], x, y, "int32", wsp)
+
+    loop_ms = statistics.median(timed_steps(torch, stream, 3, prep, loop))
+    peak, _ = peaks()
+    min_b = 2 * n * 4
+    return {
+        "workload": "c4-int32-batched", "segments": int(la.size), "keys": int(n),
+        "e_max": round(float(emax), 4), "max_segment": int((la + lb).max()),
+        "options": options or {"tile": 0, "order": 0, "ctas_per_sm": 0},
+        "ms_per_step": ms, "value": n / (ms * 1e-3) / 1e9, "unit": UNIT,
+        "graph_ms_per_step": statistics.median(gtimes),
+        "graph_value": n / (statistics.median(gtimes) * 1e-3) / 1e9,
+        "launches_per_step": ph["launches"] // max(1, steps),
+        "merge_bytes": merge_b, "exchange_bytes": exch_b, "min_bytes": min_b,
+        "method_frac": (merge_b + exch_b) / (ms * 1e-3) / 1e9 / peak,
+        "min_frac": min_b / (ms * 1e-3) / 1e9 / peak,
+        "loop_baseline": {"segments": K, "keys": kkeys, "ms": loop_ms,
+                          "value": kkeys / (loop_ms * 1e-3) / 1e9,
+                          "calls": K, "note": "one ipm_merge_inplace call per segment"},
+        "speedup_vs_loop": (n / (ms * 1e-3)) / (kkeys / (loop_ms * 1e-3)),
+        "sorted_check": ok_sorted, "buffer": buf, "pristine": pristine,
+    }
+
+
+def measure_learned(torch, ipm, workloads, dev, stream, steps, warmup, P=1 << 16,
+                    nsamples=4096, train_steps=300):
+    """The learned-split form on float32 Gaussian-mixture runs of 2^28 each: the model
+    is trained once (timed), then the split step with proposals is timed against the
+    plain split at P diagonals, and the whole merge with each split step."""
+    la = lb = 1 << 28
+    n = la + lb
+    pristine = workloads.make_buffer_torch(torch, "gmm", np.float32, la, lb, 0, dev)
+    buf = torch.empty_like(pristine)
+    diags = torch.from_numpy(workloads.split_training_diagonals(n, nsamples, 0)
+                             .view(np.int64)).to(dev)
+    model = ipm.split_model_to_device(ipm.split_model_initial_params(), dev)
+    tws = ipm.workspace(ipm.ipm_split_model_train_workspace_bytes(nsamples), dev)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    ipm.ipm_split_model_train(pristine, la, lb, "float32", diags, nsamples, model, tws,
+                              steps=train_steps, lr=1e-2)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = t0.elapsed_time(t1)
+    _, loss, _ = ipm.split_model_from_device(model)
+
+    out = torch.empty(P + 1, dtype=torch.int64, device=dev)
+    ref = torch.empty(P + 1, dtype=torch.int64, device=dev)
+    split = {}
+    for name, m in (("plain", None), ("learned", model)):
+        st = torch.zeros(5, dtype=torch.int64, device=dev)
+        ipm.ipm_merge_splits_learned(pristine, la, lb, "float32", P, m, out, st)
+        torch.cuda.synchronize()
+        stats = st.cpu().numpy()
+        if name == "plain":
+            call = (lambda: ipm.ipm_merge_splits(pristine, la, lb, "float32", P, ref))
+        else:
+            call = (lambda: ipm.ipm_merge_splits_learned(pristine, la, lb, "float32", P,
+                                                         model, out))
+        for _ in range(3):
+            call()
+        t = statistics.median(timed_steps(torch, stream, max(5, steps), lambda: None, call))
+        split[name] = {"ms": t, "rounds_per_split": float(stats[1] / stats[0]),
+                       "probes_per_split": float(stats[2] / stats[0]),
+                       "mean_abs_err": float(stats[3] / stats[0]),
+                       "max_abs_err": int(stats[4])}
+    torch.cuda.synchronize()
+    same = bool(torch.equal(out, ref))
+
+    ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, "float32"), dev)
+    merges = {}
+    for name in ("plain", "learned"):
+        if name == "plain":
+            call = (lambda: ipm.ipm_merge_inplace(buf, la, lb, "float32", ws))
+        else:
+            call = (lambda: ipm.ipm_merge_inplace_learned(buf, la, lb, "float32", model, ws))
+        for _ in range(max(1, warmup)):
+            buf.copy_(pristine)
+            call()
+        ipm.ipm_timing_read()
+        ipm.ipm_timing_enable(True)
+        times = timed_steps(torch, stream, steps, lambda: buf.copy_(pristine), call)
+        ipm.ipm_timing_enable(False)
+        ph = ipm.ipm_timing_read().as_dict()
+        if ipm.ipm_read_device_status(ws) != 0:
+            raise RuntimeError(f"learned form ({name}): device status not OK")
+        split_key = "learned_split" if name == "learned" else "split"
+        ms = statistics.median(times)
+        merges[name] = {"ms_per_step": ms, "value": n / (ms * 1e-3) / 1e9,
+                        "split_phase_ms": ph[split_key]["ms"] / steps,
+                        "launches_per_step": sum(v["launches"] for v in ph.values()) // steps}
+    ok_sorted = bool((buf[1:] >= buf[:-1]).all().item())
+    return {
+        "workload": "c5-float32-learned", "keys": n, "P": P,
+        "model": {"hidden": 32, "params": 97, "dtype": "fp32", "train_samples": nsamples,
+                  "train_steps": train_steps, "train_ms": train_ms, "train_loss": loss},
+        "split": split, "split_speedup": split["plain"]["ms"] / split["learned"]["ms"],
+        "splits_identical": same, "merge": merges,
+        "value": merges["learned"]["value"], "ms_per_step": merges["learned"]["ms_per_step"],
+        "unit": UNIT, "sorted_check": ok_sorted, "buffer": buf, "pristine": pristine,
+        "model_tensor": model,
+    }
+
+
+def _public(d):
+    return {k: v for k, v in d.items() if k not in ("buffer", "pristine", "model_tensor")}
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -219,9 +454,112 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", local)
     build_ext.build_library()
     ipm.load()
+    stream = torch.cuda.current_stream()
+    form = FORM.get(args.workload, "plain")
+    if form == "plain":
+        line = run_plain(args, rank, world, torch, ipm, workloads, dev, stream)
+    else:
+        line = run_form(args, rank, world, torch, ipm, workloads, dev, stream, form)
+    if line is None:
+        return
+    if not args.no_forms and world == 1:
+        torch.cuda.empty_cache()
+        forms = {}
+        if form != "batched":
+            forms["batched"] = _public(measure_batched(torch, ipm, workloads, dev, stream,
+                                                       steps=10, warmup=2))
+            torch.cuda.empty_cache()
+        if form != "learned":
+            forms["learned"] = _public(measure_learned(torch, ipm, workloads, dev, stream,
+                                                       steps=5, warmup=1))
+            torch.cuda.empty_cache()
+        line["forms"] = forms
+    print(json.dumps(line), flush=True)
+
+
+def run_form(args, rank, world, torch, ipm, workloads, dev, stream, form):
+    """Headline line of the batched or learned form (replicas when N > 1)."""
+    sampler = ClockSampler(gpu_uuid(torch)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    if form == "batched":
+        m = measure_batched(torch, ipm, workloads, dev, stream, args.steps, args.warmup)
+    else:
+        m = measure_learned(torch, ipm, workloads, dev, stream, args.steps, args.warmup)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = m["ms_per_step"]
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    if rank != 0:
+        return None
+    dist, dt, la, lb, desc = WORKLOADS[args.workload]
+    n = m["keys"]
+    peak, peak_kind = peaks()
+    if form == "batched":
+        achieved = (m["merge_bytes"] + m["exchange_bytes"]) / (ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "batched call (levels + merge kernels)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": f"{peak_kind} hbm_gbs", "traffic": None,
+                "bytes_per_launch": m["merge_bytes"] + m["exchange_bytes"], "launch_ms": ms}
+        launches = m["launches_per_step"] * args.steps
+    else:
+        exch_note = "exchange_level_kernel (one launch per level), as in the plain form"
+        roof = {"bound": "hbm", "kernel": exch_note, "achieved": None, "peak": peak,
+                "unit": "GB/s", "frac": None, "peak_kind": f"{peak_kind} hbm_gbs",
+                "traffic": None}
+        launches = m["merge"]["learned"]["launches_per_step"] * args.steps
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, sample, reps, _ = cpu_oracle_timing(WORKLOADS[args.workload], budget_s=10.0)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    e2e = None
+    if not args.no_e2e and form == "learned":
+        e2e = run_e2e_learned(torch, ipm, m, args.steps, stream, m["model_tensor"])
+    elif not args.no_e2e:
+        e2e = run_e2e_batched(torch, ipm, workloads, m, args.steps, stream, dev)
+    return {
+        "metric": METRIC, "value": n * world / (ms * 1e-3) / 1e9, "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dt,
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "form": form,
+                   "l2": "inputs larger than L2 (%.1f GiB buffer)" % (n * 4 / 2**30),
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roof, "form_detail": _public(m), "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clocks, "sorted_check": m["sorted_check"],
+    }
+
+
+def run_e2e_batched(torch, ipm, workloads, m, steps, stream, dev):
+    """The batched call with host buffers: H2D of the keys, the merge, D2H, timed."""
+    pristine = m["pristine"]
+    la, lb, _ = workloads.batched_lengths()
+    offs = np.concatenate([[0], np.cumsum(la + lb)[:-1]]).astype(np.int64)
+    segs = ipm.segment_table(offs, la, lb, dev)
+    n = pristine.numel()
+    ws = ipm.workspace(ipm.ipm_merge_batched_workspace_bytes(n, la.size, "int32"), dev)
+    return run_e2e(torch, pristine, steps, stream,
+                   lambda d: ipm.ipm_merge_batched(d, None, n, segs, la.size, "int32", ws))
+
+
+def run_e2e_learned(torch, ipm, m, steps, stream, model):
+    pristine = m["pristine"]
+    la = lb = pristine.numel() // 2
+    ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, "float32"), pristine.device)
+    return run_e2e(torch, pristine, steps, stream,
+                   lambda d: ipm.ipm_merge_inplace_learned(d, la, lb, "float32", model, ws))
+
+
+def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
     dist, dt, la, lb, desc = WORKLOADS[args.workload]
     n, w = la + lb, np.dtype(NP_DT[dt]).itemsize
-    stream = torch.cuda.current_stream()
 
     pristine = workloads.make_buffer_torch(torch, dist, NP_DT[dt], la, lb, 0, dev)
     buf = torch.empty_like(pristine)
@@ -292,16 +630,18 @@ def run_ours(args, rank, world):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(torch, ipm, pristine, la, lb, dt, ws, args.steps, stream)
+        e2e = run_e2e(torch, pristine, args.steps, stream,
+                      lambda d: ipm.ipm_merge_inplace(d, la, lb, dt, ws))
+    del buf, pristine
 
     if rank != 0:
-        return
+        return None
     cpu = None
     if not args.no_cpu_baseline:
         v, sample, reps, _ = cpu_oracle_timing(WORKLOADS[args.workload], budget_s=10.0)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     step_s = ms_per_step * 1e-3
-    line = {
+    return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dt,
@@ -329,32 +669,26 @@ def run_ours(args, rank, world):
         "sorted_check": ok_sorted,
         "wall_s_timed_region": wall,
     }
-    print(json.dumps(line), flush=True)
 
 
-def run_e2e(torch, ipm, pristine, la, lb, dt, ws, steps, stream):
-    """Same merge through the public API with host buffers: H2D of the input from
-    pinned memory, the merge, D2H of the result into pinned memory, all timed."""
+def run_e2e(torch, pristine, steps, stream, merge):
+    """The merge through the public API with host buffers: H2D of the input from pinned
+    memory, merge(device buffer), D2H of the result into pinned memory, all timed."""
     host_in = pristine.cpu().pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     dbuf = torch.empty_like(pristine)
+
+    def call():
+        dbuf.copy_(host_in, non_blocking=True)
+        merge(dbuf)
+        host_out.copy_(dbuf, non_blocking=True)
+
     for _ in range(2):
-        dbuf.copy_(host_in, non_blocking=True)
-        ipm.ipm_merge_inplace(dbuf, la, lb, dt, ws)
-        host_out.copy_(dbuf, non_blocking=True)
+        call()
     torch.cuda.synchronize()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(steps)]
-    for s, e in evs:
-        s.record(stream)
-        dbuf.copy_(host_in, non_blocking=True)
-        ipm.ipm_merge_inplace(dbuf, la, lb, dt, ws)
-        host_out.copy_(dbuf, non_blocking=True)
-        e.record(stream)
-    torch.cuda.synchronize()
-    ms = sum(s.elapsed_time(e) for s, e in evs) / steps
+    ms = sum(timed_steps(torch, stream, steps, lambda: None, call)) / steps
     nbytes = pristine.numel() * pristine.element_size()
-    return {"value": (la + lb) / (ms * 1e-3) / 1e9, "unit": UNIT,
+    return {"value": pristine.numel() / (ms * 1e-3) / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": ms}
 
 
