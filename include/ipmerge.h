@@ -167,6 +167,21 @@ ipm_status ipm_rotate(void *d_ptr, uint64_t len_x, uint64_t len_y, uint32_t elem
 ipm_status ipm_read_exchange_bytes(const void *d_ws, ipm_stream_t stream, uint64_t *out);
 
 /*
+ * How many of the last levels of the division stage the merge entry points fuse with
+ * the pair merge (process-wide, default 4; a device that cannot schedule clusters of
+ * 2^levels CTAs gets the largest smaller count it can).  With F fused levels, the exchange levels
+ * stop at G - F, and a thread-block cluster of 2^F CTAs takes each group of 2^F
+ * consecutive pairs: the group's region holds exactly those pairs' A and B slices, so
+ * each CTA stages its pair's two slices, the cluster barrier ensures the whole group
+ * has been read, and each pair is merged on chip and written to its final place.  The
+ * result is identical for every F; F only trades exchange passes over the buffer for
+ * cluster scheduling.  0 <= levels <= 4 (16-CTA clusters use the non-portable cluster
+ * size), else IPM_ERR_INVALID_ARG.  Not thread-safe against concurrent merge calls.
+ */
+ipm_status ipm_set_fused_levels(uint32_t levels);
+ipm_status ipm_get_fused_levels(uint32_t *levels);
+
+/*
  * Batched segmented merge: many independent in-place merges in one call.
  * Segment t of the table is the problem of Sec. 1 on its own slice of the buffer:
  * A = d_buf[offset, offset + len_a) and B = d_buf[offset + len_a, offset + len_a +

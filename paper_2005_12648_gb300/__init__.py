@@ -33,7 +33,7 @@ __all__ = [
     "ipm_split_model_train_workspace_bytes", "ipm_split_model_train", "ipm_split_model_forward",
     "ipm_split_model_loss_grad", "ipm_merge_splits_learned", "ipm_merge_inplace_learned",
     "split_model_initial_params", "split_model_to_device", "split_model_from_device",
-    "train_split_model",
+    "train_split_model", "ipm_set_fused_levels", "ipm_get_fused_levels",
 ]
 
 DTYPES = {"int32": 0, "uint32": 1, "uint64": 2, "float32": 3}
@@ -83,6 +83,8 @@ _SIGS = {
     "ipm_split_model_loss_grad": (_i, [_vp, _vp, _vp, _u32, _vp, _vp]),
     "ipm_merge_splits_learned": (_i, [_vp, _u64, _u64, _i, _u64, _vp, _vp, _vp, _vp]),
     "ipm_merge_inplace_learned": (_i, [_vp, _u64, _u64, _i, _u32, _vp, _vp, _sz, _vp]),
+    "ipm_set_fused_levels": (_i, [_u32]),
+    "ipm_get_fused_levels": (_i, [ctypes.POINTER(_u32)]),
 }
 
 
@@ -406,6 +408,16 @@ def ipm_merge_inplace_learned(buf, len_a: int, len_b: int, key_dtype, model, ws,
     _check(load().ipm_merge_inplace_learned(_ptr(buf), len_a, len_b, _dt(key_dtype),
                                             log2_pairs, _ptr(model), _ptr(ws), wsb,
                                             _stream(stream)), "ipm_merge_inplace_learned")
+
+
+def ipm_set_fused_levels(levels: int) -> None:
+    _check(load().ipm_set_fused_levels(levels), "ipm_set_fused_levels")
+
+
+def ipm_get_fused_levels() -> int:
+    out = _u32(0)
+    _check(load().ipm_get_fused_levels(ctypes.byref(out)), "ipm_get_fused_levels")
+    return int(out.value)
 
 
 # ------------------------------------------------------------------ conveniences

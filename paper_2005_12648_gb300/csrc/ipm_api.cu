@@ -85,6 +85,9 @@ class PhaseScope {
 
 constexpr uint32_t kMaxLog2Pairs = 22;
 
+// Bottom levels of the division stage fused with the pair merge (ipm_set_fused_levels).
+uint32_t g_fused_levels = 4;
+
 bool valid_key(ipm_dtype t) {
     return t == IPM_INT32 || t == IPM_UINT32 || t == IPM_UINT64 || t == IPM_FLOAT32;
 }
@@ -177,9 +180,16 @@ ipm_status merge_core(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_d
             PhaseScope ps(1, 1, stream);
             IPM_TRY(launch_xplan_levels(split, n, G, pa, key, kv, sb, stream));
         }
-        for (uint32_t l = 0; l < G; ++l) {
+        // the last F levels are fused with the pair merge (clusters of 2^F CTAs)
+        const uint32_t F =
+            usable_fused_levels(key, kv, G < g_fused_levels ? G : g_fused_levels);
+        for (uint32_t l = 0; l + F < G; ++l) {
             PhaseScope ps(2, 1, stream);
             IPM_TRY(launch_exchange_level(buf, vals, key, n, l, pa, sb, stream));
+        }
+        if (F > 0) {
+            PhaseScope ps(3, 1, stream);
+            return launch_cluster_merge(buf, vals, la, lb, key, split, G, F, sb, stream);
         }
     }
     // a3: per-pair merge
@@ -497,6 +507,18 @@ ipm_status ipm_merge_inplace_learned(void *d_buf, uint64_t len_a, uint64_t len_b
     if (!aligned(d_model, 4)) return IPM_ERR_ALIGNMENT;
     return merge_core(d_buf, nullptr, len_a, len_b, key_dtype, log2_pairs, d_ws, ws_bytes,
                       (cudaStream_t)stream, d_model);
+}
+
+ipm_status ipm_set_fused_levels(uint32_t levels) {
+    if (levels > 4) return IPM_ERR_INVALID_ARG;
+    g_fused_levels = levels;
+    return IPM_OK;
+}
+
+ipm_status ipm_get_fused_levels(uint32_t *levels) {
+    if (levels == nullptr) return IPM_ERR_INVALID_ARG;
+    *levels = g_fused_levels;
+    return IPM_OK;
 }
 
 ipm_status ipm_timing_enable(int enable) {

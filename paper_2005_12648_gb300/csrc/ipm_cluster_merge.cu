@@ -1,0 +1,381 @@
+// The last log2(C) levels of the division stage (Alg. 3) fused with the pair merge,
+// one thread-block cluster of C CTAs per group of C consecutive pairs.
+//
+// After the levels above it, the C pairs k0 .. k0+C-1 of a group occupy one contiguous
+// region [d_k0, d_{k0+C}) holding A[i_k0, i_{k0+C}) followed by B[j_k0, j_{k0+C}):
+// exactly the inputs of those pairs, and exactly the span their outputs fill.  So the
+// group needs no exchange: CTA r of the cluster stages pair k0+r's two slices (its A
+// part and its B part, wherever the group's layout puts them) in its shared memory,
+// the cluster barrier guarantees that every CTA of the group has read its inputs, and
+// then each CTA merges its pair on chip and stores it to [d_k, d_{k+1}).  The region is
+// read once and written once, and log2(C) exchange levels over the whole buffer
+// disappear.  Pairs with an empty run are moved too (their data still changes place).
+#include "ipm_internal.h"
+#include "ipm_tile_merge.cuh"
+
+namespace ipm {
+
+namespace {
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t nclusters_x() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+// Every thread of every CTA of the cluster arrives and waits (release / acquire).
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile(
+        "barrier.cluster.arrive.release.aligned;\n\t"
+        "barrier.cluster.wait.acquire.aligned;" ::
+            : "memory");
+}
+
+template <typename K, bool KV, int THREADS, int E>
+struct ClusterShape {
+    static constexpr int kTile = THREADS * E;
+    static constexpr int kSlack = 16;  // phase offsets of the three ranges
+    static constexpr size_t kKeyBytes = (size_t(kTile + kSlack) * sizeof(K) + 15) / 16 * 16;
+    static constexpr size_t kValBytes = KV ? (size_t(kTile + kSlack) * 4 + 15) / 16 * 16 : 0;
+    static constexpr size_t kSmem = 128 + kKeyBytes + kValBytes;
+};
+
+// Element phase of an address within its 16-byte line.
+template <typename T>
+__device__ __forceinline__ uint32_t phase_of(const T *p) {
+    return uint32_t(reinterpret_cast<uintptr_t>(p) & 15u) / uint32_t(sizeof(T));
+}
+
+// Issue the staging of src[0, len) into dst[0, len) (dst has src's 16-byte phase): the
+// body with one bulk copy counted on mbar, head and tail with plain loads.  Returns
+// the body bytes.
+template <typename T, int THREADS>
+__device__ __forceinline__ uint32_t stage_range(T *dst, const T *src, uint32_t len,
+                                                uint64_t *mbar) {
+    const Geo<int(sizeof(T))> gg(src, len);
+    const uint32_t tid = threadIdx.x;
+    const uint32_t bytes = gg.body * uint32_t(sizeof(T));
+    if (tid == 0 && bytes) bulk_load(dst + gg.head, src + gg.head, bytes, mbar);
+    for (uint32_t j = tid; j < gg.head; j += THREADS) dst[j] = src[j];
+    for (uint32_t j = gg.tail_start + tid; j < len; j += THREADS) dst[j] = src[j];
+    return bytes;
+}
+
+template <typename T>
+__device__ __forceinline__ uint32_t body_bytes(const T *src, uint32_t len) {
+    const Geo<int(sizeof(T))> gg(src, len);
+    return gg.body * uint32_t(sizeof(T));
+}
+
+// Store src[0, len) (src has dst's phase) to dst: body by one bulk store, head and tail
+// with plain stores.
+template <typename T, int THREADS>
+__device__ __forceinline__ void store_range(T *dst, const T *src, uint32_t len) {
+    const Geo<int(sizeof(T))> gg(dst, len);
+    const uint32_t tid = threadIdx.x;
+    const uint32_t bytes = gg.body * uint32_t(sizeof(T));
+    if (tid == 0 && bytes) bulk_store(dst + gg.head, src + gg.head, bytes);
+    for (uint32_t j = tid; j < gg.head; j += THREADS) dst[j] = src[j];
+    for (uint32_t j = gg.tail_start + tid; j < len; j += THREADS) dst[j] = src[j];
+}
+
+// Geometry of one CTA's pair in the current group, computed by thread 0 into shared
+// memory (so the merge does not have to keep it in registers).
+template <typename K>
+struct PairGeo {
+    K *gA, *gB, *gO;              // the A slice, the B slice, the output range
+    uint32_t *vA, *vB, *vO;       // payload ranges (key-value)
+    uint32_t a, b;                // run lengths
+    uint32_t offA, offB, oo;      // staged offsets (keys)
+    uint32_t offAV, offBV, ooV;   // staged offsets (payloads)
+};
+
+template <typename K, bool KV, int THREADS, int E, int C>
+__global__ void __launch_bounds__(THREADS, 1)
+    cluster_merge_kernel(K *__restrict__ buf, uint32_t *__restrict__ vals, uint64_t la,
+                         uint64_t lb, const uint64_t *__restrict__ split, uint32_t G,
+                         StatusBlock *sb) {
+    using Shape = ClusterShape<K, KV, THREADS, E>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);
+    K *R = reinterpret_cast<K *>(smem_raw + 128);
+    uint32_t *RV = reinterpret_cast<uint32_t *>(smem_raw + 128 + Shape::kKeyBytes);
+    __shared__ int abort_flag;
+    __shared__ PairGeo<K> pg;
+    volatile PairGeo<K> &vg = pg;
+    constexpr uint32_t VK = 16u / uint32_t(sizeof(K));  // keys per 16 bytes
+    constexpr uint32_t VV = 4u;                          // payloads per 16 bytes
+
+    // every CTA of a cluster runs the same number of iterations (cluster barriers)
+    const bool done = sb != nullptr && *((volatile unsigned int *)&sb->done);
+    const uint32_t tid = threadIdx.x;
+    const uint64_t P = 1ull << G;
+    const uint64_t groups = done ? 0 : P / C;
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        mbar_fence_init();
+        abort_flag = 0;
+    }
+    uint32_t parity = 0;
+
+    for (uint64_t t = cluster_id_x(); t < groups; t += nclusters_x()) {
+        if (tid == 0) {
+            const uint64_t n = la + lb;
+            const uint64_t k0 = t * C, k1 = k0 + C, k = k0 + cluster_ctarank();
+            const uint64_t dlo = (k0 * n) >> G, dhi = (k1 * n) >> G;
+            const uint64_t ilo = split[k0], ihi = split[k1];
+            const uint64_t d0 = (k * n) >> G, d1 = ((k + 1) * n) >> G;
+            const uint64_t i0 = split[k], i1 = split[k + 1];
+            // the group's layout: A[ilo, ihi) at dlo, then B[jlo, jhi); a consistent split
+            // table keeps both slices of pair k inside it
+            const bool ok = ilo <= i0 && i0 <= i1 && i1 <= ihi && ihi <= dhi && ilo <= dlo &&
+                            i0 <= d0 && i1 - i0 <= d1 - d0 && d0 - i0 >= dlo - ilo &&
+                            d1 - i1 <= dhi - ihi && d1 - d0 <= uint64_t(Shape::kTile);
+            if (!ok && sb != nullptr) set_status(sb, IPM_ERR_DEVICE);
+            const uint32_t c = ok ? uint32_t(d1 - d0) : 0u;
+            const uint32_t a = ok ? uint32_t(i1 - i0) : 0u;
+            const uint64_t posA = dlo + (i0 - ilo);
+            const uint64_t posB = dlo + (ihi - ilo) + ((d0 - i0) - (dlo - ilo));
+            K *gA = buf + posA, *gB = buf + posB, *gO = buf + d0;
+            // staged offsets with the 16-byte phases of their global ranges
+            const uint32_t oo = phase_of(gO);
+            const uint32_t offA = oo + ((phase_of(gA) + VK - oo) % VK);
+            const uint32_t offB = offA + a + ((phase_of(gB) + VK - (offA + a) % VK) % VK);
+            pg.gA = gA;
+            pg.gB = gB;
+            pg.gO = gO;
+            pg.a = a;
+            pg.b = c - a;
+            pg.offA = offA;
+            pg.offB = offB;
+            pg.oo = oo;
+            if (KV) {
+                uint32_t *vA = vals + posA, *vB = vals + posB, *vO = vals + d0;
+                const uint32_t ooV = phase_of(vO);
+                const uint32_t offAV = ooV + ((phase_of(vA) + VV - ooV) % VV);
+                pg.vA = vA;
+                pg.vB = vB;
+                pg.vO = vO;
+                pg.ooV = ooV;
+                pg.offAV = offAV;
+                pg.offBV = offAV + a + ((phase_of(vB) + VV - (offAV + a) % VV) % VV);
+            }
+        }
+        __syncthreads();
+        const uint32_t a = vg.a, b = vg.b;
+
+        // ---- stage both slices
+        if (a + b > 0) {
+            if (tid == 0) {
+                uint32_t tx = body_bytes(pg.gA, a) + body_bytes(pg.gB, b);
+                if (KV) tx += body_bytes(pg.vA, a) + body_bytes(pg.vB, b);
+                mbar_arrive_expect_tx(mbar, tx);
+            }
+            stage_range<K, THREADS>(R + vg.offA, vg.gA, a, mbar);
+            stage_range<K, THREADS>(R + vg.offB, vg.gB, b, mbar);
+            if (KV) {
+                stage_range<uint32_t, THREADS>(RV + vg.offAV, vg.vA, a, mbar);
+                stage_range<uint32_t, THREADS>(RV + vg.offBV, vg.vB, b, mbar);
+            }
+            if (!mbar_wait_bounded(mbar, parity)) atomicOr(&abort_flag, 1);
+            parity ^= 1u;
+        }
+        __syncthreads();
+        // ---- every CTA of the group has its inputs on chip: the region may be written
+        cluster_sync_all();
+        if (abort_flag) {
+            if (tid == 0 && sb != nullptr) set_status(sb, IPM_ERR_TIMEOUT);
+            continue;  // keep taking part in the cluster barriers, write nothing
+        }
+        if (a + b == 0) continue;
+
+        // ---- merge on chip into the output's phase (a move when a run is empty)
+        merge_two<K, KV, THREADS, E, true>(R + vg.offA, RV + vg.offAV, a, R + vg.offB,
+                                           RV + vg.offBV, b, R + vg.oo, RV + vg.ooV);
+        fence_proxy_async_smem();
+        __syncthreads();
+
+        // ---- store
+        const uint32_t c = vg.a + vg.b;
+        store_range<K, THREADS>(vg.gO, R + vg.oo, c);
+        if (KV) store_range<uint32_t, THREADS>(vg.vO, RV + vg.ooV, c);
+        if (tid == 0) {
+            bulk_commit();
+            bulk_wait_read0();
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+    }
+    if (tid == 0) bulk_wait_all0();
+}
+
+// Resident clusters of the kernel on the current device (0 when clusters of C CTAs
+// cannot be scheduled), queried once per instantiation.
+template <typename K, bool KV, int THREADS, int E, int C>
+int cluster_capacity() {
+    using Shape = ClusterShape<K, KV, THREADS, E>;
+    auto kern = cluster_merge_kernel<K, KV, THREADS, E, C>;
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    cached = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(Shape::kSmem)) != cudaSuccess ||
+        (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                       1) != cudaSuccess)) {
+        (void)cudaGetLastError();
+        return cached;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(C * 64, 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = Shape::kSmem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int mc = 0;
+    if (cudaOccupancyMaxActiveClusters(&mc, kern, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        mc = 0;
+    }
+    cached = mc > 0 ? mc : 0;
+    return cached;
+}
+
+template <typename K, bool KV, int THREADS, int E, int C>
+ipm_status cluster_merge_t(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
+                           const uint64_t *split, uint32_t G, StatusBlock *sb,
+                           cudaStream_t stream) {
+    using Shape = ClusterShape<K, KV, THREADS, E>;
+    auto kern = cluster_merge_kernel<K, KV, THREADS, E, C>;
+    const int max_clusters = cluster_capacity<K, KV, THREADS, E, C>();
+    if (max_clusters < 1) return IPM_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = Shape::kSmem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const uint64_t groups = (1ull << G) / C;
+    uint64_t nc = groups < uint64_t(max_clusters) ? groups : uint64_t(max_clusters);
+    if (nc == 0) nc = 1;
+    cfg.gridDim = dim3(unsigned(nc * C), 1, 1);
+    IPM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, (K *)buf, vals, la, lb, split, G, sb));
+    return IPM_OK;
+}
+
+template <typename K, bool KV>
+struct ClusterTileOf;
+template <>
+struct ClusterTileOf<int32_t, false> { static constexpr int T = 1024, E = 33; };
+template <>
+struct ClusterTileOf<uint32_t, false> { static constexpr int T = 1024, E = 33; };
+template <>
+struct ClusterTileOf<float, false> { static constexpr int T = 1024, E = 33; };
+template <>
+struct ClusterTileOf<uint64_t, false> { static constexpr int T = 512, E = 33; };
+template <typename K>
+struct ClusterTileOf<K, true> { static constexpr int T = 512, E = 33; };
+
+template <typename K, int C>
+ipm_status cluster_dispatch(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
+                            const uint64_t *split, uint32_t G, StatusBlock *sb,
+                            cudaStream_t stream) {
+    if (vals != nullptr)
+        return cluster_merge_t<K, true, ClusterTileOf<K, true>::T, ClusterTileOf<K, true>::E,
+                               C>(buf, vals, la, lb, split, G, sb, stream);
+    return cluster_merge_t<K, false, ClusterTileOf<K, false>::T, ClusterTileOf<K, false>::E,
+                           C>(buf, nullptr, la, lb, split, G, sb, stream);
+}
+
+template <typename K, int C>
+int capacity_kv(bool kv) {
+    return kv ? cluster_capacity<K, true, ClusterTileOf<K, true>::T, ClusterTileOf<K, true>::E,
+                                 C>()
+              : cluster_capacity<K, false, ClusterTileOf<K, false>::T,
+                                 ClusterTileOf<K, false>::E, C>();
+}
+
+template <int C>
+int capacity_by_key(ipm_dtype key, bool kv) {
+    switch (key) {
+    case IPM_INT32:
+        return capacity_kv<int32_t, C>(kv);
+    case IPM_UINT32:
+        return capacity_kv<uint32_t, C>(kv);
+    case IPM_UINT64:
+        return capacity_kv<uint64_t, C>(kv);
+    case IPM_FLOAT32:
+        return capacity_kv<float, C>(kv);
+    }
+    return 0;
+}
+
+template <int C>
+ipm_status cluster_by_key(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_dtype key,
+                          const uint64_t *split, uint32_t G, StatusBlock *sb,
+                          cudaStream_t stream) {
+    switch (key) {
+    case IPM_INT32:
+        return cluster_dispatch<int32_t, C>(buf, vals, la, lb, split, G, sb, stream);
+    case IPM_UINT32:
+        return cluster_dispatch<uint32_t, C>(buf, vals, la, lb, split, G, sb, stream);
+    case IPM_UINT64:
+        return cluster_dispatch<uint64_t, C>(buf, vals, la, lb, split, G, sb, stream);
+    case IPM_FLOAT32:
+        return cluster_dispatch<float, C>(buf, vals, la, lb, split, G, sb, stream);
+    }
+    return IPM_ERR_UNSUPPORTED_DTYPE;
+}
+
+}  // namespace
+
+uint32_t usable_fused_levels(ipm_dtype key, bool with_values, uint32_t wanted) {
+    for (uint32_t f = wanted; f > 0; --f) {
+        int cap = 0;
+        switch (f) {
+        case 1: cap = capacity_by_key<2>(key, with_values); break;
+        case 2: cap = capacity_by_key<4>(key, with_values); break;
+        case 3: cap = capacity_by_key<8>(key, with_values); break;
+        case 4: cap = capacity_by_key<16>(key, with_values); break;
+        default: cap = 0;
+        }
+        if (cap > 0) return f;
+    }
+    return 0;
+}
+
+ipm_status launch_cluster_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
+                                ipm_dtype key, const uint64_t *split, uint32_t G,
+                                uint32_t log2_cluster, StatusBlock *sb, cudaStream_t stream) {
+    switch (log2_cluster) {
+    case 1:
+        return cluster_by_key<2>(buf, vals, la, lb, key, split, G, sb, stream);
+    case 2:
+        return cluster_by_key<4>(buf, vals, la, lb, key, split, G, sb, stream);
+    case 3:
+        return cluster_by_key<8>(buf, vals, la, lb, key, split, G, sb, stream);
+    case 4:
+        return cluster_by_key<16>(buf, vals, la, lb, key, split, G, sb, stream);
+    }
+    return IPM_ERR_INVALID_ARG;
+}
+
+}  // namespace ipm

@@ -50,6 +50,14 @@ ipm_status launch_exchange_level(void *buf, uint32_t *vals, ipm_dtype key, uint6
                                  uint32_t l, XPlanArea pa, StatusBlock *sb,
                                  cudaStream_t stream);
 
+// The last log2_cluster levels fused with the pair merge (ipm_cluster_merge.cu): run
+// after levels 0 .. G - log2_cluster - 1; clusters of 2^log2_cluster CTAs.
+ipm_status launch_cluster_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
+                                ipm_dtype key, const uint64_t *split, uint32_t G,
+                                uint32_t log2_cluster, StatusBlock *sb, cudaStream_t stream);
+// The largest F <= wanted whose clusters of 2^F CTAs the device can schedule (0: none).
+uint32_t usable_fused_levels(ipm_dtype key, bool with_values, uint32_t wanted);
+
 // Per-pair shared-memory merge of an arranged buffer.
 ipm_status launch_tile_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
                              ipm_dtype key, const uint64_t *split, uint32_t G,

@@ -28,17 +28,19 @@ struct TileShape {
 
 enum : int { kPairAbort = 0, kPairMerged = 1, kPairInOrder = 2, kPairTrivial = 3 };
 
-// Step 2 of merge_pair_smem with EC outputs per thread (EC odd, THREADS * EC >= c):
-// each thread finds its diagonal of the pair's merge path by binary search (stable
-// predicate A[m] <= B[d-1-m]), takes EC branch-free merge steps into registers, and,
-// after a barrier, writes them back over the staged copy (EC odd keeps the blocked
-// writes conflict-free across banks).
-template <typename K, bool KV, int THREADS, int EC>
-__device__ __forceinline__ void merge_staged(K *tk, uint32_t *tv, uint32_t a, uint32_t c) {
+// Merge of two staged runs A = sA[0, a) and B = sB[0, b) (payloads vA, vB when KV) by
+// the whole CTA with EC outputs per thread (EC odd, THREADS * EC >= a + b; a, b >= 1
+// unless MAY_BE_EMPTY, which makes an empty run a move of the other): each thread
+// finds its diagonal of the merge path by binary search (stable predicate
+// A[m] <= B[d-1-m]), takes EC branch-free merge steps into registers, and, after a
+// barrier, writes them to dk[0, a + b) (dv for payloads), which may overlap the
+// sources (EC odd keeps the blocked writes conflict-free across banks).
+template <typename K, bool KV, int THREADS, int EC, bool MAY_BE_EMPTY = false>
+__device__ __forceinline__ void merge_two(const K *sA, const uint32_t *vA, uint32_t a,
+                                          const K *sB, const uint32_t *vB, uint32_t b,
+                                          K *dk, uint32_t *dv) {
     const uint32_t tid = threadIdx.x;
-    const uint32_t b = c - a;
-    const K *sA = tk;
-    const K *sB = tk + a;
+    const uint32_t c = a + b;
     const uint32_t dt = tid * uint32_t(EC);
     K ok[EC];
     uint32_t oi[KV ? EC : 1];
@@ -52,13 +54,15 @@ __device__ __forceinline__ void merge_staged(K *tk, uint32_t *tv, uint32_t a, ui
             else
                 hi = m;
         }
-        // Branch-free steps (a, b >= 1 here).  Each run keeps its current key and the two
-        // after it in registers (indices clamped to the run); the taken side shifts its
-        // window and loads the key three ahead, which is needed two steps later at the
-        // earliest, so the shared-memory latency stays off the compare chain.  An
-        // exhausted side is never taken again, so its stale keys do not matter.
+        // Branch-free steps.  Each run keeps its current key and the two after it in
+        // registers (indices clamped to the run); the taken side shifts its window and
+        // loads the key three ahead, which is needed two steps later at the earliest, so
+        // the shared-memory latency stays off the compare chain.  An exhausted (or empty)
+        // side is never taken again, so its stale keys do not matter; an empty run reads
+        // (and ignores) the first word of its staging area.
         uint32_t ia = lo, ib = dt - lo;
-        const uint32_t la1 = a - 1, lb1 = b - 1;
+        const uint32_t la1 = MAY_BE_EMPTY && a == 0 ? 0u : a - 1;
+        const uint32_t lb1 = MAY_BE_EMPTY && b == 0 ? 0u : b - 1;
         K va0 = sA[ia < la1 ? ia : la1], va1 = sA[ia + 1 < la1 ? ia + 1 : la1];
         K va2 = sA[ia + 2 < la1 ? ia + 2 : la1];
         K vb0 = sB[ib < lb1 ? ib : lb1], vb1 = sB[ib + 1 < lb1 ? ib + 1 : lb1];
@@ -70,9 +74,9 @@ __device__ __forceinline__ void merge_staged(K *tk, uint32_t *tv, uint32_t a, ui
                 oi[KV ? e : 0] = takeA ? ia : a + ib;
             else
                 ok[e] = takeA ? va0 : vb0;
-            const uint32_t src = takeA ? (ia + 3 < la1 ? ia + 3 : la1)
-                                       : a + (ib + 3 < lb1 ? ib + 3 : lb1);
-            const K nv = tk[src];
+            const K *src = takeA ? sA + (ia + 3 < la1 ? ia + 3 : la1)
+                                 : sB + (ib + 3 < lb1 ? ib + 3 : lb1);
+            const K nv = *src;
             ia += takeA ? 1u : 0u;
             ib += takeA ? 0u : 1u;
             va0 = takeA ? va1 : va0;
@@ -88,8 +92,9 @@ __device__ __forceinline__ void merge_staged(K *tk, uint32_t *tv, uint32_t a, ui
 #pragma unroll
         for (int e = 0; e < EC; ++e) {
             const uint32_t src = (dt + e < c) ? oi[KV ? e : 0] : 0u;
-            ok[e] = tk[src];
-            ov[KV ? e : 0] = tv[src];
+            const bool fromA = src < a;
+            ok[e] = fromA ? sA[src] : sB[src - a];
+            ov[KV ? e : 0] = fromA ? vA[src] : vB[src - a];
         }
     }
     __syncthreads();
@@ -97,13 +102,19 @@ __device__ __forceinline__ void merge_staged(K *tk, uint32_t *tv, uint32_t a, ui
 #pragma unroll
         for (int e = 0; e < EC; ++e) {
             if (dt + e < c) {
-                tk[dt + e] = ok[e];
-                if (KV) tv[dt + e] = ov[KV ? e : 0];
+                dk[dt + e] = ok[e];
+                if (KV) dv[dt + e] = ov[KV ? e : 0];
             }
         }
     }
 }
 
+// Step 2 of merge_pair_smem: the staged pair tk[0, c) = [A (a) | B (c - a)] merged onto
+// itself.
+template <typename K, bool KV, int THREADS, int EC>
+__device__ __forceinline__ void merge_staged(K *tk, uint32_t *tv, uint32_t a, uint32_t c) {
+    merge_two<K, KV, THREADS, EC>(tk, tv, a, tk + a, KV ? tv + a : tv, c - a, tk, tv);
+}
 
 // Merges the pair at g (payload at gv when KV) through skeys/svals.  All THREADS
 // threads of the CTA call it together.  c <= THREADS * E, a <= c.  Returns

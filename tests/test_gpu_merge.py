@@ -182,3 +182,29 @@ def test_async_on_a_side_stream(ipm, dev, orc):
         ipm.ipm_merge_inplace(buf, a.size, b.size, "int32", ws, stream=s)
     s.synchronize()
     assert first_diff(from_dev(buf, np.int32), orc.merge(a, b)) is None
+
+
+@pytest.mark.parametrize("fused", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("dt", [np.int32, np.uint64])
+def test_fused_bottom_levels_match_oracle(ipm, dev, orc, fused, dt):
+    """The last `fused` levels done by thread-block clusters (each cluster stages its
+    group's pairs, then writes them merged) give the oracle's merge for every depth,
+    including pair counts below the cluster size, empty runs inside a group, ragged
+    sizes and ties."""
+    cases = [(3_000_017, 2_900_011, "uniform", 0), (1_000_003, 700_001, "dup16", 0),
+             (50_000, 70_001, "uniform", 3), (123_457, 98_765, "alternation", 6),
+             (1_000_000, 1, "uniform", 4), (333_333, 333_333, "revdisjoint", 5),
+             (2_000_001, 17, "uniform", 0)]
+    ipm.ipm_set_fused_levels(fused)
+    try:
+        assert ipm.ipm_get_fused_levels() == fused
+        for la, lb, dist, G in cases:
+            if dist == "alternation" and dt == np.float32:
+                continue
+            a, b = W.make_pair(dist, dt, la, lb, seed=la + lb + fused)
+            G = max(G, ipm.ipm_merge_plan(la, lb, NAME[np.dtype(dt)])[0])
+            got = _merge_dev(ipm, dev, a, b, G)
+            want = orc.merge(a, b)
+            assert first_diff(got, want) is None, (la, lb, dist, G, first_diff(got, want))
+    finally:
+        ipm.ipm_set_fused_levels(4)
