@@ -510,7 +510,7 @@ def run_form(args, rank, world, torch, ipm, workloads, dev, stream, form):
                 "bytes_per_launch": m["merge_bytes"] + m["exchange_bytes"], "launch_ms": ms}
         launches = m["launches_per_step"] * args.steps
     else:
-        exch_note = "exchange_level_kernel (one launch per level), as in the plain form"
+        exch_note = "exchange_level_ws_kernel (one launch per level), as in the plain form"
         roof = {"bound": "hbm", "kernel": exch_note, "achieved": None, "peak": peak,
                 "unit": "GB/s", "frac": None, "peak_kind": f"{peak_kind} hbm_gbs",
                 "traffic": None}
@@ -651,7 +651,8 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
                    "l2": "inputs larger than L2 (%.1f GiB buffer)" % (n * w / 2**30)
                    if n * w > (129 << 20) else "L2-resident input (no flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "kernel": "exchange_level_kernel (one launch per level)",
+        "roofline": {"bound": "hbm",
+                     "kernel": "exchange_level_ws_kernel (one launch per exchange level)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
                      "traffic": None,

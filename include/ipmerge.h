@@ -161,8 +161,9 @@ ipm_status ipm_rotate(void *d_ptr, uint64_t len_x, uint64_t len_y, uint32_t elem
 
 /*
  * Algorithmic bytes the exchange levels of the last merge (or rotate) that used this
- * workspace moved: 2 bytes-per-element for every element of a one-pass exchange, 4 per
- * swapped pair of an LS block swap.  Synchronises `stream`.
+ * workspace moved (the levels that ran as exchanges; fused bottom levels move their
+ * data in the pair merge instead): 2 bytes-per-element for every element of a
+ * one-pass exchange, 4 per swapped pair of an LS block swap.  Synchronises `stream`.
  */
 ipm_status ipm_read_exchange_bytes(const void *d_ws, ipm_stream_t stream, uint64_t *out);
 
@@ -180,6 +181,15 @@ ipm_status ipm_read_exchange_bytes(const void *d_ws, ipm_stream_t stream, uint64
  */
 ipm_status ipm_set_fused_levels(uint32_t levels);
 ipm_status ipm_get_fused_levels(uint32_t *levels);
+
+/*
+ * Executor of the exchange levels (process-wide): 0 = every thread of a CTA takes
+ * every role in turn (claim, decode, stage, wait, store); 1 = warp-specialized (one
+ * producer warp claims, decodes and stages items while 15 consumer warps store the
+ * previous one; the default).  Both produce the same result; else
+ * IPM_ERR_INVALID_ARG.
+ */
+ipm_status ipm_set_exchange_engine(uint32_t engine);
 
 /*
  * Batched segmented merge: many independent in-place merges in one call.

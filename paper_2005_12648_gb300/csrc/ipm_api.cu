@@ -176,13 +176,13 @@ ipm_status merge_core(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_d
     }
     // a2: division stage, one exchange level at a time
     if (G > 0) {
-        {
-            PhaseScope ps(1, 1, stream);
-            IPM_TRY(launch_xplan_levels(split, n, G, pa, key, kv, sb, stream));
-        }
         // the last F levels are fused with the pair merge (clusters of 2^F CTAs)
         const uint32_t F =
             usable_fused_levels(key, kv, G < g_fused_levels ? G : g_fused_levels);
+        if (G > F) {
+            PhaseScope ps(1, 1, stream);
+            IPM_TRY(launch_xplan_levels(split, n, G, G - F, pa, key, kv, sb, stream));
+        }
         for (uint32_t l = 0; l + F < G; ++l) {
             PhaseScope ps(2, 1, stream);
             IPM_TRY(launch_exchange_level(buf, vals, key, n, l, pa, sb, stream));
@@ -306,7 +306,7 @@ ipm_status ipm_merge_rearrange(void *d_buf, void *d_vals, uint64_t len_a, uint64
     StatusBlock *sb = reinterpret_cast<StatusBlock *>(w);
     IPM_CUDA_TRY(cudaMemsetAsync(sb, 0, kStatusBytes, st));
     const XPlanArea pa = xplan_area_at(w + L.plan_off, G, n, key_dtype, kv);
-    IPM_TRY(launch_xplan_levels(d_split_a, n, G, pa, key_dtype, kv, sb, st));
+    IPM_TRY(launch_xplan_levels(d_split_a, n, G, G, pa, key_dtype, kv, sb, st));
     for (uint32_t l = 0; l < G; ++l)
         IPM_TRY(launch_exchange_level(d_buf, static_cast<uint32_t *>(d_vals), key_dtype, n, l,
                                       pa, sb, st));
@@ -518,6 +518,12 @@ ipm_status ipm_set_fused_levels(uint32_t levels) {
 ipm_status ipm_get_fused_levels(uint32_t *levels) {
     if (levels == nullptr) return IPM_ERR_INVALID_ARG;
     *levels = g_fused_levels;
+    return IPM_OK;
+}
+
+ipm_status ipm_set_exchange_engine(uint32_t engine) {
+    if (engine > 1) return IPM_ERR_INVALID_ARG;
+    g_exchange_engine = engine;
     return IPM_OK;
 }
 

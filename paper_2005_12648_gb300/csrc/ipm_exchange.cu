@@ -129,10 +129,6 @@ __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
     return v;
 }
 
-__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 // "Reads done" flags.  A flag is stored after every thread of the CTA has consumed
 // the registers its loads filled (so the loads have returned) and a __syncthreads;
 // the reads are then over, and a relaxed store suffices: it does not wait for the
@@ -147,24 +143,6 @@ __device__ __forceinline__ uint32_t ld_flag(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
-}
-
-// Thread 0: wait until flags[lo..hi] all reach tag.  False on timeout.
-__device__ bool wait_flags(const uint32_t *flags, uint32_t lo, uint32_t hi, uint32_t tag) {
-    unsigned long long t0 = 0;
-    for (uint32_t q = lo; q <= hi; ++q) {
-        uint32_t it = 0;
-        while (ld_flag(flags + q) < tag) {
-            if ((++it & 63u) == 0) {
-                const unsigned long long now = globaltimer_ns();
-                if (t0 == 0)
-                    t0 = now;
-                else if (now - t0 > kWaitLimitNs)
-                    return false;
-            }
-        }
-    }
-    return true;
 }
 
 // Thread 0: wait until *ctr >= target.  False on timeout.
@@ -266,50 +244,13 @@ __device__ bool wait_flag_range_poll(const uint32_t *flags, uint32_t lo, uint32_
     return true;
 }
 
-// Decode ticket t of a level plan into an item.  Every thread computes the same item.
-__device__ __forceinline__ bool decode_item(const XParams &prm, uint32_t t, uint32_t &rot_hint,
-                                            const uint32_t *pf, const RotPlan *plans,
-                                            uint32_t nrot, uint64_t n, Item &it) {
-    // the exchange holding t is the last one with pf[r] <= t.  A CTA's tickets only
-    // grow: the block probes the 512 exchanges after the previous one in one coalesced
-    // round (pf is non-decreasing, so the hits form a prefix); longer jumps bisect.
-    if (pf[rot_hint + 1] <= t) {
-        const uint32_t cand = rot_hint + 1 + threadIdx.x;
-        const int cnt = __syncthreads_count(cand <= nrot && pf[cand] <= t);
-        if (cnt < int(blockDim.x)) {
-            rot_hint += uint32_t(cnt);
-        } else {
-            uint32_t lo = rot_hint + blockDim.x, hi = nrot;
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (pf[mid] <= t)
-                    lo = mid;
-                else
-                    hi = mid;
-            }
-            rot_hint = lo;
-        }
-    }
-    const uint32_t r = rot_hint;
-    const uint32_t j = t - pf[r];
-    const RotPlan q = plans[r];
-    XPhase ph;
-    uint64_t s = q.s, a = q.a, b = q.b;
-    uint32_t before = 0;
-    bool found = false;
-    while (x_phase(prm, s, a, b, ph)) {
-        if (j < before + ph.items()) {
-            found = true;
-            break;
-        }
-        before += ph.items();
-        if (ph.final_phase) break;
-        x_after_step(ph, s, a, b);
-    }
+// Item j - before of phase ph of exchange r (ticket t; fb = the flag index of the
+// phase's item 0): its moves and the flags its stores depend on.
+__device__ __forceinline__ void decode_phase_item(const XParams &prm, const XPhase &ph,
+                                                  uint32_t t, uint32_t r, uint32_t j,
+                                                  uint32_t before, uint32_t fb, Item &it) {
     const uint64_t m = ph.a + ph.b;
-    if (!found || ph.s > n || m > n - ph.s) return false;
     const uint32_t jj = j - before;
-    const uint32_t fb = pf[r] + before;  // flag of item 0 of this phase
     it.ticket = t;
     it.r = r;
     it.before = before;
@@ -389,6 +330,51 @@ __device__ __forceinline__ bool decode_item(const XParams &prm, uint32_t t, uint
             }
         }
     }
+}
+
+// Decode ticket t of a level plan into an item.  Every thread computes the same item.
+__device__ __forceinline__ bool decode_item(const XParams &prm, uint32_t t, uint32_t &rot_hint,
+                                            const uint32_t *pf, const RotPlan *plans,
+                                            uint32_t nrot, uint64_t n, Item &it) {
+    // the exchange holding t is the last one with pf[r] <= t.  A CTA's tickets only
+    // grow: the block probes the 512 exchanges after the previous one in one coalesced
+    // round (pf is non-decreasing, so the hits form a prefix); longer jumps bisect.
+    if (pf[rot_hint + 1] <= t) {
+        const uint32_t cand = rot_hint + 1 + threadIdx.x;
+        const int cnt = __syncthreads_count(cand <= nrot && pf[cand] <= t);
+        if (cnt < int(blockDim.x)) {
+            rot_hint += uint32_t(cnt);
+        } else {
+            uint32_t lo = rot_hint + blockDim.x, hi = nrot;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (pf[mid] <= t)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            rot_hint = lo;
+        }
+    }
+    const uint32_t r = rot_hint;
+    const uint32_t j = t - pf[r];
+    const RotPlan q = plans[r];
+    XPhase ph;
+    uint64_t s = q.s, a = q.a, b = q.b;
+    uint32_t before = 0;
+    bool found = false;
+    while (x_phase(prm, s, a, b, ph)) {
+        if (j < before + ph.items()) {
+            found = true;
+            break;
+        }
+        before += ph.items();
+        if (ph.final_phase) break;
+        x_after_step(ph, s, a, b);
+    }
+    const uint64_t m = ph.a + ph.b;
+    if (!found || ph.s > n || m > n - ph.s) return false;
+    decode_phase_item(prm, ph, t, r, j, before, pf[r] + before, it);
     return true;
 }
 
@@ -708,11 +694,418 @@ __global__ void __launch_bounds__(512, 1)
     }
 }
 
-template <typename E, bool KV>
+// ---------------------------------------------------------------------------------
+// Warp-specialized executor: warp 0 is the producer (claims tickets, decodes items,
+// waits for an item's earlier LS steps, stages its blocks into a free stage), warps
+// 1..15 are the consumers (publish "reads done", wait for the flags their stores
+// depend on, store, release the stage).  Two stages; the producer keeps the next
+// item's load in flight while the consumers store the current one, so ticket claims
+// and decoding stay off the consumers' path.  Holder items (which wait on later tickets
+// of their own exchange) are drained before the producer claims another ticket, and a
+// SINGLE exchange (both stages) waits for both stages to drain: the same
+// deadlock-freedom argument as the single-role executor.
+// ---------------------------------------------------------------------------------
+
+constexpr uint32_t kWsConsumers = 480;  // threads 32..511
+
+// Warp version of decode_item: the exchange holding ticket t by a 32-wide probe of the
+// next exchanges, then a 33-way bracket search for longer jumps.
+__device__ __forceinline__ bool decode_item_warp(const XParams &prm, uint32_t t,
+                                                 uint32_t &rot_hint, const uint32_t *pf,
+                                                 const RotPlan *plans, uint32_t nrot,
+                                                 uint64_t n, Item &it) {
+    const uint32_t lane = threadIdx.x & 31u;
+    if (pf[rot_hint + 1] <= t) {
+        uint32_t lo = rot_hint + 1;  // pf[lo] <= t; pf[nrot] = total > t
+        const uint32_t cand = lo + lane;
+        const bool p = cand <= nrot && pf[cand] <= t;
+        const int c = __popc(__ballot_sync(0xffffffffu, p));
+        if (c < 32) {
+            rot_hint = lo + uint32_t(c) - 1;
+        } else {
+            lo += 31;
+            uint32_t hi = nrot;
+            while (hi - lo > 1) {
+                const uint32_t R = hi - lo;
+                const uint32_t m = lo + uint32_t((uint64_t(R) * (lane + 1)) / 33);
+                const bool q = pf[m] <= t;
+                const int cc = __popc(__ballot_sync(0xffffffffu, q));
+                const uint32_t m_lo = __shfl_sync(0xffffffffu, m, cc > 0 ? cc - 1 : 0);
+                const uint32_t m_hi = __shfl_sync(0xffffffffu, m, cc < 32 ? cc : 31);
+                if (cc > 0) lo = m_lo;
+                if (cc < 32) hi = m_hi;
+            }
+            rot_hint = lo;
+        }
+    }
+    const uint32_t r = rot_hint;
+    const uint32_t j = t - pf[r];
+    const RotPlan q = plans[r];
+    XPhase ph;
+    uint64_t s = q.s, a = q.a, b = q.b;
+    uint32_t before = 0;
+    bool found = false;
+    while (x_phase(prm, s, a, b, ph)) {
+        if (j < before + ph.items()) {
+            found = true;
+            break;
+        }
+        before += ph.items();
+        if (ph.final_phase) break;
+        x_after_step(ph, s, a, b);
+    }
+    const uint64_t m = ph.a + ph.b;
+    if (!found || ph.s > n || m > n - ph.s) return false;
+    decode_phase_item(prm, ph, t, r, j, before, pf[r] + before, it);
+    return true;
+}
+
+// Producer warp: stage the item's source blocks (TMA bodies by lane 0, heads and tails
+// by lanes 8i..8i+7 (keys) and 16+8i.. (values) written straight to shared memory),
+// then arrive on the stage's "full" barrier.
+template <typename K, bool KV>
+__device__ __forceinline__ void stage_load_ws(const Item &it, const K *buf, const uint32_t *vals,
+                                              unsigned char *stage, unsigned char *base,
+                                              uint64_t *full) {
+    using C = XCfg<K, KV>;
+    K *sk = stage_keys<K, KV>(it, stage, base);
+    uint32_t *sv = stage_vals<K, KV>(it, stage, base);
+    const uint32_t lane = threadIdx.x & 31u;
+    if (lane == 0) {
+        uint32_t tx = 0;
+        for (uint32_t i = 0; i < it.nmoves; ++i) {
+            const Geo<int(sizeof(K))> gk(buf + it.mv[i].src, uint32_t(it.mv[i].len));
+            tx += gk.body * uint32_t(sizeof(K));
+            if (KV) {
+                const Geo<4> gv(vals + it.mv[i].src, uint32_t(it.mv[i].len));
+                tx += gv.body * 4u;
+            }
+        }
+        mbar_expect_tx(full, tx);
+    }
+    __syncwarp();
+    for (uint32_t i = 0; i < it.nmoves; ++i) {
+        const Move &mv = it.mv[i];
+        const uint32_t len = uint32_t(mv.len);
+        const K *g = buf + mv.src;
+        const Geo<int(sizeof(K))> gk(g, len);
+        if (lane == 0 && gk.body)
+            bulk_load(sk + i * C::kSlotK + gk.off + gk.head, g + gk.head,
+                      gk.body * uint32_t(sizeof(K)), full);
+        if (lane >= 8 * i && lane < 8 * i + 8) {
+            const uint32_t e = lane - 8 * i;
+            const uint32_t ntail = len - gk.tail_start;
+            uint32_t jj = ~0u;
+            if (e < 4 && e < gk.head)
+                jj = e;
+            else if (e >= 4 && e - 4 < ntail)
+                jj = gk.tail_start + (e - 4);
+            if (jj != ~0u) sk[i * C::kSlotK + gk.off + jj] = __ldcg(g + jj);
+        }
+        if (KV) {
+            const uint32_t *gv = vals + mv.src;
+            const Geo<4> gvv(gv, len);
+            if (lane == 0 && gvv.body)
+                bulk_load(sv + i * C::kSlotV + gvv.off + gvv.head, gv + gvv.head, gvv.body * 4u,
+                          full);
+            if (lane >= 16 + 8 * i && lane < 24 + 8 * i) {
+                const uint32_t e = lane - 16 - 8 * i;
+                const uint32_t ntail = len - gvv.tail_start;
+                uint32_t jj = ~0u;
+                if (e < 4 && e < gvv.head)
+                    jj = e;
+                else if (e >= 4 && e - 4 < ntail)
+                    jj = gvv.tail_start + (e - 4);
+                if (jj != ~0u) sv[i * C::kSlotV + gvv.off + jj] = __ldcg(gv + jj);
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(full);
+}
+
+// dst[0, len) = src[0, len) by the consumer threads (ctid < kWsConsumers).
+template <typename T>
+__device__ __forceinline__ void copy_out_ws(const T *src, T *dst, uint32_t len, uint32_t ctid) {
+    constexpr uint32_t U = 8, NT = kWsConsumers;
+    uint32_t j0 = 0;
+    for (; j0 + U * NT <= len; j0 += U * NT) {
+        T v[U];
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) v[u] = src[j0 + u * NT + ctid];
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) dst[j0 + u * NT + ctid] = v[u];
+    }
+    for (uint32_t j = j0 + ctid; j < len; j += NT) dst[j] = src[j];
+}
+
+template <typename K, bool KV>
+__device__ __forceinline__ void stage_store_ws(const Item &it, K *buf, uint32_t *vals,
+                                               unsigned char *stage, unsigned char *base,
+                                               uint32_t ctid) {
+    using C = XCfg<K, KV>;
+    const K *sk = stage_keys<K, KV>(it, stage, base);
+    const uint32_t *sv = stage_vals<K, KV>(it, stage, base);
+    if (it.single) {  // the whole exchange [X|Y] is staged; write it rotated by |X|
+        const Move &mv = it.mv[0];
+        const Geo<int(sizeof(K))> gk(buf + mv.src, uint32_t(mv.len));
+        const uint32_t m = uint32_t(it.single_m), a = uint32_t(it.single_a);
+        const K *k0 = sk + gk.off;
+        K *dst = buf + mv.dst;
+        for (uint32_t t = ctid; t < m; t += kWsConsumers) {
+            uint32_t src = t + a;
+            if (src >= m) src -= m;
+            dst[t] = k0[src];
+        }
+        if (KV) {
+            const Geo<4> gv(vals + mv.src, uint32_t(mv.len));
+            const uint32_t *v0 = sv + gv.off;
+            uint32_t *vd = vals + mv.dst;
+            for (uint32_t t = ctid; t < m; t += kWsConsumers) {
+                uint32_t src = t + a;
+                if (src >= m) src -= m;
+                vd[t] = v0[src];
+            }
+        }
+        return;
+    }
+    for (uint32_t i = 0; i < it.nmoves; ++i) {
+        const Move &mv = it.mv[i];
+        const uint32_t len = uint32_t(mv.len);
+        const Geo<int(sizeof(K))> gk(buf + mv.src, len);
+        copy_out_ws<K>(sk + i * C::kSlotK + gk.off, buf + mv.dst, len, ctid);
+        if (KV) {
+            const Geo<4> gv(vals + mv.src, len);
+            copy_out_ws<uint32_t>(sv + i * C::kSlotV + gv.off, vals + mv.dst, len, ctid);
+        }
+    }
+}
+
+__device__ __forceinline__ void consumers_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kWsConsumers) : "memory");
+}
+
+struct WsShared {
+    Item item[2];
+    uint32_t end[2];  // the producer's end marker for the stage
+    int abort;        // set by any role on an error
+    // the consumers' decisions, written by the lead before the barrier they follow;
+    // one variable per barrier, so a slow consumer never sees the next one's value
+    int stop_wait, stop_deps;
+};
+
+// Lead consumer: wait until flags[lo..hi] all reach tag (empty range: true).  While
+// waiting, publish the next stage's item flag as soon as that stage's data has landed
+// (its descriptor is read only after the barrier shows the producer's arrival).
+// False on timeout.
+__device__ bool ws_wait_deps(const uint32_t *flags, uint32_t lo, uint32_t hi, uint32_t tag,
+                             uint64_t *nbar, uint32_t nparity, const WsShared *sh,
+                             uint32_t ns, uint32_t *wflags, bool &next_pub) {
+    auto poll_next = [&]() {
+        if (!next_pub && mbar_try_wait(nbar, nparity)) {
+            const volatile WsShared *v = sh;
+            if (!v->end[ns] && v->item[ns].flag) st_flag(wflags + v->item[ns].ticket, tag);
+            next_pub = true;
+        }
+    };
+    poll_next();
+    unsigned long long t0 = 0;
+    for (uint32_t q = lo; q <= hi && lo <= hi; ++q) {
+        uint32_t it = 0;
+        while (ld_flag(flags + q) < tag) {
+            poll_next();
+            if ((++it & 63u) == 0) {
+                const unsigned long long now = globaltimer_ns();
+                if (t0 == 0)
+                    t0 = now;
+                else if (now - t0 > kWaitLimitNs)
+                    return false;
+            }
+        }
+    }
+    return true;
+}
+
+template <typename K, bool KV>
+__global__ void __launch_bounds__(512, 1)
+    exchange_level_ws_kernel(K *__restrict__ buf, uint32_t *__restrict__ vals, uint64_t n,
+                             const RotPlan *__restrict__ plans, const uint32_t *__restrict__ pf,
+                             uint32_t nrot, uint32_t *__restrict__ flags,
+                             uint32_t *__restrict__ join, uint32_t tag, uint32_t ctr_index,
+                             StatusBlock *sb) {
+    using C = XCfg<K, KV>;
+    extern __shared__ __align__(128) unsigned char xsmem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(xsmem + 2 * C::kStageSize);
+    uint64_t *empty = full + 2;
+    __shared__ WsShared sh;
+    if (sb != nullptr && *((volatile unsigned int *)&sb->done)) return;
+    const uint32_t tid = threadIdx.x;
+    const uint32_t total = pf[nrot];
+    if (tid == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        mbar_init(&empty[0], 1);
+        mbar_init(&empty[1], 1);
+        mbar_fence_init();
+        sh.abort = 0;
+        sh.end[0] = sh.end[1] = 0;
+    }
+    __syncthreads();
+
+    if (tid < 32) {
+        // ------------------------------------------------------------- producer warp
+        const XParams prm = C::params();
+        const uint32_t lane = tid;
+        uint32_t *ctr = &sb->counters[ctr_index];
+        uint32_t issued[2] = {0, 0}, drained[2] = {0, 0};
+        uint32_t arrivals[2] = {0, 0};  // phases of full[q] the producer has started
+        uint32_t rot = 0;
+        uint32_t st = 0;
+        // wait until every item issued to stage q has been released by the consumers
+        auto drain = [&](uint32_t q) -> bool {
+            while (drained[q] < issued[q]) {
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait_bounded(&empty[q], drained[q] & 1u);
+                ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+                if (!ok) return false;
+                ++drained[q];
+            }
+            return true;
+        };
+        for (;;) {
+            uint32_t t = 0;
+            if (lane == 0) t = atomicAdd(ctr, 1u);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            bool fail = false;
+            Item it;
+            if (t < total && !decode_item_warp(prm, t, rot, pf, plans, nrot, n, it)) {
+                if (lane == 0) set_status(sb, IPM_ERR_DEVICE);
+                fail = true;
+            }
+            if (t >= total || fail || *((volatile int *)&sh.abort)) {
+                // end marker for the consumers in the next stage
+                if (drain(st)) {
+                    if (lane == 0) {
+                        sh.end[st] = 1;
+                        mbar_arrive(&full[st]);
+                    }
+                    ++arrivals[st];
+                } else if (lane == 0) {
+                    set_status(sb, IPM_ERR_TIMEOUT);
+                    sh.abort = 1;
+                }
+                break;
+            }
+            bool ok = drain(st);
+            if (ok && it.single) ok = drain(st ^ 1u);
+            if (ok && it.before > 0) {  // the item's earlier LS steps must be complete
+                bool w = true;
+                if (lane == 0) w = wait_count(join + it.r, it.before);
+                ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+            }
+            if (!ok) {
+                if (lane == 0) {
+                    set_status(sb, IPM_ERR_TIMEOUT);
+                    sh.abort = 1;
+                }
+                break;
+            }
+            if (lane == 0) {
+                sh.item[st] = it;
+                sh.end[st] = 0;
+            }
+            __syncwarp();
+            unsigned char *stage = xsmem + (st ? C::kStageSize : 0);
+            stage_load_ws<K, KV>(it, buf, vals, stage, xsmem, &full[st]);
+            ++arrivals[st];
+            ++issued[st];
+            if (it.single) ++issued[st ^ 1u];  // the consumers release both stages
+            // a stash holder waits on later tickets of its own exchange: claim no ticket
+            // that could be parked behind it
+            if (it.holder && !drain(st)) {
+                if (lane == 0) {
+                    set_status(sb, IPM_ERR_TIMEOUT);
+                    sh.abort = 1;
+                }
+                break;
+            }
+            st ^= 1u;
+        }
+        // leave only once every bulk copy this warp issued has landed (no copy may
+        // write the CTA's shared memory after it exits)
+        if (lane == 0)
+            for (uint32_t q = 0; q < 2; ++q)
+                if (arrivals[q] > 0) (void)mbar_wait_bounded(&full[q], (arrivals[q] - 1) & 1u);
+        return;
+    }
+
+    // ----------------------------------------------------------------- consumers
+    // Only the lead waits on the stage barrier and reads the shared error / end state;
+    // its decisions are read by all consumers after a barrier, so they always leave the
+    // loop together.
+    const uint32_t ctid = tid - 32;
+    const bool lead = ctid == 0;
+    uint32_t fullph[2] = {0, 0};
+    uint32_t st = 0;
+    bool cur_pub = false;  // lead: the current item's flag was published early
+    for (;;) {
+        if (lead) {
+            int stop = 0;
+            if (!mbar_wait_bounded(&full[st], fullph[st])) {
+                set_status(sb, IPM_ERR_TIMEOUT);
+                sh.abort = 1;
+                stop = 1;
+            } else if (*((volatile uint32_t *)&sh.end[st]) || *((volatile int *)&sh.abort)) {
+                stop = 1;
+            }
+            sh.stop_wait = stop;
+        }
+        consumers_sync();  // the stage's data and descriptor are visible to all consumers
+        fullph[st] ^= 1u;
+        if (sh.stop_wait) break;
+        const Item it = sh.item[st];
+        if (lead) {
+            // reads done: the data is on chip
+            if (it.flag && !cur_pub) st_flag(flags + it.ticket, tag);
+            // wait for the flags this item's stores depend on, publishing the next
+            // stage's flag as soon as its data lands
+            const uint32_t ns = st ^ 1u;
+            bool next_pub = false;
+            bool w = ws_wait_deps(flags, it.dp.lo0, it.dp.hi0, tag, &full[ns], fullph[ns], &sh,
+                                  ns, flags, next_pub);
+            if (w)
+                w = ws_wait_deps(flags, it.dp.lo1, it.dp.hi1, tag, &full[ns], fullph[ns], &sh,
+                                 ns, flags, next_pub);
+            cur_pub = next_pub;
+            int stop = 0;
+            if (!w) {
+                set_status(sb, IPM_ERR_TIMEOUT);
+                sh.abort = 1;
+                stop = 1;
+            }
+            sh.stop_deps = stop;
+        }
+        consumers_sync();
+        if (sh.stop_deps) break;
+        unsigned char *stage = xsmem + (st ? C::kStageSize : 0);
+        stage_store_ws<K, KV>(it, buf, vals, stage, xsmem, ctid);
+        if (!it.final_phase) __threadfence();  // an LS step: writes visible device-wide
+        fence_proxy_async_smem();  // our reads of the stage precede the next bulk copy into it
+        consumers_sync();
+        if (lead) {
+            if (!it.final_phase) atomicAdd(join + it.r, 1u);
+            mbar_arrive(&empty[st]);
+            if (it.single) mbar_arrive(&empty[st ^ 1u]);
+        }
+        st ^= 1u;
+    }
+}
+
+template <typename E, bool KV, bool WS>
 ipm_status exchange_level_t(void *buf, uint32_t *vals, uint64_t n, uint32_t l,
                             XPlanArea pa, StatusBlock *sb, cudaStream_t stream) {
     using C = XCfg<E, KV>;
-    auto kern = exchange_level_kernel<E, KV>;
+    auto kern = WS ? exchange_level_ws_kernel<E, KV> : exchange_level_kernel<E, KV>;
     static int grid = 0;
     if (grid == 0) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -791,16 +1184,17 @@ XPlanArea xplan_area_at(void *base, uint32_t G, uint64_t n, ipm_dtype key, bool 
     return pa;
 }
 
-ipm_status launch_xplan_levels(const uint64_t *split, uint64_t n, uint32_t G, XPlanArea pa,
-                               ipm_dtype key, bool with_values, StatusBlock *sb,
-                               cudaStream_t stream) {
-    if (G == 0) return IPM_OK;
+ipm_status launch_xplan_levels(const uint64_t *split, uint64_t n, uint32_t G,
+                               uint32_t levels, XPlanArea pa, ipm_dtype key, bool with_values,
+                               StatusBlock *sb, cudaStream_t stream) {
+    if (G == 0 || levels == 0) return IPM_OK;
+    if (levels > G) levels = G;
     // completion counters and read flags start at zero on every call
     IPM_CUDA_TRY(cudaMemsetAsync(pa.join, 0, pa.zero_bytes, stream));
     const uint32_t elem = uint32_t(dtype_bytes(key)) + (with_values ? 4u : 0u);
-    xplan_levels_kernel<<<G, kPlanThreads, 0, stream>>>(split, n, G, pa,
-                                                        exchange_params(key, with_values),
-                                                        elem, sb);
+    xplan_levels_kernel<<<levels, kPlanThreads, 0, stream>>>(split, n, G, pa,
+                                                             exchange_params(key, with_values),
+                                                             elem, sb);
     return last_launch_status();
 }
 
@@ -811,19 +1205,28 @@ ipm_status launch_xplan_single(uint64_t lx, uint64_t ly, XPlanArea pa, ipm_dtype
     return last_launch_status();
 }
 
+uint32_t g_exchange_engine = 1;
+
 ipm_status launch_exchange_level(void *buf, uint32_t *vals, ipm_dtype key, uint64_t n,
                                  uint32_t l, XPlanArea pa, StatusBlock *sb,
                                  cudaStream_t stream) {
     const bool kv = vals != nullptr;
+    const bool ws = g_exchange_engine == 1;
     switch (key) {
     case IPM_INT32:
     case IPM_UINT32:
     case IPM_FLOAT32:
-        return kv ? exchange_level_t<int32_t, true>(buf, vals, n, l, pa, sb, stream)
-                  : exchange_level_t<int32_t, false>(buf, vals, n, l, pa, sb, stream);
+        if (ws)
+            return kv ? exchange_level_t<int32_t, true, true>(buf, vals, n, l, pa, sb, stream)
+                      : exchange_level_t<int32_t, false, true>(buf, vals, n, l, pa, sb, stream);
+        return kv ? exchange_level_t<int32_t, true, false>(buf, vals, n, l, pa, sb, stream)
+                  : exchange_level_t<int32_t, false, false>(buf, vals, n, l, pa, sb, stream);
     case IPM_UINT64:
-        return kv ? exchange_level_t<uint64_t, true>(buf, vals, n, l, pa, sb, stream)
-                  : exchange_level_t<uint64_t, false>(buf, vals, n, l, pa, sb, stream);
+        if (ws)
+            return kv ? exchange_level_t<uint64_t, true, true>(buf, vals, n, l, pa, sb, stream)
+                      : exchange_level_t<uint64_t, false, true>(buf, vals, n, l, pa, sb, stream);
+        return kv ? exchange_level_t<uint64_t, true, false>(buf, vals, n, l, pa, sb, stream)
+                  : exchange_level_t<uint64_t, false, false>(buf, vals, n, l, pa, sb, stream);
     }
     return IPM_ERR_UNSUPPORTED_DTYPE;
 }

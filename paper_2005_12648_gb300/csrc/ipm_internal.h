@@ -36,14 +36,19 @@ ipm_status launch_splits(const void *buf, uint64_t la, uint64_t lb, ipm_dtype ke
                          uint64_t P, uint64_t *split, const StatusBlock *sb,
                          cudaStream_t stream);
 
-// Plans (and zeroed flags) of all G levels from a split table with P = 2^G.
-ipm_status launch_xplan_levels(const uint64_t *split, uint64_t n, uint32_t G, XPlanArea pa,
-                               ipm_dtype key, bool with_values, StatusBlock *sb,
-                               cudaStream_t stream);
+// Plans (and zeroed flags) of the first `levels` of the G levels of a split table with
+// P = 2^G; only the planned levels add to the status block's exchange bytes.
+ipm_status launch_xplan_levels(const uint64_t *split, uint64_t n, uint32_t G,
+                               uint32_t levels, XPlanArea pa, ipm_dtype key, bool with_values,
+                               StatusBlock *sb, cudaStream_t stream);
 
 // Plan of a single exchange [X|Y] at offset 0 (level 0 of a G = 1 layout).
 ipm_status launch_xplan_single(uint64_t lx, uint64_t ly, XPlanArea pa, ipm_dtype key,
                                cudaStream_t stream);
+
+// Exchange executor of launch_exchange_level: 0 = every thread in every role,
+// 1 = warp-specialized (a producer warp stages, 15 consumer warps store).
+extern uint32_t g_exchange_engine;
 
 // The exchanges of level l, one persistent launch.
 ipm_status launch_exchange_level(void *buf, uint32_t *vals, ipm_dtype key, uint64_t n,

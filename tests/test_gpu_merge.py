@@ -208,3 +208,49 @@ def test_fused_bottom_levels_match_oracle(ipm, dev, orc, fused, dt):
             assert first_diff(got, want) is None, (la, lb, dist, G, first_diff(got, want))
     finally:
         ipm.ipm_set_fused_levels(4)
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_exchange_engines_match_oracle(ipm, dev, orc, engine):
+    """Both exchange executors (all threads in every role; producer warp + consumer
+    warps) on rotations of every phase kind (SINGLE, SWAP, PAIR, SHIFT, LS steps) and on
+    whole merges (keys and key-value), against the oracle."""
+    import torch
+
+    ipm.ipm_set_exchange_engine(engine)
+    try:
+        for elem, dt in [(4, np.uint32), (8, np.uint64)]:
+            for lx, ly in [(1, 1), (5000, 4000), (65_536, 65_536), (1 << 20, (1 << 20) + 77),
+                           (3_000_017, 260_001), (260_001, 2_900_011), (1_000_003, 700_001),
+                           (700_001, 1_000_003), (4_000_037, 3_700_019), (999_983, 7919)]:
+                x = W.make_pair("uniform", dt, lx + ly, 0, seed=lx ^ ly)[0]
+                d = to_dev(x, dev)
+                ws = ipm.workspace(ipm.ipm_rotate_workspace_bytes(lx, ly, elem), dev)
+                ipm.ipm_rotate(d, lx, ly, elem, ws)
+                torch.cuda.synchronize()
+                assert ipm.ipm_read_device_status(ws) == 0
+                assert np.array_equal(bits(from_dev(d, dt)), bits(np.roll(x, -lx))), (lx, ly)
+        for dist, dt, la, lb in [("uniform", np.int32, 3_000_017, 2_900_011),
+                                 ("dup16", np.uint32, 1_000_003, 700_001),
+                                 ("revdisjoint", np.int32, 900_001, 1_200_007),
+                                 ("uniform", np.uint64, 1_500_007, 1_400_011)]:
+            for fused in (0, 4):
+                ipm.ipm_set_fused_levels(fused)
+                a, b = W.make_pair(dist, dt, la, lb, seed=la)
+                got = _merge_dev(ipm, dev, a, b)
+                assert first_diff(got, orc.merge(a, b)) is None, (dist, la, lb, fused)
+        ipm.ipm_set_fused_levels(4)
+        ka, kb = W.make_pair("zipf", np.uint32, 2_000_003, 1_700_001, seed=3)
+        keys = to_dev(np.concatenate([ka, kb]), dev)
+        vals = torch.arange(ka.size + kb.size, dtype=torch.int32, device=dev)
+        ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(ka.size, kb.size, "uint32", True), dev)
+        ipm.ipm_merge_inplace_kv(keys, vals, ka.size, kb.size, "uint32", ws)
+        torch.cuda.synchronize()
+        assert ipm.ipm_read_device_status(ws) == 0
+        wk, wv = orc.merge_kv(ka, np.arange(ka.size, dtype=np.uint32), kb,
+                              np.arange(ka.size, ka.size + kb.size, dtype=np.uint32))
+        assert np.array_equal(from_dev(keys, np.uint32), wk)
+        assert np.array_equal(vals.cpu().numpy().view(np.uint32), wv)
+    finally:
+        ipm.ipm_set_exchange_engine(1)
+        ipm.ipm_set_fused_levels(4)
