@@ -366,7 +366,7 @@ ipm_status ipm_merge_inplace_learned(void *d_buf, uint64_t len_a, uint64_t len_b
  * Some callers cannot call cudaMalloc (another framework holds nearly all device
  * memory in its own pool; a latency-critical path cannot afford an allocation and the
  * synchronisation of a later cudaFree; a plain C caller has no allocator to borrow).
- * This entry point takes no workspace: its scratch is a 4 MiB array compiled into the
+ * This entry point takes no workspace: its scratch is an 8 MiB array compiled into the
  * library, which every GPU that loads the library keeps until the process exits.
  *   - Limit: at most 2^15 pairs, i.e. len_a + len_b <= 2^15 * tile capacity
  *     (~1.1e9 4-byte keys, ~5.5e8 8-byte keys).  Larger inputs return

@@ -267,7 +267,7 @@ def ipm_read_device_status(ws, stream=None) -> int:
 
 def ipm_merge_inplace_noalloc(buf, len_a: int, len_b: int, key_dtype, stream=None) -> None:
     """The merge for callers that cannot allocate device memory: no workspace
-    argument; the library's own fixed 4 MiB scratch array is used instead (at most
+    argument; the library's own fixed 8 MiB scratch array is used instead (at most
     2^15 pairs per call, keys only; calls that overlap on the GPU race on it)."""
     _check(load().ipm_merge_inplace_noalloc(_ptr(buf), len_a, len_b, _dt(key_dtype),
                                             _stream(stream)), "ipm_merge_inplace_noalloc")

@@ -154,13 +154,20 @@ ipm_status merge_core(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_d
         return IPM_ERR_ALIGNMENT;
     if (!aligned(ws, 256)) return IPM_ERR_ALIGNMENT;
     const uint64_t n = la + lb;
-    const MergeLayout L = merge_layout(G, n, key, kv);
+    // The fused path (the last F levels done by thread-block clusters of half-size
+    // tiles) splits one level deeper: every pair then fits the half tile.
+    const uint32_t F = G + 1 <= kMaxLog2Pairs + 1
+                           ? usable_fused_levels(key, kv, g_fused_levels < G + 1 ? g_fused_levels
+                                                                                 : G + 1)
+                           : 0;
+    const uint32_t Gs = F > 0 ? G + 1 : G;  // depth of the split table
+    const MergeLayout L = merge_layout(Gs, n, key, kv);
     if (ws_bytes < L.total) return IPM_ERR_WORKSPACE;
     char *w = static_cast<char *>(ws);
     StatusBlock *sb = reinterpret_cast<StatusBlock *>(w);
     uint64_t *split = reinterpret_cast<uint64_t *>(w + L.split_off);
-    const XPlanArea pa = xplan_area_at(w + L.plan_off, G, n, key, kv);
-    const uint64_t P = uint64_t(1) << G;
+    const XPlanArea pa = xplan_area_at(w + L.plan_off, Gs, n, key, kv);
+    const uint64_t P = uint64_t(1) << Gs;
 
     {
         PhaseScope ps(model ? 6 : 0, 2, stream);
@@ -174,30 +181,20 @@ ipm_status merge_core(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_d
         else
             IPM_TRY(launch_splits(buf, la, lb, key, P, split, sb, stream));
     }
-    // a2: division stage, one exchange level at a time
-    if (G > 0) {
-        // the last F levels are fused with the pair merge (clusters of 2^F CTAs)
-        const uint32_t F =
-            usable_fused_levels(key, kv, G < g_fused_levels ? G : g_fused_levels);
-        if (G > F) {
-            PhaseScope ps(1, 1, stream);
-            IPM_TRY(launch_xplan_levels(split, n, G, G - F, pa, key, kv, sb, stream));
-        }
-        for (uint32_t l = 0; l + F < G; ++l) {
-            PhaseScope ps(2, 1, stream);
-            IPM_TRY(launch_exchange_level(buf, vals, key, n, l, pa, sb, stream));
-        }
-        if (F > 0) {
-            PhaseScope ps(3, 1, stream);
-            return launch_cluster_merge(buf, vals, la, lb, key, split, G, F, sb, stream);
-        }
+    // a2: division stage, one exchange level at a time; the last F levels are fused
+    // with the pair merge (clusters of 2^F CTAs)
+    if (Gs > F) {
+        PhaseScope ps(1, 1, stream);
+        IPM_TRY(launch_xplan_levels(split, n, Gs, Gs - F, pa, key, kv, sb, stream));
     }
-    // a3: per-pair merge
-    {
-        PhaseScope ps(3, 1, stream);
-        IPM_TRY(launch_tile_merge(buf, vals, la, lb, key, split, G, sb, stream));
+    for (uint32_t l = 0; l + F < Gs; ++l) {
+        PhaseScope ps(2, 1, stream);
+        IPM_TRY(launch_exchange_level(buf, vals, key, n, l, pa, sb, stream));
     }
-    return IPM_OK;
+    // a3: pair merge (fused with the last F levels when F > 0)
+    PhaseScope ps(3, 1, stream);
+    if (F > 0) return launch_cluster_merge(buf, vals, la, lb, key, split, Gs, F, sb, stream);
+    return launch_tile_merge(buf, vals, la, lb, key, split, G, sb, stream);
 }
 
 }  // namespace
@@ -245,7 +242,8 @@ ipm_status ipm_merge_workspace_bytes(uint64_t len_a, uint64_t len_b, ipm_dtype k
     if (bytes == nullptr) return IPM_ERR_INVALID_ARG;
     uint32_t G = 0;
     IPM_TRY(check_merge_args(len_a, len_b, key_dtype, with_values != 0, log2_pairs, &G));
-    *bytes = merge_layout(G, len_a + len_b, key_dtype, with_values != 0).total;
+    // room for the fused path's split table one level deeper
+    *bytes = merge_layout(G + 1, len_a + len_b, key_dtype, with_values != 0).total;
     return IPM_OK;
 }
 

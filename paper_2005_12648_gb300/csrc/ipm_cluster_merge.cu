@@ -1,5 +1,6 @@
 // The last log2(C) levels of the division stage (Alg. 3) fused with the pair merge,
-// one thread-block cluster of C CTAs per group of C consecutive pairs.
+// one thread-block cluster of C CTAs per group of C consecutive pairs (half-size
+// tiles, two CTAs per SM).
 //
 // After the levels above it, the C pairs k0 .. k0+C-1 of a group occupy one contiguous
 // region [d_k0, d_{k0+C}) holding A[i_k0, i_{k0+C}) followed by B[j_k0, j_{k0+C}):
@@ -100,7 +101,7 @@ struct PairGeo {
 };
 
 template <typename K, bool KV, int THREADS, int E, int C>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS, 2)
     cluster_merge_kernel(K *__restrict__ buf, uint32_t *__restrict__ vals, uint64_t la,
                          uint64_t lb, const uint64_t *__restrict__ split, uint32_t G,
                          StatusBlock *sb) {
@@ -198,9 +199,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         if (a + b == 0) continue;
 
-        // ---- merge on chip into the output's phase (a move when a run is empty)
-        merge_two<K, KV, THREADS, E, true>(R + vg.offA, RV + vg.offAV, a, R + vg.offB,
-                                           RV + vg.offBV, b, R + vg.oo, RV + vg.ooV);
+        // ---- merge on chip into the output's phase (a move when a run is empty); A at
+        // R + offA and B at R + offB (payloads: RV + offAV, RV + offBV)
+        merge_two<K, KV, THREADS, E, true>(R + vg.offA, RV + vg.offAV, a, vg.offB - vg.offA,
+                                           vg.offBV - vg.offAV, b, R + vg.oo, RV + vg.ooV);
         fence_proxy_async_smem();
         __syncthreads();
 
@@ -281,18 +283,13 @@ ipm_status cluster_merge_t(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
     return IPM_OK;
 }
 
+// Half the plain merge's tile (two CTAs per SM, so one CTA's merge overlaps the
+// other's staging): 4-byte keys 512 x 33, 8-byte keys and key-value 256 x 33.  The
+// caller splits one level deeper so that every pair fits.
 template <typename K, bool KV>
-struct ClusterTileOf;
-template <>
-struct ClusterTileOf<int32_t, false> { static constexpr int T = 1024, E = 33; };
-template <>
-struct ClusterTileOf<uint32_t, false> { static constexpr int T = 1024, E = 33; };
-template <>
-struct ClusterTileOf<float, false> { static constexpr int T = 1024, E = 33; };
-template <>
-struct ClusterTileOf<uint64_t, false> { static constexpr int T = 512, E = 33; };
-template <typename K>
-struct ClusterTileOf<K, true> { static constexpr int T = 512, E = 33; };
+struct ClusterTileOf {
+    static constexpr int T = (sizeof(K) == 4 && !KV) ? 512 : 256, E = 33;
+};
 
 template <typename K, int C>
 ipm_status cluster_dispatch(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
@@ -376,6 +373,15 @@ ipm_status launch_cluster_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t
         return cluster_by_key<16>(buf, vals, la, lb, key, split, G, sb, stream);
     }
     return IPM_ERR_INVALID_ARG;
+}
+
+}  // namespace ipm
+
+namespace ipm {
+
+uint64_t cluster_tile_capacity(ipm_dtype key, bool with_values) {
+    const bool four = key == IPM_INT32 || key == IPM_UINT32 || key == IPM_FLOAT32;
+    return uint64_t((four && !with_values) ? 512 : 256) * 33u;
 }
 
 }  // namespace ipm

@@ -62,6 +62,8 @@ ipm_status launch_cluster_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t
                                 uint32_t log2_cluster, StatusBlock *sb, cudaStream_t stream);
 // The largest F <= wanted whose clusters of 2^F CTAs the device can schedule (0: none).
 uint32_t usable_fused_levels(ipm_dtype key, bool with_values, uint32_t wanted);
+// Pair capacity of the fused kernel's tile (half the plain merge's tile).
+uint64_t cluster_tile_capacity(ipm_dtype key, bool with_values);
 
 // Per-pair shared-memory merge of an arranged buffer.
 ipm_status launch_tile_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,

@@ -23,7 +23,7 @@ namespace {
 // Largest pair count the fixed scratch serves: P = 2^15 pairs, i.e. up to
 // 2^15 * 33,792 (~1.1e9) 4-byte keys or 2^15 * 16,896 (~5.5e8) 8-byte keys per call.
 constexpr uint32_t kMaxLog2Pairs = 15;
-constexpr size_t kScratchBytes = size_t(4) << 20;  // 4 MiB; 2^15 pairs need ~2.3 MiB
+constexpr size_t kScratchBytes = size_t(8) << 20;  // 8 MiB; 2^15 pairs need ~4.6 MiB
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 

@@ -28,17 +28,18 @@ struct TileShape {
 
 enum : int { kPairAbort = 0, kPairMerged = 1, kPairInOrder = 2, kPairTrivial = 3 };
 
-// Merge of two staged runs A = sA[0, a) and B = sB[0, b) (payloads vA, vB when KV) by
-// the whole CTA with EC outputs per thread (EC odd, THREADS * EC >= a + b; a, b >= 1
-// unless MAY_BE_EMPTY, which makes an empty run a move of the other): each thread
-// finds its diagonal of the merge path by binary search (stable predicate
-// A[m] <= B[d-1-m]), takes EC branch-free merge steps into registers, and, after a
-// barrier, writes them to dk[0, a + b) (dv for payloads), which may overlap the
-// sources (EC odd keeps the blocked writes conflict-free across banks).
+// Merge of two staged runs A = sk[0, a) and B = sk[bo, bo + b) (payloads sv[0, a) and
+// sv[bov, bov + b) when KV; bo, bov >= a) by the whole CTA with EC outputs per thread (EC odd,
+// THREADS * EC >= a + b; a, b >= 1 unless MAY_BE_EMPTY, which makes an empty run a move
+// of the other): each thread finds its diagonal of the merge path by binary search
+// (stable predicate A[m] <= B[d-1-m]), takes EC branch-free merge steps into registers,
+// and, after a barrier, writes them to dk[0, a + b) (dv for payloads), which may overlap
+// the sources (EC odd keeps the blocked writes conflict-free across banks).  Both runs
+// are addressed from one base so the merge loop keeps a single pointer.
 template <typename K, bool KV, int THREADS, int EC, bool MAY_BE_EMPTY = false>
-__device__ __forceinline__ void merge_two(const K *sA, const uint32_t *vA, uint32_t a,
-                                          const K *sB, const uint32_t *vB, uint32_t b,
-                                          K *dk, uint32_t *dv) {
+__device__ __forceinline__ void merge_two(const K *sk, const uint32_t *sv, uint32_t a,
+                                          uint32_t bo, uint32_t bov, uint32_t b, K *dk,
+                                          uint32_t *dv) {
     const uint32_t tid = threadIdx.x;
     const uint32_t c = a + b;
     const uint32_t dt = tid * uint32_t(EC);
@@ -49,7 +50,7 @@ __device__ __forceinline__ void merge_two(const K *sA, const uint32_t *vA, uint3
         uint32_t hi = dt < a ? dt : a;
         while (lo < hi) {
             const uint32_t m = (lo + hi) >> 1;
-            if (key_le(sA[m], sB[dt - 1 - m]))
+            if (key_le(sk[m], sk[bo + dt - 1 - m]))
                 lo = m + 1;
             else
                 hi = m;
@@ -60,25 +61,27 @@ __device__ __forceinline__ void merge_two(const K *sA, const uint32_t *vA, uint3
         // the shared-memory latency stays off the compare chain.  An exhausted (or empty)
         // side is never taken again, so its stale keys do not matter; an empty run reads
         // (and ignores) the first word of its staging area.
-        uint32_t ia = lo, ib = dt - lo;
+        // ia: A's position; jb: B's position in sk (B ends at eb = bo + b)
+        uint32_t ia = lo, jb = bo + (dt - lo);
+        const uint32_t eb = bo + b;
         const uint32_t la1 = MAY_BE_EMPTY && a == 0 ? 0u : a - 1;
-        const uint32_t lb1 = MAY_BE_EMPTY && b == 0 ? 0u : b - 1;
-        K va0 = sA[ia < la1 ? ia : la1], va1 = sA[ia + 1 < la1 ? ia + 1 : la1];
-        K va2 = sA[ia + 2 < la1 ? ia + 2 : la1];
-        K vb0 = sB[ib < lb1 ? ib : lb1], vb1 = sB[ib + 1 < lb1 ? ib + 1 : lb1];
-        K vb2 = sB[ib + 2 < lb1 ? ib + 2 : lb1];
+        const uint32_t lb1 = MAY_BE_EMPTY && b == 0 ? bo : eb - 1;
+        K va0 = sk[ia < la1 ? ia : la1], va1 = sk[ia + 1 < la1 ? ia + 1 : la1];
+        K va2 = sk[ia + 2 < la1 ? ia + 2 : la1];
+        K vb0 = sk[jb < lb1 ? jb : lb1], vb1 = sk[jb + 1 < lb1 ? jb + 1 : lb1];
+        K vb2 = sk[jb + 2 < lb1 ? jb + 2 : lb1];
 #pragma unroll
         for (int e = 0; e < EC; ++e) {
-            const bool takeA = (ib >= b) || (ia < a && key_le(va0, vb0));
+            const bool takeA = (jb >= eb) || (ia < a && key_le(va0, vb0));
             if (KV)
-                oi[KV ? e : 0] = takeA ? ia : a + ib;
+                oi[KV ? e : 0] = takeA ? ia : jb;  // an index of sk (A: < a, B: >= bo)
             else
                 ok[e] = takeA ? va0 : vb0;
-            const K *src = takeA ? sA + (ia + 3 < la1 ? ia + 3 : la1)
-                                 : sB + (ib + 3 < lb1 ? ib + 3 : lb1);
-            const K nv = *src;
+            const uint32_t src = takeA ? (ia + 3 < la1 ? ia + 3 : la1)
+                                       : (jb + 3 < lb1 ? jb + 3 : lb1);
+            const K nv = sk[src];
             ia += takeA ? 1u : 0u;
-            ib += takeA ? 0u : 1u;
+            jb += takeA ? 0u : 1u;
             va0 = takeA ? va1 : va0;
             va1 = takeA ? va2 : va1;
             va2 = takeA ? nv : va2;
@@ -91,10 +94,9 @@ __device__ __forceinline__ void merge_two(const K *sA, const uint32_t *vA, uint3
     if (KV && dt < c) {
 #pragma unroll
         for (int e = 0; e < EC; ++e) {
-            const uint32_t src = (dt + e < c) ? oi[KV ? e : 0] : 0u;
-            const bool fromA = src < a;
-            ok[e] = fromA ? sA[src] : sB[src - a];
-            ov[KV ? e : 0] = fromA ? vA[src] : vB[src - a];
+            const uint32_t q = (dt + e < c) ? oi[KV ? e : 0] : 0u;
+            ok[e] = sk[q];
+            ov[KV ? e : 0] = sv[q < a ? q : bov + (q - bo)];
         }
     }
     __syncthreads();
@@ -110,10 +112,72 @@ __device__ __forceinline__ void merge_two(const K *sA, const uint32_t *vA, uint3
 }
 
 // Step 2 of merge_pair_smem: the staged pair tk[0, c) = [A (a) | B (c - a)] merged onto
-// itself.
+// itself (a, c - a >= 1) by the whole CTA with EC outputs per thread, the same
+// algorithm as merge_two for the contiguous layout (A and B as two pointers).
 template <typename K, bool KV, int THREADS, int EC>
 __device__ __forceinline__ void merge_staged(K *tk, uint32_t *tv, uint32_t a, uint32_t c) {
-    merge_two<K, KV, THREADS, EC>(tk, tv, a, tk + a, KV ? tv + a : tv, c - a, tk, tv);
+    const uint32_t tid = threadIdx.x;
+    const uint32_t b = c - a;
+    const K *sA = tk;
+    const K *sB = tk + a;
+    const uint32_t dt = tid * uint32_t(EC);
+    K ok[EC];
+    uint32_t oi[KV ? EC : 1];
+    if (dt < c) {
+        uint32_t lo = dt > b ? dt - b : 0u;
+        uint32_t hi = dt < a ? dt : a;
+        while (lo < hi) {
+            const uint32_t m = (lo + hi) >> 1;
+            if (key_le(sA[m], sB[dt - 1 - m]))
+                lo = m + 1;
+            else
+                hi = m;
+        }
+        uint32_t ia = lo, ib = dt - lo;
+        const uint32_t la1 = a - 1, lb1 = b - 1;
+        K va0 = sA[ia < la1 ? ia : la1], va1 = sA[ia + 1 < la1 ? ia + 1 : la1];
+        K va2 = sA[ia + 2 < la1 ? ia + 2 : la1];
+        K vb0 = sB[ib < lb1 ? ib : lb1], vb1 = sB[ib + 1 < lb1 ? ib + 1 : lb1];
+        K vb2 = sB[ib + 2 < lb1 ? ib + 2 : lb1];
+#pragma unroll
+        for (int e = 0; e < EC; ++e) {
+            const bool takeA = (ib >= b) || (ia < a && key_le(va0, vb0));
+            if (KV)
+                oi[KV ? e : 0] = takeA ? ia : a + ib;
+            else
+                ok[e] = takeA ? va0 : vb0;
+            const uint32_t src = takeA ? (ia + 3 < la1 ? ia + 3 : la1)
+                                       : a + (ib + 3 < lb1 ? ib + 3 : lb1);
+            const K nv = tk[src];
+            ia += takeA ? 1u : 0u;
+            ib += takeA ? 0u : 1u;
+            va0 = takeA ? va1 : va0;
+            va1 = takeA ? va2 : va1;
+            va2 = takeA ? nv : va2;
+            vb0 = takeA ? vb0 : vb1;
+            vb1 = takeA ? vb1 : vb2;
+            vb2 = takeA ? vb2 : nv;
+        }
+    }
+    uint32_t ov[KV ? EC : 1];
+    if (KV && dt < c) {
+#pragma unroll
+        for (int e = 0; e < EC; ++e) {
+            const uint32_t src = (dt + e < c) ? oi[KV ? e : 0] : 0u;
+            ok[e] = tk[src];
+            ov[KV ? e : 0] = tv[src];
+        }
+    }
+    __syncthreads();
+    if (dt < c) {
+#pragma unroll
+        for (int e = 0; e < EC; ++e) {
+            if (dt + e < c) {
+                tk[dt + e] = ok[e];
+                if (KV) tv[dt + e] = ov[KV ? e : 0];
+            }
+        }
+    }
 }
 
 // Merges the pair at g (payload at gv when KV) through skeys/svals.  All THREADS
