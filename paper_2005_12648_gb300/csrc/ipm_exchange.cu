@@ -698,12 +698,14 @@ __global__ void __launch_bounds__(512, 1)
 // Warp-specialized executor: warp 0 is the producer (claims tickets, decodes items,
 // waits for an item's earlier LS steps, stages its blocks into a free stage), warps
 // 1..15 are the consumers (publish "reads done", wait for the flags their stores
-// depend on, store, release the stage).  Two stages; the producer keeps the next
-// item's load in flight while the consumers store the current one, so ticket claims
-// and decoding stay off the consumers' path.  Holder items (which wait on later tickets
-// of their own exchange) are drained before the producer claims another ticket, and a
-// SINGLE exchange (both stages) waits for both stages to drain: the same
-// deadlock-freedom argument as the single-role executor.
+// depend on, store, release the stage).  Two stages; the producer stages the next item
+// while the consumers store the current one, so ticket claims and decoding stay off the
+// consumers' path.  As in the single-role executor, a CTA holds at most two claimed
+// items and claims only into a free stage (a claimed item is staged at once, so its
+// "reads done" is published as soon as its data lands), holder items (which wait on
+// later tickets of their own exchange) are drained before the next claim, and a SINGLE
+// exchange (both stages) waits for both stages to drain: the same deadlock-freedom
+// argument.
 // ---------------------------------------------------------------------------------
 
 constexpr uint32_t kWsConsumers = 480;  // threads 32..511
@@ -973,6 +975,17 @@ __global__ void __launch_bounds__(512, 1)
             return true;
         };
         for (;;) {
+            // Free the stage before claiming: a claimed item is then always staged at
+            // once, so its "reads done" can be published as soon as its data lands (a
+            // stash holder elsewhere may be waiting for it while this CTA's consumers
+            // wait for that holder).
+            if (!drain(st)) {
+                if (lane == 0) {
+                    set_status(sb, IPM_ERR_TIMEOUT);
+                    sh.abort = 1;
+                }
+                break;
+            }
             uint32_t t = 0;
             if (lane == 0) t = atomicAdd(ctr, 1u);
             t = __shfl_sync(0xffffffffu, t, 0);
@@ -983,22 +996,18 @@ __global__ void __launch_bounds__(512, 1)
                 fail = true;
             }
             if (t >= total || fail || *((volatile int *)&sh.abort)) {
-                // end marker for the consumers in the next stage
-                if (drain(st)) {
-                    if (lane == 0) {
-                        sh.end[st] = 1;
-                        mbar_arrive(&full[st]);
-                    }
-                    ++arrivals[st];
-                } else if (lane == 0) {
-                    set_status(sb, IPM_ERR_TIMEOUT);
-                    sh.abort = 1;
+                // end marker for the consumers in the next stage (free: drained above)
+                if (lane == 0) {
+                    sh.end[st] = 1;
+                    mbar_arrive(&full[st]);
                 }
+                ++arrivals[st];
                 break;
             }
-            bool ok = drain(st);
-            if (ok && it.single) ok = drain(st ^ 1u);
-            if (ok && it.before > 0) {  // the item's earlier LS steps must be complete
+            // a SINGLE exchange spans both stages; an item after LS steps of its
+            // exchange waits until they are complete
+            bool ok = !it.single || drain(st ^ 1u);
+            if (ok && it.before > 0) {
                 bool w = true;
                 if (lane == 0) w = wait_count(join + it.r, it.before);
                 ok = __shfl_sync(0xffffffffu, w, 0) != 0;

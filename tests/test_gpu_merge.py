@@ -254,3 +254,41 @@ def test_exchange_engines_match_oracle(ipm, dev, orc, engine):
     finally:
         ipm.ipm_set_exchange_engine(1)
         ipm.ipm_set_fused_levels(4)
+
+
+@pytest.mark.parametrize("engine", [0, 1])
+def test_exchange_stress_random_layouts(ipm, dev, orc, engine):
+    """Random sizes, skews and pair counts (many small exchanges of every phase kind, in
+    every interleaving of tickets across CTAs), both executors, against the oracle's
+    arranged layout."""
+    import torch
+
+    rng = np.random.default_rng(1234 + engine)
+    ipm.ipm_set_exchange_engine(engine)
+    try:
+        for it in range(24):
+            dt = [np.int32, np.uint64][it % 2]
+            dist = ["uniform", "dup16", "zipf", "alternation", "revdisjoint"][it % 5]
+            if dist == "zipf" and dt == np.int32:
+                dist = "uniform"
+            la = int(rng.integers(1, 3_000_000))
+            lb = int(rng.integers(1, 3_000_000))
+            if it % 4 == 0:
+                lb = int(rng.integers(1, 2000))  # very unbalanced
+            G = int(rng.integers(1, 13))
+            a, b = W.make_pair(dist, dt, la, lb, seed=it)
+            P = 1 << G
+            d = orc.diagonals(la + lb, P)
+            i = orc.splits_replay(a, b, d)
+            buf = to_dev(np.concatenate([a, b]), dev)
+            split = torch.from_numpy(i.astype(np.int64)).to(dev)
+            wsG = max(G, ipm.ipm_merge_plan(la, lb, NAME[np.dtype(dt)])[0])
+            ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, NAME[np.dtype(dt)], False,
+                                                             wsG), dev)
+            ipm.ipm_merge_rearrange(buf, None, la, lb, NAME[np.dtype(dt)], split, G, ws)
+            torch.cuda.synchronize()
+            assert ipm.ipm_read_device_status(ws) == 0, (it, la, lb, G)
+            want = orc.arrange(a, b, d, i)
+            assert first_diff(from_dev(buf, dt), want) is None, (it, dist, la, lb, G)
+    finally:
+        ipm.ipm_set_exchange_engine(1)
