@@ -169,18 +169,24 @@ ipm_status ipm_read_exchange_bytes(const void *d_ws, ipm_stream_t stream, uint64
 
 /*
  * How many of the last levels of the division stage the merge entry points fuse with
- * the pair merge (process-wide, default 4; a device that cannot schedule clusters of
- * 2^levels CTAs gets the largest smaller count it can).  With F fused levels, the exchange levels
- * stop at G - F, and a thread-block cluster of 2^F CTAs takes each group of 2^F
- * consecutive pairs: the group's region holds exactly those pairs' A and B slices, so
- * each CTA stages its pair's two slices, the cluster barrier ensures the whole group
- * has been read, and each pair is merged on chip and written to its final place.  The
- * result is identical for every F; F only trades exchange passes over the buffer for
- * cluster scheduling.  0 <= levels <= 4 (16-CTA clusters use the non-portable cluster
- * size), else IPM_ERR_INVALID_ARG.  Not thread-safe against concurrent merge calls.
+ * the pair merge (process-wide, default 8).  With F fused levels the exchange levels
+ * stop F levels short, and each group of 2^F consecutive pairs is finished by 2^F CTAs
+ * together: the group's region holds exactly those pairs' A and B slices, so each CTA
+ * stages its pair's two slices, the group synchronises once the whole group has been
+ * read, and each pair is merged on chip and written to its final place.  The fused path
+ * uses half-size tiles (two CTAs per SM) and splits one level deeper.  The result is
+ * identical for every F; F trades exchange passes over the buffer for group size.
+ * 0 <= levels <= 10 (the device may lower it: a group needs at most the resident CTAs,
+ * a thread-block cluster at most 16), else IPM_ERR_INVALID_ARG.  Not thread-safe
+ * against concurrent merge calls.
+ *
+ * ipm_set_fused_engine selects how a group synchronises: 0 = one thread-block cluster
+ * per group (cluster barrier; F <= 4), 1 = CTAs taken from a ticket in order and a
+ * group barrier in global memory (the default).
  */
 ipm_status ipm_set_fused_levels(uint32_t levels);
 ipm_status ipm_get_fused_levels(uint32_t *levels);
+ipm_status ipm_set_fused_engine(uint32_t engine);
 
 /*
  * Executor of the exchange levels (process-wide): 0 = every thread of a CTA takes

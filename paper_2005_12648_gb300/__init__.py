@@ -34,7 +34,7 @@ __all__ = [
     "ipm_split_model_loss_grad", "ipm_merge_splits_learned", "ipm_merge_inplace_learned",
     "split_model_initial_params", "split_model_to_device", "split_model_from_device",
     "train_split_model", "ipm_set_fused_levels", "ipm_get_fused_levels",
-    "ipm_set_exchange_engine",
+    "ipm_set_exchange_engine", "ipm_set_fused_engine",
 ]
 
 DTYPES = {"int32": 0, "uint32": 1, "uint64": 2, "float32": 3}
@@ -87,6 +87,7 @@ _SIGS = {
     "ipm_set_fused_levels": (_i, [_u32]),
     "ipm_get_fused_levels": (_i, [ctypes.POINTER(_u32)]),
     "ipm_set_exchange_engine": (_i, [_u32]),
+    "ipm_set_fused_engine": (_i, [_u32]),
 }
 
 
@@ -418,6 +419,10 @@ def ipm_set_fused_levels(levels: int) -> None:
 
 def ipm_set_exchange_engine(engine: int) -> None:
     _check(load().ipm_set_exchange_engine(engine), "ipm_set_exchange_engine")
+
+
+def ipm_set_fused_engine(engine: int) -> None:
+    _check(load().ipm_set_fused_engine(engine), "ipm_set_fused_engine")
 
 
 def ipm_get_fused_levels() -> int:

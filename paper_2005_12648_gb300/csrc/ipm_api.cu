@@ -85,8 +85,11 @@ class PhaseScope {
 
 constexpr uint32_t kMaxLog2Pairs = 22;
 
-// Bottom levels of the division stage fused with the pair merge (ipm_set_fused_levels).
-uint32_t g_fused_levels = 4;
+// Bottom levels of the division stage fused with the pair merge (ipm_set_fused_levels)
+// and how the groups synchronise: 0 = thread-block clusters (F <= 4), 1 = group
+// barriers in global memory (ipm_set_fused_engine).
+uint32_t g_fused_levels = 8;
+uint32_t g_fused_engine = 1;
 
 bool valid_key(ipm_dtype t) {
     return t == IPM_INT32 || t == IPM_UINT32 || t == IPM_UINT64 || t == IPM_FLOAT32;
@@ -128,14 +131,16 @@ ipm_status batched_variant(const ipm_batched_options *opt, uint32_t *variant) {
 }
 
 struct MergeLayout {
-    size_t split_off, plan_off, total;
+    size_t split_off, group_off, plan_off, total;
 };
 
+// status block | split table (P+1) | group counters (P) | exchange plans
 MergeLayout merge_layout(uint32_t G, uint64_t n, ipm_dtype key, bool kv) {
     MergeLayout L;
     const uint64_t P = uint64_t(1) << G;
     L.split_off = kStatusBytes;
-    L.plan_off = L.split_off + align_up(sizeof(uint64_t) * (P + 1), 256);
+    L.group_off = L.split_off + align_up(sizeof(uint64_t) * (P + 1), 256);
+    L.plan_off = L.group_off + align_up(sizeof(uint32_t) * P, 256);
     L.total = L.plan_off + xplan_area_bytes(G, n, key, kv);
     return L;
 }
@@ -154,12 +159,13 @@ ipm_status merge_core(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_d
         return IPM_ERR_ALIGNMENT;
     if (!aligned(ws, 256)) return IPM_ERR_ALIGNMENT;
     const uint64_t n = la + lb;
-    // The fused path (the last F levels done by thread-block clusters of half-size
-    // tiles) splits one level deeper: every pair then fits the half tile.
-    const uint32_t F = G + 1 <= kMaxLog2Pairs + 1
-                           ? usable_fused_levels(key, kv, g_fused_levels < G + 1 ? g_fused_levels
-                                                                                 : G + 1)
-                           : 0;
+    // The fused path (the last F levels done by groups of CTAs with half-size tiles:
+    // thread-block clusters for F <= 4 when selected, else global-memory group
+    // barriers) splits one level deeper: every pair then fits the half tile.
+    const uint32_t Fwant = g_fused_levels < G + 1 ? g_fused_levels : G + 1;
+    const bool use_clusters = g_fused_engine == 0;
+    const uint32_t F = use_clusters ? usable_fused_levels(key, kv, Fwant > 4 ? 4 : Fwant)
+                                    : usable_group_levels(key, kv, Fwant);
     const uint32_t Gs = F > 0 ? G + 1 : G;  // depth of the split table
     const MergeLayout L = merge_layout(Gs, n, key, kv);
     if (ws_bytes < L.total) return IPM_ERR_WORKSPACE;
@@ -193,7 +199,11 @@ ipm_status merge_core(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_d
     }
     // a3: pair merge (fused with the last F levels when F > 0)
     PhaseScope ps(3, 1, stream);
-    if (F > 0) return launch_cluster_merge(buf, vals, la, lb, key, split, Gs, F, sb, stream);
+    if (F > 0 && use_clusters)
+        return launch_cluster_merge(buf, vals, la, lb, key, split, Gs, F, sb, stream);
+    if (F > 0)
+        return launch_group_merge(buf, vals, la, lb, key, split, Gs, F,
+                                  reinterpret_cast<uint32_t *>(w + L.group_off), sb, stream);
     return launch_tile_merge(buf, vals, la, lb, key, split, G, sb, stream);
 }
 
@@ -507,8 +517,14 @@ ipm_status ipm_merge_inplace_learned(void *d_buf, uint64_t len_a, uint64_t len_b
                       (cudaStream_t)stream, d_model);
 }
 
+ipm_status ipm_set_fused_engine(uint32_t engine) {
+    if (engine > 1) return IPM_ERR_INVALID_ARG;
+    g_fused_engine = engine;
+    return IPM_OK;
+}
+
 ipm_status ipm_set_fused_levels(uint32_t levels) {
-    if (levels > 4) return IPM_ERR_INVALID_ARG;
+    if (levels > 10) return IPM_ERR_INVALID_ARG;
     g_fused_levels = levels;
     return IPM_OK;
 }

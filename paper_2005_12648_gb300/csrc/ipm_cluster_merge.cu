@@ -220,6 +220,198 @@ __global__ void __launch_bounds__(THREADS, 2)
     if (tid == 0) bulk_wait_all0();
 }
 
+// ---------------------------------------------------------------------------------
+// The same fusion with a group barrier in global memory instead of a cluster: groups
+// of 2^F consecutive pairs (any F with 2^F <= the resident CTAs), members taken from a
+// ticket.  Tickets are claimed in order, so only the newest group can be partially
+// claimed; every older group is complete, its members finish, and the CTAs they free
+// claim the remaining tickets: with at least 2^F resident CTAs no group waits forever.  A member counts itself in once its slices are on chip and waits
+// (bounded) until the whole group has; then it merges and stores.
+// ---------------------------------------------------------------------------------
+constexpr uint32_t kGroupTicket = 40;  // status block counter of the group kernel
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename K, bool KV, int THREADS, int E>
+__global__ void __launch_bounds__(THREADS, 2)
+    group_merge_kernel(K *__restrict__ buf, uint32_t *__restrict__ vals, uint64_t la,
+                       uint64_t lb, const uint64_t *__restrict__ split, uint32_t G, uint32_t F,
+                       uint32_t *__restrict__ gctr, StatusBlock *sb) {
+    using Shape = ClusterShape<K, KV, THREADS, E>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);
+    K *R = reinterpret_cast<K *>(smem_raw + 128);
+    uint32_t *RV = reinterpret_cast<uint32_t *>(smem_raw + 128 + Shape::kKeyBytes);
+    __shared__ int abort_flag;
+    __shared__ uint32_t s_t;
+    __shared__ PairGeo<K> pg;
+    volatile PairGeo<K> &vg = pg;
+    constexpr uint32_t VK = 16u / uint32_t(sizeof(K));
+    constexpr uint32_t VV = 4u;
+    if (sb != nullptr && *((volatile unsigned int *)&sb->done)) return;
+    const uint32_t tid = threadIdx.x;
+    const uint64_t P = 1ull << G;
+    const uint32_t gsize = 1u << F;
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        mbar_fence_init();
+        abort_flag = 0;
+    }
+    uint32_t parity = 0;
+
+    for (;;) {
+        if (tid == 0) {
+            const uint32_t t = atomicAdd(&sb->counters[kGroupTicket], 1u);
+            s_t = t;
+            if (t < P) {
+                const uint64_t n = la + lb;
+                const uint64_t k = t, k0 = (k >> F) << F, k1 = k0 + gsize;
+                const uint64_t dlo = (k0 * n) >> G, dhi = (k1 * n) >> G;
+                const uint64_t ilo = split[k0], ihi = split[k1];
+                const uint64_t d0 = (k * n) >> G, d1 = ((k + 1) * n) >> G;
+                const uint64_t i0 = split[k], i1 = split[k + 1];
+                const bool ok = ilo <= i0 && i0 <= i1 && i1 <= ihi && ihi <= dhi &&
+                                ilo <= dlo && i0 <= d0 && i1 - i0 <= d1 - d0 &&
+                                d0 - i0 >= dlo - ilo && d1 - i1 <= dhi - ihi &&
+                                d1 - d0 <= uint64_t(Shape::kTile);
+                if (!ok && sb != nullptr) set_status(sb, IPM_ERR_DEVICE);
+                const uint32_t c = ok ? uint32_t(d1 - d0) : 0u;
+                const uint32_t a = ok ? uint32_t(i1 - i0) : 0u;
+                const uint64_t posA = dlo + (i0 - ilo);
+                const uint64_t posB = dlo + (ihi - ilo) + ((d0 - i0) - (dlo - ilo));
+                K *gA = buf + posA, *gB = buf + posB, *gO = buf + d0;
+                const uint32_t oo = phase_of(gO);
+                const uint32_t offA = oo + ((phase_of(gA) + VK - oo) % VK);
+                const uint32_t offB = offA + a + ((phase_of(gB) + VK - (offA + a) % VK) % VK);
+                pg.gA = gA;
+                pg.gB = gB;
+                pg.gO = gO;
+                pg.a = a;
+                pg.b = c - a;
+                pg.offA = offA;
+                pg.offB = offB;
+                pg.oo = oo;
+                if (KV) {
+                    uint32_t *vA = vals + posA, *vB = vals + posB, *vO = vals + d0;
+                    const uint32_t ooV = phase_of(vO);
+                    const uint32_t offAV = ooV + ((phase_of(vA) + VV - ooV) % VV);
+                    pg.vA = vA;
+                    pg.vB = vB;
+                    pg.vO = vO;
+                    pg.ooV = ooV;
+                    pg.offAV = offAV;
+                    pg.offBV = offAV + a + ((phase_of(vB) + VV - (offAV + a) % VV) % VV);
+                }
+            }
+        }
+        __syncthreads();
+        const uint32_t t = s_t;
+        if (t >= P) break;
+        const uint32_t a = vg.a, b = vg.b;
+
+        // ---- stage both slices
+        if (a + b > 0) {
+            if (tid == 0) {
+                uint32_t tx = body_bytes(pg.gA, a) + body_bytes(pg.gB, b);
+                if (KV) tx += body_bytes(pg.vA, a) + body_bytes(pg.vB, b);
+                mbar_arrive_expect_tx(mbar, tx);
+            }
+            stage_range<K, THREADS>(R + vg.offA, vg.gA, a, mbar);
+            stage_range<K, THREADS>(R + vg.offB, vg.gB, b, mbar);
+            if (KV) {
+                stage_range<uint32_t, THREADS>(RV + vg.offAV, vg.vA, a, mbar);
+                stage_range<uint32_t, THREADS>(RV + vg.offBV, vg.vB, b, mbar);
+            }
+            if (!mbar_wait_bounded(mbar, parity)) atomicOr(&abort_flag, 1);
+            parity ^= 1u;
+        }
+        __syncthreads();  // every thread's head / tail loads have landed too
+        // ---- group barrier: the group's region may be written once every member has
+        // its slices on chip
+        if (tid == 0) {
+            uint32_t *ctr = gctr + (t >> F);
+            atomicAdd(ctr, 1u);
+            unsigned long long t0 = 0;
+            uint32_t it = 0;
+            while (ld_acquire_u32(ctr) < gsize) {
+                if ((++it & 63u) == 0) {
+                    const unsigned long long now = globaltimer_ns();
+                    if (t0 == 0)
+                        t0 = now;
+                    else if (now - t0 > kWaitLimitNs) {
+                        abort_flag = 1;
+                        break;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (abort_flag) {
+            if (tid == 0 && sb != nullptr) set_status(sb, IPM_ERR_TIMEOUT);
+            break;
+        }
+        if (a + b == 0) continue;
+
+        // ---- merge on chip into the output's phase (a move when a run is empty)
+        merge_two<K, KV, THREADS, E, true>(R + vg.offA, RV + vg.offAV, a, vg.offB - vg.offA,
+                                           vg.offBV - vg.offAV, b, R + vg.oo, RV + vg.ooV);
+        fence_proxy_async_smem();
+        __syncthreads();
+
+        // ---- store
+        const uint32_t c = vg.a + vg.b;
+        store_range<K, THREADS>(vg.gO, R + vg.oo, c);
+        if (KV) store_range<uint32_t, THREADS>(vg.vO, RV + vg.ooV, c);
+        if (tid == 0) {
+            bulk_commit();
+            bulk_wait_read0();
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+    }
+    if (tid == 0) bulk_wait_all0();
+}
+
+template <typename K, bool KV, int THREADS, int E>
+int group_grid() {
+    using Shape = ClusterShape<K, KV, THREADS, E>;
+    auto kern = group_merge_kernel<K, KV, THREADS, E>;
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    cached = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(Shape::kSmem)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return cached;
+    }
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, Shape::kSmem) !=
+        cudaSuccess) {
+        (void)cudaGetLastError();
+        per_sm = 0;
+    }
+    cached = per_sm > 0 ? per_sm * num_sms() : 0;
+    return cached;
+}
+
+template <typename K, bool KV, int THREADS, int E>
+ipm_status group_merge_t(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
+                         const uint64_t *split, uint32_t G, uint32_t F, uint32_t *gctr,
+                         StatusBlock *sb, cudaStream_t stream) {
+    using Shape = ClusterShape<K, KV, THREADS, E>;
+    const int grid = group_grid<K, KV, THREADS, E>();
+    if (grid < (1 << F)) return IPM_ERR_CUDA;
+    const uint64_t P = 1ull << G;
+    const unsigned g = unsigned(P < uint64_t(grid) ? P : uint64_t(grid));
+    group_merge_kernel<K, KV, THREADS, E><<<g, THREADS, Shape::kSmem, stream>>>(
+        (K *)buf, vals, la, lb, split, G, F, gctr, sb);
+    return last_launch_status();
+}
+
 // Resident clusters of the kernel on the current device (0 when clusters of C CTAs
 // cannot be scheduled), queried once per instantiation.
 template <typename K, bool KV, int THREADS, int E, int C>
@@ -342,7 +534,54 @@ ipm_status cluster_by_key(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, i
     return IPM_ERR_UNSUPPORTED_DTYPE;
 }
 
+template <typename K>
+ipm_status group_dispatch(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
+                          const uint64_t *split, uint32_t G, uint32_t F, uint32_t *gctr,
+                          StatusBlock *sb, cudaStream_t stream) {
+    if (vals != nullptr)
+        return group_merge_t<K, true, ClusterTileOf<K, true>::T, ClusterTileOf<K, true>::E>(
+            buf, vals, la, lb, split, G, F, gctr, sb, stream);
+    return group_merge_t<K, false, ClusterTileOf<K, false>::T, ClusterTileOf<K, false>::E>(
+        buf, nullptr, la, lb, split, G, F, gctr, sb, stream);
+}
+
+template <typename K>
+int group_grid_kv(bool kv) {
+    return kv ? group_grid<K, true, ClusterTileOf<K, true>::T, ClusterTileOf<K, true>::E>()
+              : group_grid<K, false, ClusterTileOf<K, false>::T, ClusterTileOf<K, false>::E>();
+}
+
 }  // namespace
+
+uint32_t usable_group_levels(ipm_dtype key, bool with_values, uint32_t wanted) {
+    int grid = 0;
+    switch (key) {
+    case IPM_INT32: grid = group_grid_kv<int32_t>(with_values); break;
+    case IPM_UINT32: grid = group_grid_kv<uint32_t>(with_values); break;
+    case IPM_UINT64: grid = group_grid_kv<uint64_t>(with_values); break;
+    case IPM_FLOAT32: grid = group_grid_kv<float>(with_values); break;
+    }
+    uint32_t f = wanted;
+    while (f > 0 && (1 << f) > grid) --f;  // a whole group must fit the resident CTAs
+    return f;
+}
+
+ipm_status launch_group_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
+                              ipm_dtype key, const uint64_t *split, uint32_t G, uint32_t F,
+                              uint32_t *gctr, StatusBlock *sb, cudaStream_t stream) {
+    IPM_CUDA_TRY(cudaMemsetAsync(gctr, 0, sizeof(uint32_t) * size_t((1ull << G) >> F), stream));
+    switch (key) {
+    case IPM_INT32:
+        return group_dispatch<int32_t>(buf, vals, la, lb, split, G, F, gctr, sb, stream);
+    case IPM_UINT32:
+        return group_dispatch<uint32_t>(buf, vals, la, lb, split, G, F, gctr, sb, stream);
+    case IPM_UINT64:
+        return group_dispatch<uint64_t>(buf, vals, la, lb, split, G, F, gctr, sb, stream);
+    case IPM_FLOAT32:
+        return group_dispatch<float>(buf, vals, la, lb, split, G, F, gctr, sb, stream);
+    }
+    return IPM_ERR_UNSUPPORTED_DTYPE;
+}
 
 uint32_t usable_fused_levels(ipm_dtype key, bool with_values, uint32_t wanted) {
     for (uint32_t f = wanted; f > 0; --f) {

@@ -64,6 +64,13 @@ ipm_status launch_cluster_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t
 uint32_t usable_fused_levels(ipm_dtype key, bool with_values, uint32_t wanted);
 // Pair capacity of the fused kernel's tile (half the plain merge's tile).
 uint64_t cluster_tile_capacity(ipm_dtype key, bool with_values);
+// The same fusion with a group barrier in global memory: groups of 2^F pairs taken from
+// a ticket (gctr: (2^G >> F) uint32 group counters in the workspace, zeroed here).
+ipm_status launch_group_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
+                              ipm_dtype key, const uint64_t *split, uint32_t G, uint32_t F,
+                              uint32_t *gctr, StatusBlock *sb, cudaStream_t stream);
+// The largest F <= wanted with at least 2^F resident CTAs of the group kernel.
+uint32_t usable_group_levels(ipm_dtype key, bool with_values, uint32_t wanted);
 
 // Per-pair shared-memory merge of an arranged buffer.
 ipm_status launch_tile_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,

@@ -184,18 +184,20 @@ def test_async_on_a_side_stream(ipm, dev, orc):
     assert first_diff(from_dev(buf, np.int32), orc.merge(a, b)) is None
 
 
-@pytest.mark.parametrize("fused", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("engine,fused", [(0, 0), (0, 1), (0, 2), (0, 3), (0, 4), (1, 1),
+                                          (1, 3), (1, 5), (1, 6), (1, 7), (1, 8), (1, 10)])
 @pytest.mark.parametrize("dt", [np.int32, np.uint64])
-def test_fused_bottom_levels_match_oracle(ipm, dev, orc, fused, dt):
-    """The last `fused` levels done by thread-block clusters (each cluster stages its
-    group's pairs, then writes them merged) give the oracle's merge for every depth,
-    including pair counts below the cluster size, empty runs inside a group, ragged
-    sizes and ties."""
+def test_fused_bottom_levels_match_oracle(ipm, dev, orc, engine, fused, dt):
+    """The last `fused` levels done by groups of CTAs (each group stages its pairs, then
+    writes them merged; groups synchronised by a thread-block cluster or by a barrier in
+    global memory) give the oracle's merge for every depth, including pair counts below
+    the group size, empty runs inside a group, ragged sizes and ties."""
     cases = [(3_000_017, 2_900_011, "uniform", 0), (1_000_003, 700_001, "dup16", 0),
              (50_000, 70_001, "uniform", 3), (123_457, 98_765, "alternation", 6),
              (1_000_000, 1, "uniform", 4), (333_333, 333_333, "revdisjoint", 5),
              (2_000_001, 17, "uniform", 0)]
     ipm.ipm_set_fused_levels(fused)
+    ipm.ipm_set_fused_engine(engine)
     try:
         assert ipm.ipm_get_fused_levels() == fused
         for la, lb, dist, G in cases:
@@ -207,7 +209,8 @@ def test_fused_bottom_levels_match_oracle(ipm, dev, orc, fused, dt):
             want = orc.merge(a, b)
             assert first_diff(got, want) is None, (la, lb, dist, G, first_diff(got, want))
     finally:
-        ipm.ipm_set_fused_levels(4)
+        ipm.ipm_set_fused_levels(8)
+        ipm.ipm_set_fused_engine(1)
 
 
 @pytest.mark.parametrize("engine", [0, 1])
@@ -234,12 +237,12 @@ def test_exchange_engines_match_oracle(ipm, dev, orc, engine):
                                  ("dup16", np.uint32, 1_000_003, 700_001),
                                  ("revdisjoint", np.int32, 900_001, 1_200_007),
                                  ("uniform", np.uint64, 1_500_007, 1_400_011)]:
-            for fused in (0, 4):
+            for fused in (0, 4, 6):
                 ipm.ipm_set_fused_levels(fused)
                 a, b = W.make_pair(dist, dt, la, lb, seed=la)
                 got = _merge_dev(ipm, dev, a, b)
                 assert first_diff(got, orc.merge(a, b)) is None, (dist, la, lb, fused)
-        ipm.ipm_set_fused_levels(4)
+        ipm.ipm_set_fused_levels(8)
         ka, kb = W.make_pair("zipf", np.uint32, 2_000_003, 1_700_001, seed=3)
         keys = to_dev(np.concatenate([ka, kb]), dev)
         vals = torch.arange(ka.size + kb.size, dtype=torch.int32, device=dev)
@@ -253,7 +256,7 @@ def test_exchange_engines_match_oracle(ipm, dev, orc, engine):
         assert np.array_equal(vals.cpu().numpy().view(np.uint32), wv)
     finally:
         ipm.ipm_set_exchange_engine(1)
-        ipm.ipm_set_fused_levels(4)
+        ipm.ipm_set_fused_levels(8)
 
 
 @pytest.mark.parametrize("engine", [0, 1])
