@@ -225,8 +225,11 @@ __global__ void __launch_bounds__(THREADS, 2)
 // of 2^F consecutive pairs (any F with 2^F <= the resident CTAs), members taken from a
 // ticket.  Tickets are claimed in order, so only the newest group can be partially
 // claimed; every older group is complete, its members finish, and the CTAs they free
-// claim the remaining tickets: with at least 2^F resident CTAs no group waits forever.  A member counts itself in once its slices are on chip and waits
-// (bounded) until the whole group has; then it merges and stores.
+// claim the remaining tickets: with at least 2^F resident CTAs no group waits forever.
+// A member counts itself in once its slices are on chip, merges them on chip (the
+// merge writes only shared memory), then waits (bounded) until the whole group has
+// counted in before it stores.  The next ticket is claimed once the current pair has
+// passed its barrier, while the pair's bulk store drains.
 // ---------------------------------------------------------------------------------
 constexpr uint32_t kGroupTicket = 40;  // status block counter of the group kernel
 
@@ -234,6 +237,57 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
     uint32_t v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Claim the next pair (thread 0): its ticket and, when it is a pair, its geometry
+// within its group's region.  Returns the ticket.
+template <typename K, bool KV, uint32_t TILE>
+__device__ __forceinline__ uint32_t group_claim(PairGeo<K> &pg, K *buf, uint32_t *vals,
+                                                uint64_t la, uint64_t lb,
+                                                const uint64_t *__restrict__ split,
+                                                uint32_t G, uint32_t F, StatusBlock *sb) {
+    constexpr uint32_t VK = 16u / uint32_t(sizeof(K));
+    constexpr uint32_t VV = 4u;
+    const uint32_t t = atomicAdd(&sb->counters[kGroupTicket], 1u);
+    if (uint64_t(t) >= (1ull << G)) return t;
+    const uint64_t n = la + lb;
+    const uint64_t k = t, k0 = (k >> F) << F, k1 = k0 + (1ull << F);
+    const uint64_t dlo = (k0 * n) >> G, dhi = (k1 * n) >> G;
+    const uint64_t ilo = split[k0], ihi = split[k1];
+    const uint64_t d0 = (k * n) >> G, d1 = ((k + 1) * n) >> G;
+    const uint64_t i0 = split[k], i1 = split[k + 1];
+    const bool ok = ilo <= i0 && i0 <= i1 && i1 <= ihi && ihi <= dhi && ilo <= dlo &&
+                    i0 <= d0 && i1 - i0 <= d1 - d0 && d0 - i0 >= dlo - ilo &&
+                    d1 - i1 <= dhi - ihi && d1 - d0 <= uint64_t(TILE);
+    if (!ok) set_status(sb, IPM_ERR_DEVICE);
+    const uint32_t c = ok ? uint32_t(d1 - d0) : 0u;
+    const uint32_t a = ok ? uint32_t(i1 - i0) : 0u;
+    // the group's layout: A[ilo, ihi) at dlo, then B
+    const uint64_t posA = dlo + (i0 - ilo);
+    const uint64_t posB = dlo + (ihi - ilo) + ((d0 - i0) - (dlo - ilo));
+    K *gA = buf + posA, *gB = buf + posB, *gO = buf + d0;
+    const uint32_t oo = phase_of(gO);
+    const uint32_t offA = oo + ((phase_of(gA) + VK - oo) % VK);
+    pg.gA = gA;
+    pg.gB = gB;
+    pg.gO = gO;
+    pg.a = a;
+    pg.b = c - a;
+    pg.offA = offA;
+    pg.offB = offA + a + ((phase_of(gB) + VK - (offA + a) % VK) % VK);
+    pg.oo = oo;
+    if (KV) {
+        uint32_t *vA = vals + posA, *vB = vals + posB, *vO = vals + d0;
+        const uint32_t ooV = phase_of(vO);
+        const uint32_t offAV = ooV + ((phase_of(vA) + VV - ooV) % VV);
+        pg.vA = vA;
+        pg.vB = vB;
+        pg.vO = vO;
+        pg.ooV = ooV;
+        pg.offAV = offAV;
+        pg.offBV = offAV + a + ((phase_of(vB) + VV - (offAV + a) % VV) % VV);
+    }
+    return t;
 }
 
 template <typename K, bool KV, int THREADS, int E>
@@ -247,12 +301,9 @@ __global__ void __launch_bounds__(THREADS, 2)
     K *R = reinterpret_cast<K *>(smem_raw + 128);
     uint32_t *RV = reinterpret_cast<uint32_t *>(smem_raw + 128 + Shape::kKeyBytes);
     __shared__ int abort_flag;
-    __shared__ uint32_t s_t;
-    __shared__ PairGeo<K> pg;
-    volatile PairGeo<K> &vg = pg;
-    constexpr uint32_t VK = 16u / uint32_t(sizeof(K));
-    constexpr uint32_t VV = 4u;
-    if (sb != nullptr && *((volatile unsigned int *)&sb->done)) return;
+    __shared__ uint32_t s_t[2];
+    __shared__ PairGeo<K> pgs[2];  // the current pair and the next one
+    if (sb == nullptr || *((volatile unsigned int *)&sb->done)) return;
     const uint32_t tid = threadIdx.x;
     const uint64_t P = 1ull << G;
     const uint32_t gsize = 1u << F;
@@ -260,64 +311,22 @@ __global__ void __launch_bounds__(THREADS, 2)
         mbar_init(mbar, 1);
         mbar_fence_init();
         abort_flag = 0;
+        s_t[0] = group_claim<K, KV, Shape::kTile>(pgs[0], buf, vals, la, lb, split, G, F, sb);
     }
-    uint32_t parity = 0;
+    __syncthreads();
+    uint32_t parity = 0, cur = 0;
 
     for (;;) {
-        if (tid == 0) {
-            const uint32_t t = atomicAdd(&sb->counters[kGroupTicket], 1u);
-            s_t = t;
-            if (t < P) {
-                const uint64_t n = la + lb;
-                const uint64_t k = t, k0 = (k >> F) << F, k1 = k0 + gsize;
-                const uint64_t dlo = (k0 * n) >> G, dhi = (k1 * n) >> G;
-                const uint64_t ilo = split[k0], ihi = split[k1];
-                const uint64_t d0 = (k * n) >> G, d1 = ((k + 1) * n) >> G;
-                const uint64_t i0 = split[k], i1 = split[k + 1];
-                const bool ok = ilo <= i0 && i0 <= i1 && i1 <= ihi && ihi <= dhi &&
-                                ilo <= dlo && i0 <= d0 && i1 - i0 <= d1 - d0 &&
-                                d0 - i0 >= dlo - ilo && d1 - i1 <= dhi - ihi &&
-                                d1 - d0 <= uint64_t(Shape::kTile);
-                if (!ok && sb != nullptr) set_status(sb, IPM_ERR_DEVICE);
-                const uint32_t c = ok ? uint32_t(d1 - d0) : 0u;
-                const uint32_t a = ok ? uint32_t(i1 - i0) : 0u;
-                const uint64_t posA = dlo + (i0 - ilo);
-                const uint64_t posB = dlo + (ihi - ilo) + ((d0 - i0) - (dlo - ilo));
-                K *gA = buf + posA, *gB = buf + posB, *gO = buf + d0;
-                const uint32_t oo = phase_of(gO);
-                const uint32_t offA = oo + ((phase_of(gA) + VK - oo) % VK);
-                const uint32_t offB = offA + a + ((phase_of(gB) + VK - (offA + a) % VK) % VK);
-                pg.gA = gA;
-                pg.gB = gB;
-                pg.gO = gO;
-                pg.a = a;
-                pg.b = c - a;
-                pg.offA = offA;
-                pg.offB = offB;
-                pg.oo = oo;
-                if (KV) {
-                    uint32_t *vA = vals + posA, *vB = vals + posB, *vO = vals + d0;
-                    const uint32_t ooV = phase_of(vO);
-                    const uint32_t offAV = ooV + ((phase_of(vA) + VV - ooV) % VV);
-                    pg.vA = vA;
-                    pg.vB = vB;
-                    pg.vO = vO;
-                    pg.ooV = ooV;
-                    pg.offAV = offAV;
-                    pg.offBV = offAV + a + ((phase_of(vB) + VV - (offAV + a) % VV) % VV);
-                }
-            }
-        }
-        __syncthreads();
-        const uint32_t t = s_t;
+        const uint32_t t = s_t[cur];
         if (t >= P) break;
+        volatile PairGeo<K> &vg = pgs[cur];
         const uint32_t a = vg.a, b = vg.b;
 
         // ---- stage both slices
         if (a + b > 0) {
             if (tid == 0) {
-                uint32_t tx = body_bytes(pg.gA, a) + body_bytes(pg.gB, b);
-                if (KV) tx += body_bytes(pg.vA, a) + body_bytes(pg.vB, b);
+                uint32_t tx = body_bytes(pgs[cur].gA, a) + body_bytes(pgs[cur].gB, b);
+                if (KV) tx += body_bytes(pgs[cur].vA, a) + body_bytes(pgs[cur].vB, b);
                 mbar_arrive_expect_tx(mbar, tx);
             }
             stage_range<K, THREADS>(R + vg.offA, vg.gA, a, mbar);
@@ -330,11 +339,22 @@ __global__ void __launch_bounds__(THREADS, 2)
             parity ^= 1u;
         }
         __syncthreads();  // every thread's head / tail loads have landed too
+        uint32_t *ctr = gctr + (t >> F);
+        // ---- count in: this pair's slices are on chip (a timed-out stage counts in
+        // too, so that the other members are not held up before they see the error)
+        if (tid == 0) atomicAdd(ctr, 1u);
+
+        // ---- merge on chip into the output's phase (a move when a run is empty); only
+        // shared memory is written, so this needs no barrier
+        if (a + b > 0 && !abort_flag)
+            merge_two<K, KV, THREADS, E, true>(R + vg.offA, RV + vg.offAV, a,
+                                               vg.offB - vg.offA, vg.offBV - vg.offAV, b,
+                                               R + vg.oo, RV + vg.ooV);
+        fence_proxy_async_smem();
+
         // ---- group barrier: the group's region may be written once every member has
         // its slices on chip
-        if (tid == 0) {
-            uint32_t *ctr = gctr + (t >> F);
-            atomicAdd(ctr, 1u);
+        if (tid == 0 && !abort_flag) {
             unsigned long long t0 = 0;
             uint32_t it = 0;
             while (ld_acquire_u32(ctr) < gsize) {
@@ -351,27 +371,24 @@ __global__ void __launch_bounds__(THREADS, 2)
         }
         __syncthreads();
         if (abort_flag) {
-            if (tid == 0 && sb != nullptr) set_status(sb, IPM_ERR_TIMEOUT);
+            if (tid == 0) set_status(sb, IPM_ERR_TIMEOUT);
             break;
         }
-        if (a + b == 0) continue;
 
-        // ---- merge on chip into the output's phase (a move when a run is empty)
-        merge_two<K, KV, THREADS, E, true>(R + vg.offA, RV + vg.offAV, a, vg.offB - vg.offA,
-                                           vg.offBV - vg.offAV, b, R + vg.oo, RV + vg.ooV);
-        fence_proxy_async_smem();
-        __syncthreads();
-
-        // ---- store
-        const uint32_t c = vg.a + vg.b;
-        store_range<K, THREADS>(vg.gO, R + vg.oo, c);
-        if (KV) store_range<uint32_t, THREADS>(vg.vO, RV + vg.ooV, c);
+        // ---- store, and claim the next pair while the bulk store reads shared memory
+        if (a + b > 0) {
+            store_range<K, THREADS>(vg.gO, R + vg.oo, a + b);
+            if (KV) store_range<uint32_t, THREADS>(vg.vO, RV + vg.ooV, a + b);
+        }
         if (tid == 0) {
             bulk_commit();
+            s_t[cur ^ 1u] =
+                group_claim<K, KV, Shape::kTile>(pgs[cur ^ 1u], buf, vals, la, lb, split, G, F, sb);
             bulk_wait_read0();
         }
         fence_proxy_async_smem();
         __syncthreads();
+        cur ^= 1u;
     }
     if (tid == 0) bulk_wait_all0();
 }
