@@ -29,6 +29,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -438,6 +439,51 @@ def measure_learned(torch, ipm, workloads, dev, stream, steps, warmup, P=1 << 16
     }
 
 
+def measure_rotations(torch, ipm, dev, stream, steps=5, warmup=3):
+    """The partition exchange [X|Y] -> [Y|X] of 2^29 uint32 elements (2 GiB, larger
+    than L2) by linear shifting (ipm_rotate, the merge's exchange engine) and by
+    circular shifting (ipm_rotate_cs), for split points whose cycle counts
+    gcd(|X|, |Y|) span the coalesced and the scattered regime; both results are
+    compared with each other and with the definition (a roll)."""
+    peak, _ = peaks()
+    n = 1 << 29
+    half = n // 2
+    pristine = torch.randint(0, 1 << 31, (n,), dtype=torch.int64, device=dev).to(torch.int32)
+    buf = torch.empty_like(pristine)
+    out = []
+    for lx in (half, half + 64, half + 1):
+        ly = n - lx
+        res = {"len_x": lx, "len_y": ly, "cycles": math.gcd(lx, ly)}
+        kept = {}
+        for name, wsq, fn in (("ls", ipm.ipm_rotate_workspace_bytes, ipm.ipm_rotate),
+                              ("cs", ipm.ipm_rotate_cs_workspace_bytes, ipm.ipm_rotate_cs)):
+            ws = ipm.workspace(wsq(lx, ly, 4), dev)
+
+            def prep():
+                buf.copy_(pristine)
+
+            def call():
+                fn(buf, lx, ly, 4, ws)
+
+            for _ in range(warmup):
+                prep()
+                call()
+            torch.cuda.synchronize()
+            kept[name] = buf.clone()
+            ms = float(np.median(timed_steps(torch, stream, steps, prep, call)))
+            gbs = 2.0 * n * 4 / (ms * 1e-3) / 1e9
+            res[name] = {"ms": ms, "gbs": gbs, "frac": gbs / peak}
+            del ws
+        want = torch.roll(pristine, -lx)
+        res["identical"] = bool(torch.equal(kept["ls"], want) and torch.equal(kept["cs"], want))
+        res["cs_over_ls_time"] = res["cs"]["ms"] / res["ls"]["ms"]
+        del kept, want
+        out.append(res)
+    return {"workload": "exchange of 2^29 uint32 elements (2 GiB), split points with "
+                        "2^28, 128 and 1 cycles", "bytes_per_call": 2 * n * 4,
+            "peak_gbs": peak, "shapes": out}
+
+
 def _public(d):
     return {k: v for k, v in d.items() if k not in ("buffer", "pristine", "model_tensor")}
 
@@ -473,6 +519,8 @@ def run_ours(args, rank, world):
             forms["learned"] = _public(measure_learned(torch, ipm, workloads, dev, stream,
                                                        steps=5, warmup=1))
             torch.cuda.empty_cache()
+        forms["rotate"] = measure_rotations(torch, ipm, dev, stream)
+        torch.cuda.empty_cache()
         line["forms"] = forms
     print(json.dumps(line), flush=True)
 

@@ -160,6 +160,25 @@ ipm_status ipm_rotate(void *d_ptr, uint64_t len_x, uint64_t len_y, uint32_t elem
                       void *d_ws, size_t ws_bytes, ipm_stream_t stream);
 
 /*
+ * The same exchange by circular shifting (Sec. 3.4, with the cycle count of its proof
+ * of correctness: gcd(len_x, len_y) cycles): every position x takes the element at
+ * (x + len_x) mod n, followed cycle by cycle; cycles longer than a worker's share are
+ * cut into segments that run concurrently (a first launch saves each segment's first
+ * value).  Every element is read once and written once; accesses coalesce only when
+ * the cycle count is >= 32, so this is the comparison point for ipm_rotate, not the
+ * path the merge uses.  elem_bytes is 4 or 8.  The workspace (status block + at most
+ * 2^19 saved elements, <= 4 MiB + 256 B) comes from ipm_rotate_cs_workspace_bytes for
+ * the same sizes; d_ptr must be elem_bytes-aligned, d_ws 256-byte aligned.  Errors:
+ * IPM_ERR_INVALID_ARG (NULL pointer, a length above 2^40), IPM_ERR_UNSUPPORTED_DTYPE
+ * (elem_bytes), IPM_ERR_WORKSPACE, IPM_ERR_ALIGNMENT, IPM_ERR_CUDA (launch failure).
+ * len_x = 0 or len_y = 0 returns IPM_OK without touching the device.
+ */
+ipm_status ipm_rotate_cs_workspace_bytes(uint64_t len_x, uint64_t len_y, uint32_t elem_bytes,
+                                         size_t *bytes);
+ipm_status ipm_rotate_cs(void *d_ptr, uint64_t len_x, uint64_t len_y, uint32_t elem_bytes,
+                         void *d_ws, size_t ws_bytes, ipm_stream_t stream);
+
+/*
  * Algorithmic bytes the exchange levels of the last merge (or rotate) that used this
  * workspace moved (the levels that ran as exchanges; fused bottom levels move their
  * data in the pair merge instead): 2 bytes-per-element for every element of a

@@ -23,7 +23,8 @@ __all__ = [
     "IpmError", "DTYPES", "load", "ipm_status_string", "ipm_version", "ipm_merge_plan",
     "ipm_merge_workspace_bytes", "ipm_merge_inplace", "ipm_merge_inplace_kv",
     "ipm_merge_splits", "ipm_merge_rearrange", "ipm_merge_pairs",
-    "ipm_rotate_workspace_bytes", "ipm_rotate", "ipm_read_device_status",
+    "ipm_rotate_workspace_bytes", "ipm_rotate", "ipm_rotate_cs_workspace_bytes",
+    "ipm_rotate_cs", "ipm_read_device_status",
     "ipm_read_exchange_bytes",
     "ipm_timing_enable", "ipm_timing_read", "IpmTiming", "ipm_merge_inplace_noalloc",
     "workspace", "merge_inplace", "merge_inplace_kv",
@@ -70,6 +71,8 @@ _SIGS = {
     "ipm_rotate_workspace_bytes": (_i, [_u64, _u64, _u32, ctypes.POINTER(_sz)]),
     "ipm_read_exchange_bytes": (_i, [_vp, _vp, ctypes.POINTER(_u64)]),
     "ipm_rotate": (_i, [_vp, _u64, _u64, _u32, _vp, _sz, _vp]),
+    "ipm_rotate_cs_workspace_bytes": (_i, [_u64, _u64, _u32, ctypes.POINTER(_sz)]),
+    "ipm_rotate_cs": (_i, [_vp, _u64, _u64, _u32, _vp, _sz, _vp]),
     "ipm_read_device_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
     "ipm_merge_inplace_noalloc": (_i, [_vp, _u64, _u64, _i, _vp]),
     "ipm_timing_enable": (_i, [_i]),
@@ -257,6 +260,20 @@ def ipm_rotate(ptr, len_x: int, len_y: int, elem_bytes: int, ws,
     wsb = _nbytes(ws) if ws_bytes is None else ws_bytes
     _check(load().ipm_rotate(_ptr(ptr), len_x, len_y, elem_bytes, _ptr(ws), wsb,
                              _stream(stream)), "ipm_rotate")
+
+
+def ipm_rotate_cs_workspace_bytes(len_x: int, len_y: int, elem_bytes: int) -> int:
+    out = _sz(0)
+    _check(load().ipm_rotate_cs_workspace_bytes(len_x, len_y, elem_bytes, ctypes.byref(out)),
+           "ipm_rotate_cs_workspace_bytes")
+    return int(out.value)
+
+
+def ipm_rotate_cs(ptr, len_x: int, len_y: int, elem_bytes: int, ws,
+                  ws_bytes: int | None = None, stream=None) -> None:
+    wsb = _nbytes(ws) if ws_bytes is None else ws_bytes
+    _check(load().ipm_rotate_cs(_ptr(ptr), len_x, len_y, elem_bytes, _ptr(ws), wsb,
+                                _stream(stream)), "ipm_rotate_cs")
 
 
 def ipm_read_device_status(ws, stream=None) -> int:

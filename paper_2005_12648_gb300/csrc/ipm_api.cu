@@ -366,6 +366,30 @@ ipm_status ipm_rotate(void *d_ptr, uint64_t len_x, uint64_t len_y, uint32_t elem
     return launch_exchange_level(d_ptr, nullptr, t, len_x + len_y, 0, pa, sb, st);
 }
 
+ipm_status ipm_rotate_cs_workspace_bytes(uint64_t len_x, uint64_t len_y, uint32_t elem_bytes,
+                                         size_t *bytes) {
+    if (bytes == nullptr) return IPM_ERR_INVALID_ARG;
+    if (elem_bytes != 4 && elem_bytes != 8) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (len_x > (uint64_t(1) << 40) || len_y > (uint64_t(1) << 40)) return IPM_ERR_INVALID_ARG;
+    const CsPlan pl = cs_plan(len_x, len_y);
+    *bytes = kStatusBytes + align_up(size_t(pl.W) * elem_bytes, 256);
+    return IPM_OK;
+}
+
+ipm_status ipm_rotate_cs(void *d_ptr, uint64_t len_x, uint64_t len_y, uint32_t elem_bytes,
+                         void *d_ws, size_t ws_bytes, ipm_stream_t stream) {
+    size_t need = 0;
+    IPM_TRY(ipm_rotate_cs_workspace_bytes(len_x, len_y, elem_bytes, &need));
+    if (len_x == 0 || len_y == 0) return IPM_OK;
+    if (d_ptr == nullptr) return IPM_ERR_INVALID_ARG;
+    if (d_ws == nullptr || ws_bytes < need) return IPM_ERR_WORKSPACE;
+    if (!aligned(d_ptr, elem_bytes) || !aligned(d_ws, 256)) return IPM_ERR_ALIGNMENT;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = static_cast<char *>(d_ws);
+    IPM_CUDA_TRY(cudaMemsetAsync(w, 0, kStatusBytes, st));
+    return launch_cs_rotate(d_ptr, elem_bytes, cs_plan(len_x, len_y), w + kStatusBytes, st);
+}
+
 ipm_status ipm_read_exchange_bytes(const void *d_ws, ipm_stream_t stream, uint64_t *out) {
     if (d_ws == nullptr || out == nullptr) return IPM_ERR_INVALID_ARG;
     unsigned long long v = 0;

@@ -72,6 +72,17 @@ ipm_status launch_group_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t l
 // The largest F <= wanted with at least 2^F resident CTAs of the group kernel.
 uint32_t usable_group_levels(ipm_dtype key, bool with_values, uint32_t wanted);
 
+// Circular-shifting exchange (ipm_cs_rotate.cu): g = gcd(lx, ly) cycles of L = n / g
+// positions, cut into segments of S steps (W segments, each with a saved first value)
+// unless every cycle fits one worker (whole).
+struct CsPlan {
+    uint64_t lx, n, g, L, S, W;
+    bool whole;
+};
+CsPlan cs_plan(uint64_t lx, uint64_t ly);
+ipm_status launch_cs_rotate(void *ptr, uint32_t elem_bytes, const CsPlan &pl, void *save,
+                            cudaStream_t stream);
+
 // Per-pair shared-memory merge of an arranged buffer.
 ipm_status launch_tile_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
                              ipm_dtype key, const uint64_t *split, uint32_t G,

@@ -65,6 +65,12 @@ def test_host_queries(lib):
     # O(P): split table + plans, a few hundred bytes per pair at most
     assert 256 < ws < 400 * (1 << G) + 4096
     assert m.ipm_rotate_workspace_bytes(1000, 10, 4) >= 256
+    # CS: status block only when every cycle fits one worker (gcd 1000, cycles of 2)...
+    assert m.ipm_rotate_cs_workspace_bytes(1000, 1000, 4) == 256
+    # ...else one saved element per segment, at most 2^19 of them
+    assert 256 < m.ipm_rotate_cs_workspace_bytes(1000, 9, 8) <= 256 + 8 * 64
+    for lx, ly in [(1 << 28, (1 << 28) + 1), ((1 << 30) + 3, 1 << 30), (1 << 40, 1)]:
+        assert m.ipm_rotate_cs_workspace_bytes(lx, ly, 8) <= 256 + 8 * (1 << 19)
 
 
 def test_argument_errors_return_before_any_cuda_call(lib):
@@ -86,6 +92,12 @@ def test_argument_errors_return_before_any_cuda_call(lib):
     assert L.ipm_merge_splits(0x1000, 4, 4, 0, 0, 0x2000, null) == 1
     # rotate: bad element size
     assert L.ipm_rotate(0x1000, 4, 4, 2, 0x2000, 4096, null) == 2
+    assert L.ipm_rotate_cs(0x1000, 4, 4, 2, 0x2000, 4096, null) == 2
+    # CS: misaligned buffer, small workspace, NULL buffer
+    assert L.ipm_rotate_cs(0x1002, 4, 4, 4, 0x2000, 4096, null) == 3
+    assert L.ipm_rotate_cs(0x1000, 1000, 9, 4, 0x2000, 16, null) == 4
+    assert L.ipm_rotate_cs(null, 4, 4, 4, 0x2000, 4096, null) == 1
+    assert L.ipm_rotate_cs(null, 0, 4, 4, null, 0, null) == 0
     # empty inputs are a no-op that succeeds without touching the device
     assert L.ipm_merge_inplace(null, 0, 0, 0, 0, null, 0, null) == 0
     with pytest.raises(m.IpmError):
