@@ -71,6 +71,8 @@ def _declare(L: ctypes.CDLL) -> None:
         getattr(L, f"orc_srecpar_{s}").argtypes = [vp, u64, u64, ctypes.c_int, u64,
                                                    ctypes.c_int, ctypes.c_int, vp, _u64p]
         getattr(L, f"orc_arrange_{s}").argtypes = [vp, u64, vp, u64, vp, vp, u64, vp]
+        getattr(L, f"orc_division_{s}").argtypes = [vp, u64, vp, u64, ctypes.c_int,
+                                                    ctypes.c_int, vp, vp]
     L.orc_mlp_forward.argtypes = [vp, ctypes.c_int, vp, u64, vp]
     L.orc_mlp_loss_grad.argtypes = [vp, ctypes.c_int, vp, vp, u64, vp]
     L.orc_mlp_loss_grad.restype = ctypes.c_double
@@ -187,6 +189,31 @@ def srecpar(buf: np.ndarray, middle: int, depth_limit: int, size_limit: int = 1,
         {"exact": 0, "findmedian": 1}[split], {"ls": 0, "cs": 1}[shift], _p(tmp),
         ctypes.byref(mv))
     return x, int(mv.value)
+
+
+def division(a, b, depth: int, split: str = "findmedian"):
+    """Pair boundaries of the division of Alg. 3 to 2^depth pairs (no data moved):
+    (ia, jb), 2^depth + 1 entries each; pair k is A[ia[k], ia[k+1]) with
+    B[jb[k], jb[k+1]).  split is "exact" (half-diagonal stable split) or "findmedian"."""
+    a, b = _c(a), _c(b)
+    P = 1 << int(depth)
+    ia = np.zeros(P + 1, dtype=np.uint64)
+    jb = np.zeros(P + 1, dtype=np.uint64)
+    getattr(lib(), f"orc_division_{_sfx(a, b)}")(_p(a), a.size, _p(b), b.size, int(depth),
+                                                 {"exact": 0, "findmedian": 1}[split],
+                                                 _p(ia), _p(jb))
+    return ia, jb
+
+
+def division_balance(ia, jb):
+    """Largest pair of a division: (over the pairs that need a merge, i.e. both sides
+    non-empty; over all pairs).  The comparison metric of Sec. 4 is
+    (Max_FindMedian - Max_optimal) / Max_optimal of these."""
+    na = np.diff(ia.astype(np.int64))
+    nb = np.diff(jb.astype(np.int64))
+    c = na + nb
+    need = (na > 0) & (nb > 0)
+    return int(c[need].max()) if need.any() else 0, int(c.max())
 
 
 def arrange(a, b, d, i) -> np.ndarray:

@@ -330,6 +330,46 @@ void FN(orc_srecpar)(T *arr, uint64_t middle, uint64_t size, int depth_limit,
 }
 
 /*
+ * The division of Alg. 3 without the data movement (the pair boundaries its recursion
+ * reaches), for the balance comparison of Sec. 4 (FindMedian against the optimal
+ * split).  Level by level, every region [A[ia[k0], ia[k1]) | B[jb[k0], jb[k1])) is cut
+ * in two at its pivot (pA, pB): the exact stable split at the region's half diagonal
+ * floor(c/2) (split_kind 0) or FindMedian (split_kind 1).  A region with an empty side
+ * is not divided further, as in Alg. 3 (it needs no merge); it stays whole in its left
+ * child and its right child is empty.  Outputs the 2^depth + 1 boundaries:
+ * pair k = A[ia[k], ia[k+1]) with B[jb[k], jb[k+1]).
+ */
+void FN(orc_division)(const T *a, uint64_t la, const T *b, uint64_t lb, int depth,
+                      int split_kind, uint64_t *ia, uint64_t *jb)
+{
+    const uint64_t P = (uint64_t)1 << depth;
+    ia[0] = 0;
+    jb[0] = 0;
+    ia[P] = la;
+    jb[P] = lb;
+    for (int l = 0; l < depth; ++l) {
+        const uint64_t step = P >> l;
+        for (uint64_t k0 = 0; k0 < P; k0 += step) {
+            const uint64_t k1 = k0 + step, mid = k0 + step / 2;
+            const uint64_t ra = ia[k1] - ia[k0], rb = jb[k1] - jb[k0];
+            uint64_t pa, pb;
+            if (ra == 0 || rb == 0) {
+                pa = ra;
+                pb = rb;
+            } else if (split_kind == 0) {
+                const uint64_t d = (ra + rb) / 2;
+                pa = FN(orc_split_bsearch)(a + ia[k0], ra, b + jb[k0], rb, d);
+                pb = d - pa;
+            } else {
+                FN(orc_findmedian)(a + ia[k0], ra, b + jb[k0], rb, &pa, &pb);
+            }
+            ia[mid] = ia[k0] + pa;
+            jb[mid] = jb[k0] + pb;
+        }
+    }
+}
+
+/*
  * The layout the division stage produces (Sec. 3): A_0 B_0 A_1 B_1 ... A_{P-1}
  * B_{P-1}, where pair k holds A[i_k, i_{k+1}) and B[j_k, j_{k+1}) with
  * j_k = d_k - i_k.  Written out of place from the split table (d, i), P+1 entries.

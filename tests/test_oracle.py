@@ -313,3 +313,85 @@ def test_adam_first_step_closed_form(orc):
     orc.adam_step(p, m, v, g, lr, 0.9, 0.999, eps, 1)
     # first step: mhat = g, vhat = g^2  ->  p - lr * g / (|g| + eps)
     assert np.allclose(p, p0 - lr * g / (np.abs(g) + eps), rtol=1e-12, atol=0)
+
+
+# ------------------------------------------------- division balance (Sec. 4, E1)
+
+def _halving_sizes(n, depth):
+    """Sizes after depth levels of cutting every region at floor(c/2)."""
+    sizes = [n]
+    for _ in range(depth):
+        sizes = [s for c in sizes for s in (c // 2, c - c // 2)]
+    return sizes
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3, 5])
+def test_division_exact_halves_every_region(orc, depth):
+    """When no region runs out of one side, the exact split cuts each region at its half
+    diagonal: the pair sizes are the recursive floor / ceil halves of n."""
+    for la, lb in [(1000, 1000), (1000, 999), (4096, 4095), (2048, 2049)]:
+        a = np.arange(la, dtype=np.int64).astype(np.int32) * 2
+        b = np.arange(lb, dtype=np.int64).astype(np.int32) * 2 + 1
+        ia, jb = orc.division(a, b, depth, "exact")
+        sizes = (np.diff(ia.astype(np.int64)) + np.diff(jb.astype(np.int64))).tolist()
+        assert sizes == _halving_sizes(la + lb, depth)
+
+
+@pytest.mark.parametrize("split", ["exact", "findmedian"])
+def test_division_is_a_partition_of_the_merge(orc, split):
+    """Brute force on small runs with many ties: every division yields pairs whose
+    separate merges, concatenated, are the sorted whole (the exact split also keeps the
+    stable order of equal keys)."""
+    rng = random.Random(17)
+    for _ in range(300):
+        la, lb = rng.randint(0, 40), rng.randint(0, 40)
+        a, b = workloads.make_pair(rng.choice(["dup16", "uniform", "paper"]), np.int32, la,
+                                   lb, seed=rng.randint(0, 9999))
+        depth = rng.randint(1, 4)
+        ia, jb = orc.division(a, b, depth, split)
+        assert ia[0] == 0 and jb[0] == 0 and ia[-1] == la and jb[-1] == lb
+        assert np.all(np.diff(ia.astype(np.int64)) >= 0)
+        assert np.all(np.diff(jb.astype(np.int64)) >= 0)
+        # keys with their origin (0 = A, 1 = B) and index: the stable merge order
+        ka = [(int(x), 0, i) for i, x in enumerate(a)]
+        kb = [(int(x), 1, j) for j, x in enumerate(b)]
+        out = []
+        for k in range(len(ia) - 1):
+            part = ka[int(ia[k]):int(ia[k + 1])] + kb[int(jb[k]):int(jb[k + 1])]
+            out += sorted(part)  # (key, origin, index): a tie takes A, then index order
+        keys = [t[0] for t in out]
+        assert keys == sorted(keys)
+        if split == "exact":
+            assert out == sorted(ka + kb)
+
+
+def test_division_stops_at_one_sided_regions(orc):
+    # A entirely below B: FindMedian's first corner case gives (|A|, 0); each side is
+    # then whole in one region and the deeper levels leave it as it is
+    a = np.arange(10, dtype=np.int32)
+    b = np.arange(10, 30, dtype=np.int32)
+    ia, jb = orc.division(a, b, 3, "findmedian")
+    na, nb = np.diff(ia.astype(np.int64)), np.diff(jb.astype(np.int64))
+    assert sorted((na + nb).tolist(), reverse=True)[:2] == [20, 10]
+    assert not np.any((na > 0) & (nb > 0))
+    assert orc.division_balance(ia, jb) == (0, 20)
+    # depth 1 is one call of FindMedian
+    for seed in range(20):
+        a, b = workloads.make_pair("paper", np.int32, 300 + seed, 500, seed=seed)
+        ia, jb = orc.division(a, b, 1, "findmedian")
+        assert (int(ia[1]), int(jb[1])) == orc.findmedian(a, b)
+
+
+def test_division_findmedian_close_to_exact_on_the_paper_workload(orc):
+    """Sec. 4 reports the FindMedian division as close to the optimal one on its
+    workload, sometimes better (one-sided regions need no merge); under this reading the
+    largest pair that needs a merge differs by a relative 5e-3 at most, either way, for
+    T = 2..16 and the three split points."""
+    n = 1 << 16
+    for frac in (0.25, 0.5, 0.75):
+        la = int(n * frac)
+        a, b = workloads.make_pair("paper", np.int32, la, n - la, seed=4)
+        for depth in (1, 2, 3, 4):
+            fm = orc.division_balance(*orc.division(a, b, depth, "findmedian"))[0]
+            ex = orc.division_balance(*orc.division(a, b, depth, "exact"))[0]
+            assert ex > 0 and abs(fm - ex) / ex < 5e-3, (frac, depth, fm, ex)
