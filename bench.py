@@ -480,8 +480,71 @@ def measure_rotations(torch, ipm, dev, stream, steps=5, warmup=3):
         del kept, want
         out.append(res)
     return {"workload": "exchange of 2^29 uint32 elements (2 GiB), split points with "
-                        "2^28, 128 and 1 cycles", "bytes_per_call": 2 * n * 4,
+                        "2^28, 64 and 1 cycles", "bytes_per_call": 2 * n * 4,
             "peak_gbs": peak, "shapes": out}
+
+
+def _largest_pairs(ia, jb):
+    """Largest pair of a division: over the pairs that need a merge (both sides
+    non-empty) and over all pairs."""
+    na = np.diff(ia.astype(np.int64))
+    nb = np.diff(jb.astype(np.int64))
+    c = na + nb
+    need = (na > 0) & (nb > 0)
+    return (int(c[need].max()) if need.any() else 0), int(c.max())
+
+
+def measure_division(torch, ipm, workloads, dev, stream, steps=10, warmup=3):
+    """The balance comparison of Sec. 4 (E1): the division of Alg. 3 by FindMedian
+    against the optimal (exact half-diagonal) split, (Max_FM - Max_opt) / Max_opt of
+    the largest pair that needs a merge, on the paper's random-walk workload at its
+    largest size (2^22 int32 keys) split at 1/4, 1/2, 3/4, for T = 2..16; and at the
+    merge's own scale (2^28 + 2^28 uniform int32, T = 2^15), with the time of the
+    FindMedian division against the exact splits the merge uses."""
+    table = []
+    n = 1 << 22
+    for frac in (0.25, 0.5, 0.75):
+        la = int(n * frac)
+        buf = workloads.make_buffer_torch(torch, "paper", np.int32, la, n - la, 4, dev)
+        row = {"split_at": frac, "T": [], "rel_diff": [], "rel_diff_all_pairs": []}
+        for depth in (1, 2, 3, 4):
+            fm = _largest_pairs(*[t.cpu().numpy() for t in ipm.division_splits(
+                buf, la, n - la, "int32", depth, "findmedian")])
+            ex = _largest_pairs(*[t.cpu().numpy() for t in ipm.division_splits(
+                buf, la, n - la, "int32", depth, "exact")])
+            row["T"].append(1 << depth)
+            row["rel_diff"].append((fm[0] - ex[0]) / ex[0])
+            row["rel_diff_all_pairs"].append((fm[1] - ex[1]) / ex[1])
+        table.append(row)
+        del buf
+    la = lb = 1 << 28
+    buf = workloads.make_buffer_torch(torch, "uniform", np.int32, la, lb, 0, dev)
+    depth = 15
+    fm = _largest_pairs(*[t.cpu().numpy() for t in ipm.division_splits(
+        buf, la, lb, "int32", depth, "findmedian")])
+    ex = _largest_pairs(*[t.cpu().numpy() for t in ipm.division_splits(
+        buf, la, lb, "int32", depth, "exact")])
+    ia = torch.empty((1 << depth) + 1, dtype=torch.int64, device=dev)
+    jb = torch.empty_like(ia)
+    split = torch.empty_like(ia)
+    times = {}
+    for name, call in (
+            ("findmedian_division", lambda: ipm.ipm_division_splits(
+                buf, la, lb, "int32", depth, "findmedian", ia, jb)),
+            ("exact_division", lambda: ipm.ipm_division_splits(
+                buf, la, lb, "int32", depth, "exact", ia, jb)),
+            ("merge_splits", lambda: ipm.ipm_merge_splits(buf, la, lb, "int32", 1 << depth,
+                                                          split))):
+        for _ in range(warmup):
+            call()
+        times[name] = float(np.median(timed_steps(torch, stream, steps, lambda: None, call)))
+    return {"workload": "paper random walk x[i] = x[i-1] + floor(5 U), 2^22 int32 keys; "
+                        "uniform int32 2^28 + 2^28 at T = 2^15",
+            "metric": "(Max_FindMedian - Max_optimal) / Max_optimal, largest pair that "
+                      "needs a merge", "paper_workload_2p22": table,
+            "uniform_2p29": {"T": 1 << depth, "max_pair_findmedian": fm[0],
+                             "max_pair_exact": ex[0], "rel_diff": (fm[0] - ex[0]) / ex[0],
+                             "ms": times}}
 
 
 def _public(d):
@@ -520,6 +583,8 @@ def run_ours(args, rank, world):
                                                        steps=5, warmup=1))
             torch.cuda.empty_cache()
         forms["rotate"] = measure_rotations(torch, ipm, dev, stream)
+        torch.cuda.empty_cache()
+        forms["division"] = measure_division(torch, ipm, workloads, dev, stream)
         torch.cuda.empty_cache()
         line["forms"] = forms
     print(json.dumps(line), flush=True)

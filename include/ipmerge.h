@@ -125,6 +125,31 @@ ipm_status ipm_merge_splits(const void *d_buf, uint64_t len_a, uint64_t len_b,
                             ipm_stream_t stream);
 
 /*
+ * The division of Alg. 3 (sRecPar, Sec. 3.3) to 2^depth pairs without moving data,
+ * for the balance comparison of Sec. 4 between FindMedian (Alg. 1, Sec. 3.1) and the
+ * optimal split.  Level by level (depth levels), every region
+ * A[d_ia[k0], d_ia[k1]) | B[d_jb[k0], d_jb[k1]) is cut at its pivot (pA, pB):
+ *   IPM_SPLIT_EXACT       the exact stable split at the region's half diagonal
+ *                         floor(c/2) (the optimal balance);
+ *   IPM_SPLIT_FINDMEDIAN  FindMedian, read as: both corner cases first (A before B:
+ *                         (|A|, 0); A after B: (0, |B|)); the midpoints recomputed at the
+ *                         top of each iteration and returned when their keys are equal;
+ *                         the midpoints of the final intervals when one empties.
+ * A region with an empty side is not divided (Alg. 3 stops there): it stays whole in
+ * its left child and the right child is empty.  d_ia and d_jb (device, caller-owned)
+ * receive 2^depth + 1 boundaries each: pair k is A[d_ia[k], d_ia[k+1]) with
+ * B[d_jb[k], d_jb[k+1]).  d_buf = A|B is only read.  depth <= 24.  One launch per
+ * level, asynchronous on `stream`.  Errors: IPM_ERR_INVALID_ARG (NULL pointers, depth,
+ * split_kind), IPM_ERR_UNSUPPORTED_DTYPE, IPM_ERR_ALIGNMENT (d_buf not aligned to the
+ * key size, d_ia / d_jb not 8-byte aligned), IPM_ERR_CUDA.
+ */
+#define IPM_SPLIT_EXACT 0u
+#define IPM_SPLIT_FINDMEDIAN 1u
+ipm_status ipm_division_splits(const void *d_buf, uint64_t len_a, uint64_t len_b,
+                               ipm_dtype key_dtype, uint32_t depth, uint32_t split_kind,
+                               uint64_t *d_ia, uint64_t *d_jb, ipm_stream_t stream);
+
+/*
  * Step 2 alone: the division stage of Alg. 3 applied to d_buf from a split table made
  * by ipm_merge_splits with P = 2^log2_pairs.  Afterwards pair k occupies
  * d_buf[d_k, d_{k+1}) as A[i_k, i_{k+1}) followed by B[j_k, j_{k+1}).  d_vals may be

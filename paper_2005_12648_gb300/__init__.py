@@ -24,7 +24,8 @@ __all__ = [
     "ipm_merge_workspace_bytes", "ipm_merge_inplace", "ipm_merge_inplace_kv",
     "ipm_merge_splits", "ipm_merge_rearrange", "ipm_merge_pairs",
     "ipm_rotate_workspace_bytes", "ipm_rotate", "ipm_rotate_cs_workspace_bytes",
-    "ipm_rotate_cs", "ipm_read_device_status",
+    "ipm_rotate_cs", "ipm_division_splits", "SPLIT_KINDS", "division_splits",
+    "ipm_read_device_status",
     "ipm_read_exchange_bytes",
     "ipm_timing_enable", "ipm_timing_read", "IpmTiming", "ipm_merge_inplace_noalloc",
     "workspace", "merge_inplace", "merge_inplace_kv",
@@ -73,6 +74,7 @@ _SIGS = {
     "ipm_rotate": (_i, [_vp, _u64, _u64, _u32, _vp, _sz, _vp]),
     "ipm_rotate_cs_workspace_bytes": (_i, [_u64, _u64, _u32, ctypes.POINTER(_sz)]),
     "ipm_rotate_cs": (_i, [_vp, _u64, _u64, _u32, _vp, _sz, _vp]),
+    "ipm_division_splits": (_i, [_vp, _u64, _u64, _i, _u32, _u32, _vp, _vp, _vp]),
     "ipm_read_device_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
     "ipm_merge_inplace_noalloc": (_i, [_vp, _u64, _u64, _i, _vp]),
     "ipm_timing_enable": (_i, [_i]),
@@ -274,6 +276,30 @@ def ipm_rotate_cs(ptr, len_x: int, len_y: int, elem_bytes: int, ws,
     wsb = _nbytes(ws) if ws_bytes is None else ws_bytes
     _check(load().ipm_rotate_cs(_ptr(ptr), len_x, len_y, elem_bytes, _ptr(ws), wsb,
                                 _stream(stream)), "ipm_rotate_cs")
+
+
+SPLIT_KINDS = {"exact": 0, "findmedian": 1}
+
+
+def ipm_division_splits(buf, len_a: int, len_b: int, key_dtype, depth: int, split_kind,
+                        ia, jb, stream=None) -> None:
+    kind = SPLIT_KINDS[split_kind] if isinstance(split_kind, str) else int(split_kind)
+    _check(load().ipm_division_splits(_ptr(buf), len_a, len_b, _dt(key_dtype), depth, kind,
+                                      _ptr(ia), _ptr(jb), _stream(stream)),
+           "ipm_division_splits")
+
+
+def division_splits(buf, len_a: int, len_b: int, key_dtype, depth: int,
+                    split_kind="findmedian", stream=None):
+    """Pair boundaries of the division of Alg. 3 to 2^depth pairs, as two int64 device
+    tensors (ia, jb) of 2^depth + 1 entries (pair k: A[ia[k], ia[k+1]) with
+    B[jb[k], jb[k+1]))."""
+    import torch
+
+    ia = torch.empty((1 << depth) + 1, dtype=torch.int64, device=buf.device)
+    jb = torch.empty_like(ia)
+    ipm_division_splits(buf, len_a, len_b, key_dtype, depth, split_kind, ia, jb, stream)
+    return ia, jb
 
 
 def ipm_read_device_status(ws, stream=None) -> int:

@@ -366,6 +366,20 @@ ipm_status ipm_rotate(void *d_ptr, uint64_t len_x, uint64_t len_y, uint32_t elem
     return launch_exchange_level(d_ptr, nullptr, t, len_x + len_y, 0, pa, sb, st);
 }
 
+ipm_status ipm_division_splits(const void *d_buf, uint64_t len_a, uint64_t len_b,
+                               ipm_dtype key_dtype, uint32_t depth, uint32_t split_kind,
+                               uint64_t *d_ia, uint64_t *d_jb, ipm_stream_t stream) {
+    if (dtype_bytes(key_dtype) == 0) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (depth > 24 || split_kind > IPM_SPLIT_FINDMEDIAN) return IPM_ERR_INVALID_ARG;
+    if (d_ia == nullptr || d_jb == nullptr) return IPM_ERR_INVALID_ARG;
+    if (len_a + len_b > 0 && d_buf == nullptr) return IPM_ERR_INVALID_ARG;
+    if (len_a > (uint64_t(1) << 40) || len_b > (uint64_t(1) << 40)) return IPM_ERR_INVALID_ARG;
+    if (!aligned(d_buf, size_t(dtype_bytes(key_dtype))) || !aligned(d_ia, 8) || !aligned(d_jb, 8))
+        return IPM_ERR_ALIGNMENT;
+    return launch_division(d_buf, len_a, len_b, key_dtype, depth, split_kind, d_ia, d_jb,
+                           (cudaStream_t)stream);
+}
+
 ipm_status ipm_rotate_cs_workspace_bytes(uint64_t len_x, uint64_t len_y, uint32_t elem_bytes,
                                          size_t *bytes) {
     if (bytes == nullptr) return IPM_ERR_INVALID_ARG;

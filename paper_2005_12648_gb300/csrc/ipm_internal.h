@@ -72,6 +72,11 @@ ipm_status launch_group_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t l
 // The largest F <= wanted with at least 2^F resident CTAs of the group kernel.
 uint32_t usable_group_levels(ipm_dtype key, bool with_values, uint32_t wanted);
 
+// Division of Alg. 3 to 2^depth pairs (ipm_division.cu): the pair boundaries only.
+ipm_status launch_division(const void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
+                           uint32_t depth, uint32_t kind, uint64_t *ia, uint64_t *jb,
+                           cudaStream_t stream);
+
 // Circular-shifting exchange (ipm_cs_rotate.cu): g = gcd(lx, ly) cycles of L = n / g
 // positions, cut into segments of S steps (W segments, each with a saved first value)
 // unless every cycle fits one worker (whole).

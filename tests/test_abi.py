@@ -98,6 +98,14 @@ def test_argument_errors_return_before_any_cuda_call(lib):
     assert L.ipm_rotate_cs(0x1000, 1000, 9, 4, 0x2000, 16, null) == 4
     assert L.ipm_rotate_cs(null, 4, 4, 4, 0x2000, 4096, null) == 1
     assert L.ipm_rotate_cs(null, 0, 4, 4, null, 0, null) == 0
+    # division: depth, split kind, dtype, NULL outputs, alignment
+    assert L.ipm_division_splits(0x1000, 4, 4, 0, 25, 0, 0x2000, 0x3000, null) == 1
+    assert L.ipm_division_splits(0x1000, 4, 4, 0, 3, 2, 0x2000, 0x3000, null) == 1
+    assert L.ipm_division_splits(0x1000, 4, 4, 7, 3, 0, 0x2000, 0x3000, null) == 2
+    assert L.ipm_division_splits(0x1000, 4, 4, 0, 3, 0, null, 0x3000, null) == 1
+    assert L.ipm_division_splits(null, 4, 4, 0, 3, 0, 0x2000, 0x3000, null) == 1
+    assert L.ipm_division_splits(0x1004, 4, 4, 2, 3, 0, 0x2000, 0x3000, null) == 3
+    assert L.ipm_division_splits(0x1000, 4, 4, 0, 3, 0, 0x2004, 0x3000, null) == 3
     # empty inputs are a no-op that succeeds without touching the device
     assert L.ipm_merge_inplace(null, 0, 0, 0, 0, null, 0, null) == 0
     with pytest.raises(m.IpmError):

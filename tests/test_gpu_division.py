@@ -1,0 +1,74 @@
+"""GPU parity of the division of Alg. 3 (pair boundaries, FindMedian or exact splits)
+against the oracle's, bit for bit, and the balance comparison of Sec. 4 (E1)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import NAME, to_dev
+
+pytestmark = pytest.mark.gpu
+
+DISTS = ["paper", "uniform", "dup16", "zipf", "disjoint", "revdisjoint", "alternation"]
+
+
+def _gpu_division(ipm, buf, la, lb, dt, depth, split):
+    import torch
+
+    ia, jb = ipm.division_splits(buf, la, lb, NAME[np.dtype(dt)], depth, split)
+    torch.cuda.synchronize()
+    return ia.cpu().numpy().astype(np.uint64), jb.cpu().numpy().astype(np.uint64)
+
+
+@pytest.mark.parametrize("split", ["exact", "findmedian"])
+@pytest.mark.parametrize("dt", [np.int32, np.uint32, np.uint64, np.float32])
+def test_division_matches_oracle(ipm, dev, orc, split, dt):
+    sizes = [(0, 0), (0, 17), (17, 0), (1, 1), (1, 1000), (1000, 1), (5000, 5000),
+             (12_345, 67_890), (65_536, 16_384), (100_003, 99_991)]
+    for dist in DISTS:
+        for la, lb in sizes:
+            a, b = W.make_pair(dist, dt, la, lb, seed=la * 7 + lb)
+            buf = to_dev(np.concatenate([a, b]), dev)
+            for depth in (0, 1, 3, 6, 9):
+                got = _gpu_division(ipm, buf, la, lb, dt, depth, split)
+                want = orc.division(a, b, depth, split)
+                assert np.array_equal(got[0], want[0]), (dist, la, lb, depth)
+                assert np.array_equal(got[1], want[1]), (dist, la, lb, depth)
+
+
+@pytest.mark.parametrize("frac", [0.25, 0.5, 0.75])
+def test_e1_balance_paper_workload_2p22(ipm, dev, orc, frac):
+    """The paper's largest size, S = 2^22 int32 keys of its random-walk workload split
+    at 1/4, 1/2 and 3/4, T = 2..2^12: boundaries equal the oracle's for both splits; for
+    the paper's thread counts (T <= 16) the largest pair that needs a merge stays within
+    0.5 % of the optimal one (deeper, FindMedian drifts: ~3 % at T = 4096)."""
+    n = 1 << 22
+    la = int(n * frac)
+    a, b = W.make_pair("paper", np.int32, la, n - la, seed=11)
+    buf = to_dev(np.concatenate([a, b]), dev)
+    for depth in (1, 2, 3, 4, 8, 12):
+        res = {}
+        for split in ("exact", "findmedian"):
+            got = _gpu_division(ipm, buf, la, n - la, np.int32, depth, split)
+            want = orc.division(a, b, depth, split)
+            assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+            res[split] = orc.division_balance(*got)[0]
+        if depth <= 4:
+            assert abs(res["findmedian"] - res["exact"]) <= 5e-3 * res["exact"], (depth, res)
+
+
+@pytest.mark.slow
+def test_division_fullsize_uniform_2p28x2(ipm, dev, orc):
+    """2^28 + 2^28 uniform int32 at 2^15 pairs (the merge's pair count): boundaries equal
+    the oracle's; the exact division's pairs are the halving sizes."""
+    import torch
+
+    la = lb = 1 << 28
+    buf = W.make_buffer_torch(torch, "uniform", np.int32, la, lb, 0, dev)
+    host = W.as_numpy_keys(buf, np.int32)
+    for split in ("exact", "findmedian"):
+        got = _gpu_division(ipm, buf, la, lb, np.int32, 15, split)
+        want = orc.division(host[:la], host[la:], 15, split)
+        assert np.array_equal(got[0], want[0]) and np.array_equal(got[1], want[1])
+        if split == "exact":
+            sizes = np.diff(got[0].astype(np.int64)) + np.diff(got[1].astype(np.int64))
+            assert set(sizes.tolist()) == {1 << 14}
