@@ -696,16 +696,18 @@ __global__ void __launch_bounds__(512, 1)
 
 // ---------------------------------------------------------------------------------
 // Warp-specialized executor: warp 0 is the producer (claims tickets, decodes items,
-// waits for an item's earlier LS steps, stages its blocks into a free stage), warps
-// 1..15 are the consumers (publish "reads done", wait for the flags their stores
-// depend on, store, release the stage).  Two stages; the producer stages the next item
-// while the consumers store the current one, so ticket claims and decoding stay off the
-// consumers' path.  As in the single-role executor, a CTA holds at most two claimed
-// items and claims only into a free stage (a claimed item is staged at once, so its
-// "reads done" is published as soon as its data lands), holder items (which wait on
-// later tickets of their own exchange) are drained before the next claim, and a SINGLE
-// exchange (both stages) waits for both stages to drain: the same deadlock-freedom
-// argument.
+// waits for an item's earlier LS steps, stages its blocks into a free stage, publishes
+// "reads done" as soon as the data has landed), warps 1..15 are the consumers (publish
+// "reads done" if the producer has not, wait for the flags their stores depend on,
+// store, release the stage).  Two stages; the producer stages the next item while the
+// consumers store the current one, and claims the ticket after it as soon as it has
+// staged one, so ticket claims and decoding stay off the consumers' path.  Deadlock
+// freedom: a claimed item waits only for a stage of its own CTA (and, after LS steps,
+// for those steps); the stages hold earlier items, which wait only on earlier tickets;
+// a stash holder, the one item that waits on later tickets (of its own exchange), is
+// drained before the next claim; and a SINGLE exchange (both stages) waits for both
+// stages to drain.  So by induction on the ticket order every claimed item is staged,
+// every "reads done" is published and every wait ends.
 // ---------------------------------------------------------------------------------
 
 constexpr uint32_t kWsConsumers = 480;  // threads 32..511
@@ -762,9 +764,32 @@ __device__ __forceinline__ bool decode_item_warp(const XParams &prm, uint32_t t,
     return true;
 }
 
-// Producer warp: stage the item's source blocks (TMA bodies by lane 0, heads and tails
-// by lanes 8i..8i+7 (keys) and 16+8i.. (values) written straight to shared memory),
-// then arrive on the stage's "full" barrier.
+// Producer warp: stage the item's source blocks, then arrive on the stage's "full"
+// barrier.  Each range is loaded whole by one bulk copy of the 16-byte lines it
+// occupies (its first line from the start, its last line to the end): the copy keeps
+// the range's phase in shared memory (element j at offset off + j, as the stores
+// expect) and never leaves the lines that hold the range's own elements, so it stays
+// within the buffer's pages; the few neighbouring elements it also copies are never
+// stored.  No element is loaded with a plain load, so the producer never waits for
+// global memory here.
+template <typename T>
+__device__ __forceinline__ uint32_t line_span_bytes(const T *g, uint32_t len) {
+    if (len == 0) return 0;
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(g) & ~uintptr_t(15);
+    const uintptr_t hi = (reinterpret_cast<uintptr_t>(g + len) + 15) & ~uintptr_t(15);
+    return uint32_t(hi - lo);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_line_span(T *slot, const T *g, uint32_t len,
+                                               uint64_t *full) {
+    const uint32_t bytes = line_span_bytes(g, len);
+    if (bytes)
+        bulk_load(slot, reinterpret_cast<const T *>(reinterpret_cast<uintptr_t>(g) &
+                                                    ~uintptr_t(15)),
+                  bytes, full);
+}
+
 template <typename K, bool KV>
 __device__ __forceinline__ void stage_load_ws(const Item &it, const K *buf, const uint32_t *vals,
                                               unsigned char *stage, unsigned char *base,
@@ -772,58 +797,20 @@ __device__ __forceinline__ void stage_load_ws(const Item &it, const K *buf, cons
     using C = XCfg<K, KV>;
     K *sk = stage_keys<K, KV>(it, stage, base);
     uint32_t *sv = stage_vals<K, KV>(it, stage, base);
-    const uint32_t lane = threadIdx.x & 31u;
-    if (lane == 0) {
-        uint32_t tx = 0;
-        for (uint32_t i = 0; i < it.nmoves; ++i) {
-            const Geo<int(sizeof(K))> gk(buf + it.mv[i].src, uint32_t(it.mv[i].len));
-            tx += gk.body * uint32_t(sizeof(K));
-            if (KV) {
-                const Geo<4> gv(vals + it.mv[i].src, uint32_t(it.mv[i].len));
-                tx += gv.body * 4u;
-            }
-        }
-        mbar_expect_tx(full, tx);
-    }
-    __syncwarp();
+    if ((threadIdx.x & 31u) != 0) return;
+    uint32_t tx = 0;
     for (uint32_t i = 0; i < it.nmoves; ++i) {
-        const Move &mv = it.mv[i];
-        const uint32_t len = uint32_t(mv.len);
-        const K *g = buf + mv.src;
-        const Geo<int(sizeof(K))> gk(g, len);
-        if (lane == 0 && gk.body)
-            bulk_load(sk + i * C::kSlotK + gk.off + gk.head, g + gk.head,
-                      gk.body * uint32_t(sizeof(K)), full);
-        if (lane >= 8 * i && lane < 8 * i + 8) {
-            const uint32_t e = lane - 8 * i;
-            const uint32_t ntail = len - gk.tail_start;
-            uint32_t jj = ~0u;
-            if (e < 4 && e < gk.head)
-                jj = e;
-            else if (e >= 4 && e - 4 < ntail)
-                jj = gk.tail_start + (e - 4);
-            if (jj != ~0u) sk[i * C::kSlotK + gk.off + jj] = __ldcg(g + jj);
-        }
-        if (KV) {
-            const uint32_t *gv = vals + mv.src;
-            const Geo<4> gvv(gv, len);
-            if (lane == 0 && gvv.body)
-                bulk_load(sv + i * C::kSlotV + gvv.off + gvv.head, gv + gvv.head, gvv.body * 4u,
-                          full);
-            if (lane >= 16 + 8 * i && lane < 24 + 8 * i) {
-                const uint32_t e = lane - 16 - 8 * i;
-                const uint32_t ntail = len - gvv.tail_start;
-                uint32_t jj = ~0u;
-                if (e < 4 && e < gvv.head)
-                    jj = e;
-                else if (e >= 4 && e - 4 < ntail)
-                    jj = gvv.tail_start + (e - 4);
-                if (jj != ~0u) sv[i * C::kSlotV + gvv.off + jj] = __ldcg(gv + jj);
-            }
-        }
+        const uint32_t len = uint32_t(it.mv[i].len);
+        tx += line_span_bytes(buf + it.mv[i].src, len);
+        if (KV) tx += line_span_bytes(vals + it.mv[i].src, len);
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(full);
+    mbar_expect_tx(full, tx);
+    for (uint32_t i = 0; i < it.nmoves; ++i) {
+        const uint32_t len = uint32_t(it.mv[i].len);
+        load_line_span(sk + i * C::kSlotK, buf + it.mv[i].src, len, full);
+        if (KV) load_line_span(sv + i * C::kSlotV, vals + it.mv[i].src, len, full);
+    }
+    mbar_arrive(full);
 }
 
 // dst[0, len) = src[0, len) by the consumer threads (ctid < kWsConsumers).
@@ -963,39 +950,77 @@ __global__ void __launch_bounds__(512, 1)
         uint32_t arrivals[2] = {0, 0};  // phases of full[q] the producer has started
         uint32_t rot = 0;
         uint32_t st = 0;
+        // "reads done" of the items staged last, published (lane 0) as soon as their
+        // data has landed, while the producer waits for a stage: the flags never wait
+        // for this CTA's consumers to reach the item
+        bool pend_on[2] = {false, false};
+        uint32_t pend_par[2] = {0, 0}, pend_ticket[2] = {0, 0};
+        auto try_publish = [&]() {
+            for (uint32_t q = 0; q < 2; ++q)
+                if (pend_on[q] && mbar_try_wait(&full[q], pend_par[q])) {
+                    st_flag(flags + pend_ticket[q], tag);
+                    pend_on[q] = false;
+                }
+        };
         // wait until every item issued to stage q has been released by the consumers
         auto drain = [&](uint32_t q) -> bool {
             while (drained[q] < issued[q]) {
                 bool ok = true;
-                if (lane == 0) ok = mbar_wait_bounded(&empty[q], drained[q] & 1u);
+                if (lane == 0) {
+                    unsigned long long t0 = 0;
+                    for (uint32_t i = 0;; ++i) {
+                        if (mbar_try_wait(&empty[q], drained[q] & 1u)) break;
+                        try_publish();
+                        if ((i & 255u) == 0) {
+                            const unsigned long long now = globaltimer_ns();
+                            if (t0 == 0) {
+                                t0 = now;
+                            } else if (now - t0 > kWaitLimitNs) {
+                                ok = false;
+                                break;
+                            }
+                        }
+                    }
+                }
                 ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
                 if (!ok) return false;
                 ++drained[q];
             }
             return true;
         };
-        for (;;) {
-            // Free the stage before claiming: a claimed item is then always staged at
-            // once, so its "reads done" can be published as soon as its data lands (a
-            // stash holder elsewhere may be waiting for it while this CTA's consumers
-            // wait for that holder).
-            if (!drain(st)) {
-                if (lane == 0) {
-                    set_status(sb, IPM_ERR_TIMEOUT);
-                    sh.abort = 1;
-                }
-                break;
-            }
-            uint32_t t = 0;
+        // claim and decode the next ticket (the whole warp)
+        auto claim = [&](Item &it, uint32_t &t) -> bool {
+            t = 0;
             if (lane == 0) t = atomicAdd(ctr, 1u);
             t = __shfl_sync(0xffffffffu, t, 0);
-            bool fail = false;
-            Item it;
             if (t < total && !decode_item_warp(prm, t, rot, pf, plans, nrot, n, it)) {
                 if (lane == 0) set_status(sb, IPM_ERR_DEVICE);
-                fail = true;
+                return false;
             }
-            if (t >= total || fail || *((volatile int *)&sh.abort)) {
+            return true;
+        };
+        auto fail_timeout = [&]() {
+            if (lane == 0) {
+                set_status(sb, IPM_ERR_TIMEOUT);
+                sh.abort = 1;
+            }
+        };
+        // The next ticket is claimed as soon as the current item is staged, so its
+        // claim and decode overlap the wait for a free stage.  A claimed item waits for
+        // nothing but a stage of this CTA (and, after LS steps, for those steps), and
+        // the stages hold only earlier items that wait on earlier tickets; a stash
+        // holder, the one item that waits on later tickets, is drained before the next
+        // claim.  So every claimed ticket gets staged and every "reads done" gets
+        // published.
+        Item it;
+        uint32_t t = 0;
+        bool ok_claim = claim(it, t);
+        for (;;) {
+            if (!drain(st)) {
+                fail_timeout();
+                break;
+            }
+            if (t >= total || !ok_claim || *((volatile int *)&sh.abort)) {
                 // end marker for the consumers in the next stage (free: drained above)
                 if (lane == 0) {
                     sh.end[st] = 1;
@@ -1013,10 +1038,7 @@ __global__ void __launch_bounds__(512, 1)
                 ok = __shfl_sync(0xffffffffu, w, 0) != 0;
             }
             if (!ok) {
-                if (lane == 0) {
-                    set_status(sb, IPM_ERR_TIMEOUT);
-                    sh.abort = 1;
-                }
+                fail_timeout();
                 break;
             }
             if (lane == 0) {
@@ -1026,19 +1048,22 @@ __global__ void __launch_bounds__(512, 1)
             __syncwarp();
             unsigned char *stage = xsmem + (st ? C::kStageSize : 0);
             stage_load_ws<K, KV>(it, buf, vals, stage, xsmem, &full[st]);
+            if (lane == 0 && it.flag) {
+                pend_on[st] = true;
+                pend_par[st] = arrivals[st] & 1u;
+                pend_ticket[st] = it.ticket;
+            }
             ++arrivals[st];
             ++issued[st];
             if (it.single) ++issued[st ^ 1u];  // the consumers release both stages
             // a stash holder waits on later tickets of its own exchange: claim no ticket
             // that could be parked behind it
             if (it.holder && !drain(st)) {
-                if (lane == 0) {
-                    set_status(sb, IPM_ERR_TIMEOUT);
-                    sh.abort = 1;
-                }
+                fail_timeout();
                 break;
             }
             st ^= 1u;
+            ok_claim = claim(it, t);
         }
         // leave only once every bulk copy this warp issued has landed (no copy may
         // write the CTA's shared memory after it exits)
