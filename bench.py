@@ -58,6 +58,9 @@ WORKLOADS = {
                             "int32 L_A=2^29, L_B=2^20, uniform"),
     "c2-uint64-uniform": ("uniform", "uint64", 1 << 28, 1 << 28,
                           "uint64 L_A=L_B=2^28, uniform [0,2^64)"),
+    "c3-uint32-kv-zipf": ("zipf", "uint32", 1 << 26, 1 << 26,
+                          "key-value: uint32 keys Zipf(1.2) over 2^20 ranks, uint32 payload = "
+                          "original buffer index, L_A=L_B=2^26; ipm_merge_inplace_kv"),
     "c1-int32-uniform": ("uniform", "int32", 1 << 20, 1 << 20,
                          "int32 L_A=L_B=2^20, uniform (L2-resident, 8 MiB)"),
     "c2s-int32-uniform": ("uniform", "int32", 1 << 25, 1 << 25,
@@ -72,6 +75,7 @@ WORKLOADS = {
                            "(300 Adam steps); ipm_merge_inplace_learned"),
 }
 FORM = {"c4-int32-batched": "batched", "c5-float32-learned": "learned"}
+KV_WORKLOADS = {"c3-uint32-kv-zipf"}  # plain form with a uint32 payload per key
 NP_DT = {"int32": np.int32, "uint32": np.uint32, "uint64": np.uint64, "float32": np.float32}
 
 
@@ -212,17 +216,27 @@ def cpu_oracle_timing(wl, budget_s: float = 10.0, steps: int | None = None,
         return keys * len(times) / tot / 1e9, sample, len(times), tot
 
     dist, dt, la, lb, _ = wl
+    kv = wl is WORKLOADS["c3-uint32-kv-zipf"]
     scale = max(1, (la + lb) // (1 << 25))
     sa, sb = max(1, la // scale), max(1, lb // scale)
     a, b = workloads.make_pair(dist, NP_DT[dt], sa, sb, seed=0)
+    va = np.arange(sa, dtype=np.uint32)
+    vb = np.arange(sa, sa + sb, dtype=np.uint32)
+
+    def merge_once():
+        if kv:
+            oracle.merge_kv(a, va, b, vb)
+        else:
+            oracle.merge(a, b)
+
     oracle.merge(a[:1024], b[:1024])
     for _ in range(warmup):
-        oracle.merge(a, b)
+        merge_once()
     times = []
     t_end = time.perf_counter() + budget_s
     while True:
         t0 = time.perf_counter()
-        oracle.merge(a, b)
+        merge_once()
         times.append(time.perf_counter() - t0)
         if steps is not None:
             if len(times) >= steps:
@@ -230,8 +244,9 @@ def cpu_oracle_timing(wl, budget_s: float = 10.0, steps: int | None = None,
         elif time.perf_counter() > t_end:
             break
     tot = sum(times)
-    sample = (f"oracle two-pointer merge on L_A={sa}, L_B={sb} keys of the same generator "
-              f"(1/{scale} of the workload), {len(times)} reps, 1 thread")
+    sample = (f"oracle two-pointer merge{' (key-value)' if kv else ''} on L_A={sa}, "
+              f"L_B={sb} keys of the same generator (1/{scale} of the workload), "
+              f"{len(times)} reps, 1 thread")
     return (sa + sb) * len(times) / tot / 1e9, sample, len(times), tot
 
 
@@ -658,32 +673,47 @@ def run_e2e_batched(torch, ipm, workloads, m, steps, stream, dev):
     segs = ipm.segment_table(offs, la, lb, dev)
     n = pristine.numel()
     ws = ipm.workspace(ipm.ipm_merge_batched_workspace_bytes(n, la.size, "int32"), dev)
-    return run_e2e(torch, pristine, steps, stream,
-                   lambda d: ipm.ipm_merge_batched(d, None, n, segs, la.size, "int32", ws))
+    return run_e2e(torch, [pristine], steps, stream,
+                   lambda d: ipm.ipm_merge_batched(d[0], None, n, segs, la.size, "int32", ws))
 
 
 def run_e2e_learned(torch, ipm, m, steps, stream, model):
     pristine = m["pristine"]
     la = lb = pristine.numel() // 2
     ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, "float32"), pristine.device)
-    return run_e2e(torch, pristine, steps, stream,
-                   lambda d: ipm.ipm_merge_inplace_learned(d, la, lb, "float32", model, ws))
+    return run_e2e(torch, [pristine], steps, stream,
+                   lambda d: ipm.ipm_merge_inplace_learned(d[0], la, lb, "float32", model, ws))
 
 
 def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
     dist, dt, la, lb, desc = WORKLOADS[args.workload]
-    n, w = la + lb, np.dtype(NP_DT[dt]).itemsize
+    kv = args.workload in KV_WORKLOADS
+    n, w = la + lb, np.dtype(NP_DT[dt]).itemsize + (4 if kv else 0)
 
     pristine = workloads.make_buffer_torch(torch, dist, NP_DT[dt], la, lb, 0, dev)
     buf = torch.empty_like(pristine)
-    G, tile = ipm.ipm_merge_plan(la, lb, dt)
-    ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, dt), dev)
+    # key-value: payload = the key's original buffer index
+    vpristine = torch.arange(n, dtype=torch.int64, device=dev).to(torch.int32) if kv else None
+    vbuf = torch.empty_like(vpristine) if kv else None
+    G, tile = ipm.ipm_merge_plan(la, lb, dt, with_values=kv)
+    ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, dt, with_values=kv), dev)
 
     mb = method_bytes(n, w)
 
-    def step():
+    def merge(kb, vb=None):
+        if kv:
+            ipm.ipm_merge_inplace_kv(kb, vb, la, lb, dt, ws)
+        else:
+            ipm.ipm_merge_inplace(kb, la, lb, dt, ws)
+
+    def restore():
         buf.copy_(pristine)
-        ipm.ipm_merge_inplace(buf, la, lb, dt, ws)
+        if kv:
+            vbuf.copy_(vpristine)
+
+    def step():
+        restore()
+        merge(buf, vbuf)
 
     for _ in range(args.warmup):
         step()
@@ -704,9 +734,9 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
            for _ in range(args.steps)]
     wall0 = time.perf_counter()
     for s, e in evs:
-        buf.copy_(pristine)
+        restore()
         s.record(stream)
-        ipm.ipm_merge_inplace(buf, la, lb, dt, ws)
+        merge(buf, vbuf)
         e.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
@@ -725,8 +755,16 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
     if ipm.ipm_read_device_status(ws) != 0:
         raise RuntimeError("device status not OK after the timed steps")
 
-    # sanity: the last step's output is sorted (cheap device check; parity is in tests)
-    ok_sorted = bool((buf[1:] >= buf[:-1]).all().item()) if dt == "int32" else None
+    # sanity: the last step's output is sorted (cheap device check; parity is in tests);
+    # key-value: equal keys keep their payloads (original indices) ascending
+    ok_sorted = None
+    if dt == "int32" and not kv:
+        ok_sorted = bool((buf[1:] >= buf[:-1]).all().item())
+    elif kv and dt == "uint32":
+        k64 = buf.to(torch.int64) & 0xFFFFFFFF
+        ok_sorted = bool(((k64[1:] > k64[:-1]) |
+                          ((k64[1:] == k64[:-1]) & (vbuf[1:] > vbuf[:-1]))).all().item())
+        del k64
 
     peak, peak_kind = peaks()
     exch = phases["exchange"]
@@ -743,9 +781,9 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(torch, pristine, args.steps, stream,
-                      lambda d: ipm.ipm_merge_inplace(d, la, lb, dt, ws))
-    del buf, pristine
+        e2e = run_e2e(torch, [pristine, vpristine] if kv else [pristine], args.steps, stream,
+                      lambda d: merge(*d))
+    del buf, pristine, vbuf, vpristine
 
     if rank != 0:
         return None
@@ -757,9 +795,11 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dt,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": f"{dt} key + uint32 payload" if kv else dt,
         "data": "synthetic",
-        "config": {"workload": args.workload, "description": desc, "form": "plain",
+        "config": {"workload": args.workload, "description": desc,
+                   "form": "key-value" if kv else "plain",
                    "log2_pairs": G, "tile_capacity": tile,
                    "l2": "inputs larger than L2 (%.1f GiB buffer)" % (n * w / 2**30)
                    if n * w > (129 << 20) else "L2-resident input (no flush)",
@@ -785,24 +825,27 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
     }
 
 
-def run_e2e(torch, pristine, steps, stream, merge):
-    """The merge through the public API with host buffers: H2D of the input from pinned
-    memory, merge(device buffer), D2H of the result into pinned memory, all timed."""
-    host_in = pristine.cpu().pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    dbuf = torch.empty_like(pristine)
+def run_e2e(torch, pristines, steps, stream, merge):
+    """The merge through the public API with host buffers: H2D of the inputs (keys, and
+    payloads for key-value) from pinned memory, merge(device buffers), D2H of the
+    results into pinned memory, all timed."""
+    host_in = [p.cpu().pin_memory() for p in pristines]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    dbuf = [torch.empty_like(p) for p in pristines]
 
     def call():
-        dbuf.copy_(host_in, non_blocking=True)
+        for d, h in zip(dbuf, host_in):
+            d.copy_(h, non_blocking=True)
         merge(dbuf)
-        host_out.copy_(dbuf, non_blocking=True)
+        for h, d in zip(host_out, dbuf):
+            h.copy_(d, non_blocking=True)
 
     for _ in range(2):
         call()
     torch.cuda.synchronize()
     ms = sum(timed_steps(torch, stream, steps, lambda: None, call)) / steps
-    nbytes = pristine.numel() * pristine.element_size()
-    return {"value": pristine.numel() / (ms * 1e-3) / 1e9, "unit": UNIT,
+    nbytes = sum(p.numel() * p.element_size() for p in pristines)
+    return {"value": pristines[0].numel() / (ms * 1e-3) / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": ms}
 
 

@@ -16,7 +16,10 @@
 // "my reads are done" in a flag, and waits only on items with smaller tickets (a
 // holder, which writes its stash last, also waits on the later tiles of its own
 // exchange; at most max_holders such CTAs exist per exchange, fewer than the
-// resident CTAs, so the tiles always find a CTA).  Consecutive phases of one exchange
+// resident CTAs, so the tiles always find a CTA).  The upper levels have few
+// exchanges, so they get more holders (level_holders): a bigger on-chip stash turns an
+// exchange of a large and a mid-sized block into one SHIFT pass instead of a long
+// chain of LS steps.  Consecutive phases of one exchange
 // (LS steps) are ordered by a per-exchange completion counter.  Every wait is bounded
 // in time; on expiry the kernel records IPM_ERR_TIMEOUT and all CTAs leave.
 #include "ipm_exchange.cuh"
@@ -28,6 +31,15 @@ namespace ipm {
 namespace {
 
 constexpr uint32_t kPlanThreads = 1024;
+
+// Stash holders per exchange at level l: about half the resident CTAs shared by the
+// level's 2^l exchanges (hcap = half the resident CTAs, from the host), at least the
+// base 8 and at most 64.  The plan and the level kernels use the same value.
+constexpr uint32_t kMinHolders = 8, kMaxHoldersCap = 64;
+__host__ __device__ inline uint32_t level_holders(uint32_t l, uint32_t hcap) {
+    const uint32_t h = l < 31 ? hcap >> l : 0u;
+    return h < kMinHolders ? kMinHolders : (h > kMaxHoldersCap ? kMaxHoldersCap : h);
+}
 
 struct RotPlan {
     uint64_t s, a, b;
@@ -78,9 +90,11 @@ __device__ __forceinline__ RotPlan level_rotation(const uint64_t *split, uint64_
 // the status block) their algorithmic bytes.
 __global__ void __launch_bounds__(kPlanThreads)
     xplan_levels_kernel(const uint64_t *__restrict__ split, uint64_t n, uint32_t G,
-                        XPlanArea pa, XParams prm, uint32_t elem, StatusBlock *sb) {
+                        XPlanArea pa, XParams prm, uint32_t hcap, uint32_t elem,
+                        StatusBlock *sb) {
     if (sb != nullptr && *((volatile const unsigned int *)&sb->done)) return;
     const uint32_t l = blockIdx.x;
+    prm.max_holders = level_holders(l, hcap);
     const uint64_t R = 1ull << l;
     RotPlan *plans = reinterpret_cast<RotPlan *>(pa.plans) + (R - 1);
     uint32_t *pf = pa.item_pf + (R - 1) + l;
@@ -110,7 +124,9 @@ __global__ void __launch_bounds__(kPlanThreads)
     if (sb != nullptr && bytes) atomicAdd(&sb->exchange_bytes, bytes);
 }
 
-__global__ void xplan_single_kernel(uint64_t lx, uint64_t ly, XPlanArea pa, XParams prm) {
+__global__ void xplan_single_kernel(uint64_t lx, uint64_t ly, XPlanArea pa, XParams prm,
+                                    uint32_t hcap) {
+    prm.max_holders = level_holders(0, hcap);
     if (threadIdx.x == 0) {
         RotPlan q{0, lx, ly};
         uint64_t it = 0, by = 0;
@@ -182,14 +198,13 @@ struct XCfg {
     static constexpr size_t kStageVBytes = KV ? (size_t(2) * kSlotV * 4 + 15) / 16 * 16 : 0;
     static constexpr size_t kStageSize = kStageKBytes + kStageVBytes;
     static constexpr size_t kSmem = 2 * kStageSize + 64;  // two stages + two mbarriers
-    static constexpr uint32_t kMaxHolders = 8;
     // pair tile = one slot per block; shift tile, stash chunk and SINGLE exchange = two
     // slots (they start at slot 0 with their own phase offset < kKPad)
     // a SINGLE exchange is staged across both stages (keys, then values)
     static constexpr uint32_t kSingleCap =
         uint32_t((2 * kStageSize - 64) / kElemBytes) / 32u * 32u;
     __host__ __device__ static XParams params() {
-        return XParams{kSlot, 2 * kSlot, 2 * kSlot, kMaxHolders, kSingleCap};
+        return XParams{kSlot, 2 * kSlot, 2 * kSlot, 8u, kSingleCap};  // holders: per level
     }
 };
 
@@ -562,13 +577,14 @@ __global__ void __launch_bounds__(512, 1)
                           const RotPlan *__restrict__ plans, const uint32_t *__restrict__ pf,
                           uint32_t nrot, uint32_t *__restrict__ flags,
                           uint32_t *__restrict__ join, uint32_t tag, uint32_t ctr_index,
-                          StatusBlock *sb) {
+                          uint32_t holders, StatusBlock *sb) {
     using C = XCfg<K, KV>;
     extern __shared__ __align__(128) unsigned char xsmem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(xsmem + 2 * C::kStageSize);
     __shared__ Shared sh;
     if (sb != nullptr && *((volatile unsigned int *)&sb->done)) return;
-    const XParams prm = C::params();
+    XParams prm = C::params();
+    prm.max_holders = holders;
     const uint32_t tid = threadIdx.x;
     const uint32_t total = pf[nrot];
     uint32_t *ctr = &sb->counters[ctr_index];
@@ -921,7 +937,7 @@ __global__ void __launch_bounds__(512, 1)
                              const RotPlan *__restrict__ plans, const uint32_t *__restrict__ pf,
                              uint32_t nrot, uint32_t *__restrict__ flags,
                              uint32_t *__restrict__ join, uint32_t tag, uint32_t ctr_index,
-                             StatusBlock *sb) {
+                             uint32_t holders, StatusBlock *sb) {
     using C = XCfg<K, KV>;
     extern __shared__ __align__(128) unsigned char xsmem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(xsmem + 2 * C::kStageSize);
@@ -943,7 +959,8 @@ __global__ void __launch_bounds__(512, 1)
 
     if (tid < 32) {
         // ------------------------------------------------------------- producer warp
-        const XParams prm = C::params();
+        XParams prm = C::params();
+        prm.max_holders = holders;
         const uint32_t lane = tid;
         uint32_t *ctr = &sb->counters[ctr_index];
         uint32_t issued[2] = {0, 0}, drained[2] = {0, 0};
@@ -1135,6 +1152,10 @@ __global__ void __launch_bounds__(512, 1)
     }
 }
 
+// Half the resident CTAs of the level kernels (one per SM at least), the base of the
+// per-level holder count; the same on the plan side.
+uint32_t holder_cap() { return uint32_t(num_sms()) / 2u; }
+
 template <typename E, bool KV, bool WS>
 ipm_status exchange_level_t(void *buf, uint32_t *vals, uint64_t n, uint32_t l,
                             XPlanArea pa, StatusBlock *sb, cudaStream_t stream) {
@@ -1161,7 +1182,8 @@ ipm_status exchange_level_t(void *buf, uint32_t *vals, uint64_t n, uint32_t l,
     const uint32_t *pf = pa.item_pf + (R - 1) + l;
     kern<<<grid, C::kThreads, C::kSmem, stream>>>((E *)buf, vals, n, plans, pf, uint32_t(R),
                                                   pa.flags, pa.join + (R - 1), l + 1,
-                                                  kTicketCounter0 + l, sb);
+                                                  kTicketCounter0 + l,
+                                                  level_holders(l, holder_cap()), sb);
     return last_launch_status();
 }
 
@@ -1193,10 +1215,12 @@ size_t xplan_area_bytes(uint32_t G, uint64_t n, ipm_dtype key, bool with_values)
 
 uint64_t max_level_items(uint32_t G, uint64_t n, const XParams &prm) {
     // per exchange: tiles of its LS steps and of its final phase (<= 2 m / pair_tile + 2
-    // per phase), at most n / (cap * max_holders) LS steps in all, max_holders + 1 more
+    // per phase), at most n / (cap * kMinHolders) LS steps in all, and its holders: a
+    // level's R exchanges hold at most max(kMinHolders R, kMaxHoldersCap) of them
+    (void)prm.max_holders;
     const uint64_t R = 1ull << (G ? G - 1 : 0);
-    return 2 * n / prm.pair_tile + n / (uint64_t(prm.cap) * prm.max_holders) +
-           R * (prm.max_holders + 6) + 16;
+    return 2 * n / prm.pair_tile + n / (uint64_t(prm.cap) * kMinHolders) +
+           R * (kMinHolders + 6) + kMaxHoldersCap + 16;
 }
 
 XPlanArea xplan_area_at(void *base, uint32_t G, uint64_t n, ipm_dtype key, bool with_values) {
@@ -1228,14 +1252,15 @@ ipm_status launch_xplan_levels(const uint64_t *split, uint64_t n, uint32_t G,
     const uint32_t elem = uint32_t(dtype_bytes(key)) + (with_values ? 4u : 0u);
     xplan_levels_kernel<<<levels, kPlanThreads, 0, stream>>>(split, n, G, pa,
                                                              exchange_params(key, with_values),
-                                                             elem, sb);
+                                                             holder_cap(), elem, sb);
     return last_launch_status();
 }
 
 ipm_status launch_xplan_single(uint64_t lx, uint64_t ly, XPlanArea pa, ipm_dtype key,
                                cudaStream_t stream) {
     IPM_CUDA_TRY(cudaMemsetAsync(pa.join, 0, pa.zero_bytes, stream));
-    xplan_single_kernel<<<1, 32, 0, stream>>>(lx, ly, pa, exchange_params(key, false));
+    xplan_single_kernel<<<1, 32, 0, stream>>>(lx, ly, pa, exchange_params(key, false),
+                                               holder_cap());
     return last_launch_status();
 }
 
