@@ -58,6 +58,8 @@ WORKLOADS = {
                             "int32 L_A=2^29, L_B=2^20, uniform"),
     "c2-uint64-uniform": ("uniform", "uint64", 1 << 28, 1 << 28,
                           "uint64 L_A=L_B=2^28, uniform [0,2^64)"),
+    "c2-int64-uniform": ("uniform", "int64", 1 << 28, 1 << 28,
+                         "int64 L_A=L_B=2^28, uniform over the full signed range"),
     "c3-uint32-kv-zipf": ("zipf", "uint32", 1 << 26, 1 << 26,
                           "key-value: uint32 keys Zipf(1.2) over 2^20 ranks, uint32 payload = "
                           "original buffer index, L_A=L_B=2^26; ipm_merge_inplace_kv"),
@@ -76,7 +78,8 @@ WORKLOADS = {
 }
 FORM = {"c4-int32-batched": "batched", "c5-float32-learned": "learned"}
 KV_WORKLOADS = {"c3-uint32-kv-zipf"}  # plain form with a uint32 payload per key
-NP_DT = {"int32": np.int32, "uint32": np.uint32, "uint64": np.uint64, "float32": np.float32}
+NP_DT = {"int32": np.int32, "uint32": np.uint32, "uint64": np.uint64, "float32": np.float32,
+         "int64": np.int64}
 
 
 def parse():
@@ -758,7 +761,7 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
     # sanity: the last step's output is sorted (cheap device check; parity is in tests);
     # key-value: equal keys keep their payloads (original indices) ascending
     ok_sorted = None
-    if dt == "int32" and not kv:
+    if dt in ("int32", "int64") and not kv:
         ok_sorted = bool((buf[1:] >= buf[:-1]).all().item())
     elif kv and dt == "uint32":
         k64 = buf.to(torch.int64) & 0xFFFFFFFF

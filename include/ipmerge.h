@@ -17,8 +17,9 @@
  *     library never allocates or frees device memory; every call that needs scratch
  *     takes a caller-owned workspace sized by the matching *_workspace_bytes query.
  *   - Lengths and offsets count elements, not bytes.
- *   - Keys are compared with the key type's own "<=": signed for IPM_INT32, unsigned
- *     for IPM_UINT32 / IPM_UINT64, IEEE for IPM_FLOAT32 (NaN keys are not allowed;
+ *   - Keys are compared with the key type's own "<=": signed for IPM_INT32 /
+ *     IPM_INT64, unsigned for IPM_UINT32 / IPM_UINT64, IEEE for IPM_FLOAT32 (NaN keys
+ *     are not allowed;
  *     -0.0 and +0.0 compare equal and keep their input order).
  *   - The merge is stable: equal keys keep their input order, every A element before
  *     every equal B element.  Keys (and payloads) are only moved, never computed, so
@@ -59,7 +60,8 @@ typedef enum {
     IPM_INT32 = 0,
     IPM_UINT32 = 1,
     IPM_UINT64 = 2,
-    IPM_FLOAT32 = 3
+    IPM_FLOAT32 = 3,
+    IPM_INT64 = 4
 } ipm_dtype;
 
 /* Human-readable name of a status code (static string). */

@@ -26,7 +26,8 @@ _lock = threading.Lock()
 _lib = None
 
 SUFFIX = {np.dtype(np.int32): "i32", np.dtype(np.uint32): "u32",
-          np.dtype(np.uint64): "u64", np.dtype(np.float32): "f32"}
+          np.dtype(np.uint64): "u64", np.dtype(np.float32): "f32",
+          np.dtype(np.int64): "i64"}
 
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 

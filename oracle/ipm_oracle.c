@@ -45,6 +45,12 @@
 #undef T
 #undef SUF
 
+#define T int64_t
+#define SUF i64
+#include "oracle_typed.h"
+#undef T
+#undef SUF
+
 /* ------------------------------------------------------------------------------ */
 /* Learned split proposer: y(x) = b2 + sum_h w2[h] * tanh(w1[h] * x + b1[h]).       */
 /* Parameter layout (3H+1 doubles): w1[0..H), b1[0..H), w2[0..H), b2.               */

@@ -39,8 +39,8 @@ __all__ = [
     "ipm_set_exchange_engine", "ipm_set_fused_engine",
 ]
 
-DTYPES = {"int32": 0, "uint32": 1, "uint64": 2, "float32": 3}
-_ELEM = {0: 4, 1: 4, 2: 8, 3: 4}
+DTYPES = {"int32": 0, "uint32": 1, "uint64": 2, "float32": 3, "int64": 4}
+_ELEM = {0: 4, 1: 4, 2: 8, 3: 4, 4: 8}
 STATUS = {0: "IPM_OK", 1: "IPM_ERR_INVALID_ARG", 2: "IPM_ERR_UNSUPPORTED_DTYPE",
           3: "IPM_ERR_ALIGNMENT", 4: "IPM_ERR_WORKSPACE", 5: "IPM_ERR_CUDA",
           6: "IPM_ERR_TIMEOUT", 7: "IPM_ERR_DEVICE"}
@@ -151,7 +151,7 @@ def _dt(dtype) -> int:
     if name in DTYPES:
         return DTYPES[name]
     raise ValueError(f"cannot map {dtype!r} to an ipm_dtype; pass 'int32', 'uint32', "
-                     "'uint64' or 'float32'")
+                     "'uint64', 'float32' or 'int64'")
 
 
 def _ptr(x) -> int | None:

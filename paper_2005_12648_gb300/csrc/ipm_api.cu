@@ -92,7 +92,8 @@ uint32_t g_fused_levels = 8;
 uint32_t g_fused_engine = 1;
 
 bool valid_key(ipm_dtype t) {
-    return t == IPM_INT32 || t == IPM_UINT32 || t == IPM_UINT64 || t == IPM_FLOAT32;
+    return t == IPM_INT32 || t == IPM_UINT32 || t == IPM_UINT64 || t == IPM_FLOAT32 ||
+           t == IPM_INT64;
 }
 
 // Smallest G with 2^G * tile >= n.

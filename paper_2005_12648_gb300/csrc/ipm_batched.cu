@@ -12,6 +12,8 @@ ipm_status batched_launch_u64(void *, uint32_t *, uint64_t, batched::QueueArea, 
                               uint32_t, uint32_t, StatusBlock *, cudaStream_t);
 ipm_status batched_launch_f32(void *, uint32_t *, uint64_t, batched::QueueArea, uint32_t,
                               uint32_t, uint32_t, StatusBlock *, cudaStream_t);
+ipm_status batched_launch_i64(void *, uint32_t *, uint64_t, batched::QueueArea, uint32_t,
+                              uint32_t, uint32_t, StatusBlock *, cudaStream_t);
 
 namespace {
 
@@ -187,6 +189,7 @@ uint64_t batched_tile(ipm_dtype key, bool with_values, uint32_t variant) {
     case IPM_FLOAT32:
         return with_values ? tile_t<int32_t, true>(variant) : tile_t<int32_t, false>(variant);
     case IPM_UINT64:
+    case IPM_INT64:
         return with_values ? tile_t<uint64_t, true>(variant)
                            : tile_t<uint64_t, false>(variant);
     }
@@ -240,6 +243,9 @@ ipm_status launch_batched(void *buf, uint32_t *vals, uint64_t buf_len, ipm_dtype
                                   stream);
     case IPM_FLOAT32:
         return batched_launch_f32(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm, sb,
+                                  stream);
+    case IPM_INT64:
+        return batched_launch_i64(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm, sb,
                                   stream);
     }
     return IPM_ERR_UNSUPPORTED_DTYPE;

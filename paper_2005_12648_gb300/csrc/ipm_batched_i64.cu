@@ -1,0 +1,14 @@
+// Batched segmented merge kernels for int64_t keys (one translation unit per key type so
+// the variants compile in parallel).
+#include "ipm_batched.cuh"
+
+namespace ipm {
+
+ipm_status batched_launch_i64(void *buf, uint32_t *vals, uint64_t buf_len,
+                               batched::QueueArea qa, uint32_t nseg, uint32_t variant,
+                               uint32_t ctas_per_sm, StatusBlock *sb, cudaStream_t stream) {
+    return batched::batched_dispatch<int64_t>(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm,
+                                          sb, stream);
+}
+
+}  // namespace ipm

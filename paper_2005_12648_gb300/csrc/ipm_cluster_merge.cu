@@ -527,6 +527,7 @@ int capacity_by_key(ipm_dtype key, bool kv) {
     case IPM_UINT32:
         return capacity_kv<uint32_t, C>(kv);
     case IPM_UINT64:
+    case IPM_INT64:
         return capacity_kv<uint64_t, C>(kv);
     case IPM_FLOAT32:
         return capacity_kv<float, C>(kv);
@@ -545,6 +546,8 @@ ipm_status cluster_by_key(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, i
         return cluster_dispatch<uint32_t, C>(buf, vals, la, lb, split, G, sb, stream);
     case IPM_UINT64:
         return cluster_dispatch<uint64_t, C>(buf, vals, la, lb, split, G, sb, stream);
+    case IPM_INT64:
+        return cluster_dispatch<int64_t, C>(buf, vals, la, lb, split, G, sb, stream);
     case IPM_FLOAT32:
         return cluster_dispatch<float, C>(buf, vals, la, lb, split, G, sb, stream);
     }
@@ -576,6 +579,7 @@ uint32_t usable_group_levels(ipm_dtype key, bool with_values, uint32_t wanted) {
     case IPM_INT32: grid = group_grid_kv<int32_t>(with_values); break;
     case IPM_UINT32: grid = group_grid_kv<uint32_t>(with_values); break;
     case IPM_UINT64: grid = group_grid_kv<uint64_t>(with_values); break;
+    case IPM_INT64: grid = group_grid_kv<int64_t>(with_values); break;
     case IPM_FLOAT32: grid = group_grid_kv<float>(with_values); break;
     }
     uint32_t f = wanted;
@@ -594,6 +598,8 @@ ipm_status launch_group_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t l
         return group_dispatch<uint32_t>(buf, vals, la, lb, split, G, F, gctr, sb, stream);
     case IPM_UINT64:
         return group_dispatch<uint64_t>(buf, vals, la, lb, split, G, F, gctr, sb, stream);
+    case IPM_INT64:
+        return group_dispatch<int64_t>(buf, vals, la, lb, split, G, F, gctr, sb, stream);
     case IPM_FLOAT32:
         return group_dispatch<float>(buf, vals, la, lb, split, G, F, gctr, sb, stream);
     }

@@ -63,6 +63,7 @@ inline int dtype_bytes(ipm_dtype t) {
     case IPM_FLOAT32:
         return 4;
     case IPM_UINT64:
+    case IPM_INT64:
         return 8;
     }
     return 0;

@@ -130,6 +130,7 @@ ipm_status launch_division(const void *buf, uint64_t la, uint64_t lb, ipm_dtype 
     case IPM_INT32: return division_t<int32_t>(buf, la, lb, depth, kind, ia, jb, stream);
     case IPM_UINT32: return division_t<uint32_t>(buf, la, lb, depth, kind, ia, jb, stream);
     case IPM_UINT64: return division_t<uint64_t>(buf, la, lb, depth, kind, ia, jb, stream);
+    case IPM_INT64: return division_t<int64_t>(buf, la, lb, depth, kind, ia, jb, stream);
     case IPM_FLOAT32: return division_t<float>(buf, la, lb, depth, kind, ia, jb, stream);
     default: return IPM_ERR_UNSUPPORTED_DTYPE;
     }

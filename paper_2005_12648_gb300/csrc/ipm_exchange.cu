@@ -1196,6 +1196,7 @@ XParams exchange_params(ipm_dtype key, bool with_values) {
     case IPM_FLOAT32:
         return with_values ? XCfg<int32_t, true>::params() : XCfg<int32_t, false>::params();
     case IPM_UINT64:
+    case IPM_INT64:  // moved, never compared
         return with_values ? XCfg<uint64_t, true>::params() : XCfg<uint64_t, false>::params();
     }
     return XParams{1, 2, 1, 1, 1};
@@ -1281,6 +1282,7 @@ ipm_status launch_exchange_level(void *buf, uint32_t *vals, ipm_dtype key, uint6
         return kv ? exchange_level_t<int32_t, true, false>(buf, vals, n, l, pa, sb, stream)
                   : exchange_level_t<int32_t, false, false>(buf, vals, n, l, pa, sb, stream);
     case IPM_UINT64:
+    case IPM_INT64:  // moved, never compared
         if (ws)
             return kv ? exchange_level_t<uint64_t, true, true>(buf, vals, n, l, pa, sb, stream)
                       : exchange_level_t<uint64_t, false, true>(buf, vals, n, l, pa, sb, stream);

@@ -292,6 +292,8 @@ ipm_status launch_learned_splits(const void *buf, uint64_t la, uint64_t lb, ipm_
         return learned_splits_t<uint32_t>(buf, la, lb, P, model, split, stats, sb, stream);
     case IPM_UINT64:
         return learned_splits_t<uint64_t>(buf, la, lb, P, model, split, stats, sb, stream);
+    case IPM_INT64:
+        return learned_splits_t<int64_t>(buf, la, lb, P, model, split, stats, sb, stream);
     case IPM_FLOAT32:
         return learned_splits_t<float>(buf, la, lb, P, model, split, stats, sb, stream);
     }
@@ -323,6 +325,9 @@ ipm_status launch_split_model_train(const void *buf, uint64_t la, uint64_t lb, i
         break;
     case IPM_UINT64:
         IPM_TRY(targets_t<uint64_t>(buf, la, lb, diags, n, x, t, sb, stream));
+        break;
+    case IPM_INT64:
+        IPM_TRY(targets_t<int64_t>(buf, la, lb, diags, n, x, t, sb, stream));
         break;
     case IPM_FLOAT32:
         IPM_TRY(targets_t<float>(buf, la, lb, diags, n, x, t, sb, stream));

@@ -61,6 +61,9 @@ ipm_status launch_early_exit(const void *buf, uint64_t la, uint64_t lb, ipm_dtyp
     case IPM_UINT64:
         early_exit_kernel<uint64_t><<<1, 32, 0, stream>>>((const uint64_t *)buf, la, lb, sb);
         break;
+    case IPM_INT64:
+        early_exit_kernel<int64_t><<<1, 32, 0, stream>>>((const int64_t *)buf, la, lb, sb);
+        break;
     case IPM_FLOAT32:
         early_exit_kernel<float><<<1, 32, 0, stream>>>((const float *)buf, la, lb, sb);
         break;
@@ -80,6 +83,8 @@ ipm_status launch_splits(const void *buf, uint64_t la, uint64_t lb, ipm_dtype ke
         return splits_t<uint32_t>(buf, la, lb, P, split, sb, stream);
     case IPM_UINT64:
         return splits_t<uint64_t>(buf, la, lb, P, split, sb, stream);
+    case IPM_INT64:
+        return splits_t<int64_t>(buf, la, lb, P, split, sb, stream);
     case IPM_FLOAT32:
         return splits_t<float>(buf, la, lb, P, split, sb, stream);
     }

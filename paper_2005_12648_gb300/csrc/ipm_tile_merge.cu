@@ -94,6 +94,10 @@ template <>
 struct TileOf<float, true> { static constexpr int T = 512, E = 33; };
 template <>
 struct TileOf<uint64_t, true> { static constexpr int T = 512, E = 33; };
+template <>
+struct TileOf<int64_t, false> { static constexpr int T = 512, E = 33; };
+template <>
+struct TileOf<int64_t, true> { static constexpr int T = 512, E = 33; };
 
 template <typename K>
 ipm_status tile_merge_dispatch(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
@@ -116,6 +120,7 @@ uint64_t tile_capacity(ipm_dtype key, bool with_values) {
         return with_values ? uint64_t(TileOf<int32_t, true>::T) * TileOf<int32_t, true>::E
                            : uint64_t(TileOf<int32_t, false>::T) * TileOf<int32_t, false>::E;
     case IPM_UINT64:
+    case IPM_INT64:
         return with_values ? uint64_t(TileOf<uint64_t, true>::T) * TileOf<uint64_t, true>::E
                            : uint64_t(TileOf<uint64_t, false>::T) * TileOf<uint64_t, false>::E;
     }
@@ -132,6 +137,8 @@ ipm_status launch_tile_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t lb
         return tile_merge_dispatch<uint32_t>(buf, vals, la, lb, split, G, sb, stream);
     case IPM_UINT64:
         return tile_merge_dispatch<uint64_t>(buf, vals, la, lb, split, G, sb, stream);
+    case IPM_INT64:
+        return tile_merge_dispatch<int64_t>(buf, vals, la, lb, split, G, sb, stream);
     case IPM_FLOAT32:
         return tile_merge_dispatch<float>(buf, vals, la, lb, split, G, sb, stream);
     }

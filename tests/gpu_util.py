@@ -2,9 +2,11 @@
 import numpy as np
 
 STORAGE = {np.dtype(np.int32): np.int32, np.dtype(np.uint32): np.int32,
-           np.dtype(np.uint64): np.int64, np.dtype(np.float32): np.float32}
+           np.dtype(np.uint64): np.int64, np.dtype(np.float32): np.float32,
+           np.dtype(np.int64): np.int64}
 NAME = {np.dtype(np.int32): "int32", np.dtype(np.uint32): "uint32",
-        np.dtype(np.uint64): "uint64", np.dtype(np.float32): "float32"}
+        np.dtype(np.uint64): "uint64", np.dtype(np.float32): "float32",
+        np.dtype(np.int64): "int64"}
 
 
 def to_dev(x: np.ndarray, dev):

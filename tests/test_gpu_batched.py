@@ -8,7 +8,7 @@ from gpu_util import NAME, first_diff, from_dev, to_dev
 
 pytestmark = pytest.mark.gpu
 
-DTYPES = [np.int32, np.uint32, np.uint64, np.float32]
+DTYPES = [np.int32, np.uint32, np.uint64, np.float32, np.int64]
 OPTIONS = [None, {"tile": 1}, {"tile": 3}, {"order": 1},
            {"tile": 2, "ctas_per_sm": 1, "order": 1}]
 
@@ -85,7 +85,7 @@ def test_batched_keys_match_oracle(ipm, dev, orc, dt, opt):
     assert first_diff(got, want) is None, first_diff(got, want)
 
 
-@pytest.mark.parametrize("dt", [np.uint32, np.uint64, np.float32])
+@pytest.mark.parametrize("dt", [np.uint32, np.uint64, np.float32, np.int64])
 @pytest.mark.parametrize("opt", [0, 1, 2])
 def test_batched_kv_stable(ipm, dev, orc, dt, opt):
     tile = ipm.ipm_merge_plan(1, 1, NAME[np.dtype(dt)], True)[1]

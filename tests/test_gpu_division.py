@@ -20,7 +20,7 @@ def _gpu_division(ipm, buf, la, lb, dt, depth, split):
 
 
 @pytest.mark.parametrize("split", ["exact", "findmedian"])
-@pytest.mark.parametrize("dt", [np.int32, np.uint32, np.uint64, np.float32])
+@pytest.mark.parametrize("dt", [np.int32, np.uint32, np.uint64, np.float32, np.int64])
 def test_division_matches_oracle(ipm, dev, orc, split, dt):
     sizes = [(0, 0), (0, 17), (17, 0), (1, 1), (1, 1000), (1000, 1), (5000, 5000),
              (12_345, 67_890), (65_536, 16_384), (100_003, 99_991)]

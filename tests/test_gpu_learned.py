@@ -175,7 +175,8 @@ def test_learned_splits_with_a_useless_model(ipm, dev, orc):
 
 @pytest.mark.parametrize("dist,dt", [("gmm", np.float32), ("uniform", np.int32),
                                      ("dup16", np.uint32), ("alternation", np.uint64),
-                                     ("revdisjoint", np.int32)])
+                                     ("revdisjoint", np.int32), ("disjoint", np.int64),
+                                     ("uniform", np.int64)])
 @pytest.mark.parametrize("la,lb", [(1, 1), (5000, 0), (300_007, 299_993), (1_234_567, 77_777)])
 def test_merge_inplace_learned_matches_oracle(ipm, dev, orc, dist, dt, la, lb):
     import torch

@@ -10,7 +10,7 @@ from gpu_util import NAME, bits, first_diff, from_dev, to_dev
 
 pytestmark = pytest.mark.gpu
 
-DTYPES = [np.int32, np.uint32, np.uint64, np.float32]
+DTYPES = [np.int32, np.uint32, np.uint64, np.float32, np.int64]
 
 
 def _merge_dev(ipm, dev, a, b, log2_pairs=0):
@@ -186,7 +186,7 @@ def test_async_on_a_side_stream(ipm, dev, orc):
 
 @pytest.mark.parametrize("engine,fused", [(0, 0), (0, 1), (0, 2), (0, 3), (0, 4), (1, 1),
                                           (1, 3), (1, 5), (1, 6), (1, 7), (1, 8), (1, 10)])
-@pytest.mark.parametrize("dt", [np.int32, np.uint64])
+@pytest.mark.parametrize("dt", [np.int32, np.uint64, np.int64])
 def test_fused_bottom_levels_match_oracle(ipm, dev, orc, engine, fused, dt):
     """The last `fused` levels done by groups of CTAs (each group stages its pairs, then
     writes them merged; groups synchronised by a thread-block cluster or by a barrier in

@@ -7,10 +7,12 @@ generator (SplitMix64 of seed, stream and index), so the numpy and the torch ver
 produce identical integer inputs.
 
 Distributions (per run, then sorted):
-  uniform       int32 U[0,2^31), uint32 U[0,2^32), uint64 U[0,2^64), float32 U[0,1)
+  uniform       int32 U[0,2^31), uint32 U[0,2^32), uint64 U[0,2^64), int64 the full
+                signed range, float32 U[0,1)
                 on a 2^-24 grid
   dup16         U{0..15} (heavy duplicates)
-  disjoint      max(A) < min(B): A in [0,2^30), B in [2^30,2^31) (uint64: B >= 2^63)
+  disjoint      max(A) < min(B): A in [0,2^30), B in [2^30,2^31) (uint64: B >= 2^63;
+                int64: A in [-2^62, 0), B in [0, 2^62))
   revdisjoint   the same ranges with A and B exchanged (B < A)
   alternation   A[i] = 2i, B[j] = 2j+1
   zipf          key = rank-1, rank ~ Zipf(s=1.2) on 1..2^20, inverse CDF
@@ -31,7 +33,7 @@ C2 = 0x94D049BB133111EB
 DISTS = ("uniform", "dup16", "disjoint", "revdisjoint", "alternation", "zipf", "gmm",
          "paper")
 DTYPES = {"int32": np.int32, "uint32": np.uint32, "uint64": np.uint64,
-          "float32": np.float32}
+          "float32": np.float32, "int64": np.int64}
 
 
 def _mix_seed(seed: int, stream: int) -> int:
@@ -113,6 +115,8 @@ def _values_np(dist: str, dtype, side: int, n: int, seed: int) -> np.ndarray:
             return (h >> np.uint64(32)).astype(np.uint32)
         if dt == np.uint64:
             return h
+        if dt == np.int64:
+            return h.view(np.int64)  # the full signed range
         if dt == np.float32:
             return ((h >> np.uint64(40)).astype(np.float64) * 2.0 ** -24).astype(np.float32)
     if dist in ("disjoint", "revdisjoint"):
@@ -124,6 +128,9 @@ def _values_np(dist: str, dtype, side: int, n: int, seed: int) -> np.ndarray:
         if dt == np.float32:
             v = (h >> np.uint64(41)).astype(np.float64) * 2.0 ** -23
             return (v + (1.0 if hi else 0.0)).astype(np.float32)
+        if dt == np.int64:  # low side negative, high side non-negative
+            v = (h >> np.uint64(2)).astype(np.int64)
+            return v if hi else v - (1 << 62)
         v = (h >> np.uint64(34)).astype(np.int64) + ((1 << 30) if hi else 0)
         return v.astype(dt)
     raise ValueError(f"unknown distribution {dist!r} for {dt}")
@@ -172,7 +179,8 @@ def storage_dtype(torch, dtype):
     """torch storage dtype carrying the key bits (unsigned keys ride in signed ints)."""
     dt = np.dtype(dtype)
     return {np.dtype(np.int32): torch.int32, np.dtype(np.uint32): torch.int32,
-            np.dtype(np.uint64): torch.int64, np.dtype(np.float32): torch.float32}[dt]
+            np.dtype(np.uint64): torch.int64, np.dtype(np.float32): torch.float32,
+            np.dtype(np.int64): torch.int64}[dt]
 
 
 def _sorted_side_torch(torch, dist, dtype, side, n, seed, device):
@@ -200,6 +208,8 @@ def _sorted_side_torch(torch, dist, dtype, side, n, seed, device):
             v = h ^ _i64(1 << 63)  # unsigned order as signed order
             v = torch.sort(v).values ^ _i64(1 << 63)
             return v
+        elif dt == np.int64:
+            return torch.sort(h).values
         else:
             v = _lsr(torch, h, 40).to(torch.float64) * 2.0 ** -24
             return torch.sort(v.to(torch.float32)).values
@@ -213,6 +223,9 @@ def _sorted_side_torch(torch, dist, dtype, side, n, seed, device):
         if dt == np.float32:
             v = _lsr(torch, h, 41).to(torch.float64) * 2.0 ** -23 + (1.0 if hi else 0.0)
             return torch.sort(v.to(torch.float32)).values
+        if dt == np.int64:
+            v = _lsr(torch, h, 2)
+            return torch.sort(v if hi else v - (1 << 62)).values
         v = _lsr(torch, h, 34) + ((1 << 30) if hi else 0)
     else:
         raise ValueError(dist)
