@@ -59,6 +59,7 @@ def _declare(L: ctypes.CDLL) -> None:
     for s in SUFFIX.values():
         getattr(L, f"orc_merge_{s}").argtypes = [vp, u64, vp, u64, vp]
         getattr(L, f"orc_merge_kv_{s}").argtypes = [vp, vp, u64, vp, vp, u64, vp, vp]
+        getattr(L, f"orc_merge_kvw_{s}").argtypes = [vp, vp, u64, vp, vp, u64, u64, vp, vp]
         getattr(L, f"orc_splits_replay_{s}").argtypes = [vp, u64, vp, u64, vp, u64, vp]
         f = getattr(L, f"orc_split_bsearch_{s}")
         f.argtypes = [vp, u64, vp, u64, u64]
@@ -116,6 +117,20 @@ def merge_kv(ka, va, kb, vb):
     vo = np.empty(ka.size + kb.size, dtype=np.uint32)
     getattr(lib(), f"orc_merge_kv_{_sfx(ka, kb)}")(_p(ka), _p(va), ka.size, _p(kb), _p(vb),
                                                    kb.size, _p(ko), _p(vo))
+    return ko, vo
+
+
+def merge_kvw(ka, va, kb, vb):
+    """Key-value stable merge with payloads of any element size (va, vb: numpy arrays
+    of one dtype, e.g. uint64 or a structured record); returns (keys, payloads)."""
+    ka, kb, va, vb = _c(ka), _c(kb), _c(va), _c(vb)
+    if va.dtype != vb.dtype or va.size != ka.size or vb.size != kb.size:
+        raise ValueError("payloads must match their keys and share one dtype")
+    ko = np.empty(ka.size + kb.size, dtype=ka.dtype)
+    vo = np.empty(ka.size + kb.size, dtype=va.dtype)
+    getattr(lib(), f"orc_merge_kvw_{_sfx(ka, kb)}")(_p(ka), _p(va), ka.size, _p(kb), _p(vb),
+                                                    kb.size, va.dtype.itemsize, _p(ko),
+                                                    _p(vo))
     return ko, vo
 
 

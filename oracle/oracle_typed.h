@@ -50,6 +50,27 @@ void FN(orc_merge_kv)(const T *ka, const uint32_t *va, uint64_t la,
 }
 
 /*
+ * The same with a payload of w bytes per element (any record: it is only copied).
+ */
+void FN(orc_merge_kvw)(const T *ka, const unsigned char *va, uint64_t la,
+                       const T *kb, const unsigned char *vb, uint64_t lb, uint64_t w,
+                       T *kout, unsigned char *vout)
+{
+    uint64_t i = 0, j = 0;
+    for (uint64_t t = 0; t < la + lb; ++t) {
+        if (j == lb || (i < la && ka[i] <= kb[j])) {
+            kout[t] = ka[i];
+            memcpy(vout + t * w, va + i * w, (size_t)w);
+            ++i;
+        } else {
+            kout[t] = kb[j];
+            memcpy(vout + t * w, vb + j * w, (size_t)w);
+            ++j;
+        }
+    }
+}
+
+/*
  * Exact split, first form: replay the plain merge and record, for each diagonal
  * d[k] (ascending, each <= la+lb), how many A elements are among the first d[k]
  * outputs.  This is the "optimal" split of Sec. 3.1 taken at a chosen output count.

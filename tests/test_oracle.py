@@ -395,3 +395,33 @@ def test_division_findmedian_close_to_exact_on_the_paper_workload(orc):
             fm = orc.division_balance(*orc.division(a, b, depth, "findmedian"))[0]
             ex = orc.division_balance(*orc.division(a, b, depth, "exact"))[0]
             assert ex > 0 and abs(fm - ex) / ex < 5e-3, (frac, depth, fm, ex)
+
+
+def test_merge_kvw_moves_wide_payloads_as_the_4_byte_form(orc):
+    """A payload of any width follows its key: an 8-byte payload's two halves each
+    equal the 4-byte oracle's payload result, and a 16-byte record moves whole."""
+    rng = random.Random(23)
+    for _ in range(50):
+        la, lb = rng.randint(0, 300), rng.randint(0, 300)
+        a, b = workloads.make_pair(rng.choice(["dup16", "uniform", "zipf"]), np.int64, la,
+                                   lb, seed=rng.randint(0, 9999))
+        va = np.array([rng.getrandbits(64) for _ in range(la)], dtype=np.uint64)
+        vb = np.array([rng.getrandbits(64) for _ in range(lb)], dtype=np.uint64)
+        ko, vo = orc.merge_kvw(a, va, b, vb)
+        for shift in (0, 32):
+            lo_a = ((va >> np.uint64(shift)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+            lo_b = ((vb >> np.uint64(shift)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+            k4, v4 = orc.merge_kv(a, lo_a, b, lo_b)
+            assert np.array_equal(ko, k4)
+            assert np.array_equal(((vo >> np.uint64(shift)) & np.uint64(0xFFFFFFFF))
+                                  .astype(np.uint32), v4)
+        rec = np.dtype([("x", np.uint64), ("y", np.uint64)])
+        ra = np.zeros(la, rec)
+        rb = np.zeros(lb, rec)
+        ra["x"], ra["y"] = va, np.arange(la, dtype=np.uint64)
+        rb["x"], rb["y"] = vb, np.arange(la, la + lb, dtype=np.uint64)
+        _, ro = orc.merge_kvw(a, ra, b, rb)
+        assert np.array_equal(ro["x"], vo)
+        # stability: the origin index rises within each run of equal keys
+        same = ko[1:] == ko[:-1]
+        assert np.all(ro["y"][1:][same] > ro["y"][:-1][same])
