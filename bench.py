@@ -63,6 +63,9 @@ WORKLOADS = {
     "c3-uint32-kv-zipf": ("zipf", "uint32", 1 << 26, 1 << 26,
                           "key-value: uint32 keys Zipf(1.2) over 2^20 ranks, uint32 payload = "
                           "original buffer index, L_A=L_B=2^26; ipm_merge_inplace_kv"),
+    "f1-uint64-kv64-uniform": ("uniform", "uint64", 1 << 27, 1 << 27,
+                               "key-value: uint64 keys uniform [0,2^64), uint64 payload = "
+                               "original buffer index, L_A=L_B=2^27; ipm_merge_inplace_kv"),
     "c1-int32-uniform": ("uniform", "int32", 1 << 20, 1 << 20,
                          "int32 L_A=L_B=2^20, uniform (L2-resident, 8 MiB)"),
     "c2s-int32-uniform": ("uniform", "int32", 1 << 25, 1 << 25,
@@ -77,7 +80,8 @@ WORKLOADS = {
                            "(300 Adam steps); ipm_merge_inplace_learned"),
 }
 FORM = {"c4-int32-batched": "batched", "c5-float32-learned": "learned"}
-KV_WORKLOADS = {"c3-uint32-kv-zipf"}  # plain form with a uint32 payload per key
+# key-value workloads: the payload type per workload (payload = original buffer index)
+KV_WORKLOADS = {"c3-uint32-kv-zipf": "uint32", "f1-uint64-kv64-uniform": "uint64"}
 NP_DT = {"int32": np.int32, "uint32": np.uint32, "uint64": np.uint64, "float32": np.float32,
          "int64": np.int64}
 
@@ -219,16 +223,18 @@ def cpu_oracle_timing(wl, budget_s: float = 10.0, steps: int | None = None,
         return keys * len(times) / tot / 1e9, sample, len(times), tot
 
     dist, dt, la, lb, _ = wl
-    kv = wl is WORKLOADS["c3-uint32-kv-zipf"]
+    vdt = next((KV_WORKLOADS[k] for k, v in WORKLOADS.items()
+                if v is wl and k in KV_WORKLOADS), None)
+    kv = vdt is not None
     scale = max(1, (la + lb) // (1 << 25))
     sa, sb = max(1, la // scale), max(1, lb // scale)
     a, b = workloads.make_pair(dist, NP_DT[dt], sa, sb, seed=0)
-    va = np.arange(sa, dtype=np.uint32)
-    vb = np.arange(sa, sa + sb, dtype=np.uint32)
+    va = np.arange(sa, dtype=NP_DT[vdt] if kv else np.uint32)
+    vb = np.arange(sa, sa + sb, dtype=NP_DT[vdt] if kv else np.uint32)
 
     def merge_once():
         if kv:
-            oracle.merge_kv(a, va, b, vb)
+            oracle.merge_kvw(a, va, b, vb)
         else:
             oracle.merge(a, b)
 
@@ -691,21 +697,27 @@ def run_e2e_learned(torch, ipm, m, steps, stream, model):
 def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
     dist, dt, la, lb, desc = WORKLOADS[args.workload]
     kv = args.workload in KV_WORKLOADS
-    n, w = la + lb, np.dtype(NP_DT[dt]).itemsize + (4 if kv else 0)
+    vdt = KV_WORKLOADS.get(args.workload)
+    vbytes = 8 if vdt == "uint64" else (4 if kv else 0)
+    n, w = la + lb, np.dtype(NP_DT[dt]).itemsize + vbytes
 
     pristine = workloads.make_buffer_torch(torch, dist, NP_DT[dt], la, lb, 0, dev)
     buf = torch.empty_like(pristine)
     # key-value: payload = the key's original buffer index
-    vpristine = torch.arange(n, dtype=torch.int64, device=dev).to(torch.int32) if kv else None
+    vpristine = None
+    if kv:
+        vpristine = torch.arange(n, dtype=torch.int64, device=dev)
+        if vbytes == 4:
+            vpristine = vpristine.to(torch.int32)
     vbuf = torch.empty_like(vpristine) if kv else None
-    G, tile = ipm.ipm_merge_plan(la, lb, dt, with_values=kv)
-    ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, dt, with_values=kv), dev)
+    G, tile = ipm.ipm_merge_plan(la, lb, dt, with_values=vbytes)
+    ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, dt, with_values=vbytes), dev)
 
     mb = method_bytes(n, w)
 
     def merge(kb, vb=None):
         if kv:
-            ipm.ipm_merge_inplace_kv(kb, vb, la, lb, dt, ws)
+            ipm.ipm_merge_inplace_kv(kb, vb, la, lb, dt, ws, val_dtype=vdt)
         else:
             ipm.ipm_merge_inplace(kb, la, lb, dt, ws)
 
@@ -763,8 +775,9 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
     ok_sorted = None
     if dt in ("int32", "int64") and not kv:
         ok_sorted = bool((buf[1:] >= buf[:-1]).all().item())
-    elif kv and dt == "uint32":
-        k64 = buf.to(torch.int64) & 0xFFFFFFFF
+    elif kv and dt in ("uint32", "uint64"):
+        # unsigned order as signed order (uint64: flip the top bit; uint32: widen)
+        k64 = (buf.to(torch.int64) & 0xFFFFFFFF) if dt == "uint32" else (buf ^ (-(1 << 63)))
         ok_sorted = bool(((k64[1:] > k64[:-1]) |
                           ((k64[1:] == k64[:-1]) & (vbuf[1:] > vbuf[:-1]))).all().item())
         del k64
@@ -799,7 +812,7 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": f"{dt} key + uint32 payload" if kv else dt,
+        "dtype": f"{dt} key + {vdt} payload" if kv else dt,
         "data": "synthetic",
         "config": {"workload": args.workload, "description": desc,
                    "form": "key-value" if kv else "plain",

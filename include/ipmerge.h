@@ -73,15 +73,17 @@ int ipm_version(void);
 /*
  * Number of pairs P = 2^log2_pairs the plain merge uses for n = len_a + len_b keys of
  * this dtype (the smallest power of two whose pairs all fit one CTA's shared-memory
- * tile), and that tile's capacity in elements.  with_values selects the key-value
- * tile.  Either output pointer may be NULL.
+ * tile), and that tile's capacity in elements.  with_values is the payload width:
+ * 0 keys only, 1 or 4 a 4-byte payload, 8 an 8-byte payload (other values:
+ * IPM_ERR_UNSUPPORTED_DTYPE).  Either output pointer may be NULL.
  */
 ipm_status ipm_merge_plan(uint64_t len_a, uint64_t len_b, ipm_dtype key_dtype,
                           int with_values, uint32_t *log2_pairs, uint64_t *tile_capacity);
 
 /*
- * Workspace bytes for ipm_merge_inplace / _kv with this size, dtype and pair count
- * (log2_pairs = 0 picks the automatic count of ipm_merge_plan).  The size is O(P):
+ * Workspace bytes for ipm_merge_inplace / _kv with this size, dtype, payload width
+ * (with_values as for ipm_merge_plan) and pair count (log2_pairs = 0 picks the
+ * automatic count of ipm_merge_plan).  The size is O(P):
  * the split table, the per-level exchange plans and a 256-byte status block.
  */
 ipm_status ipm_merge_workspace_bytes(uint64_t len_a, uint64_t len_b, ipm_dtype key_dtype,
@@ -105,9 +107,13 @@ ipm_status ipm_merge_inplace(void *d_buf, uint64_t len_a, uint64_t len_b,
                              size_t ws_bytes, ipm_stream_t stream);
 
 /*
- * Key-value form of ipm_merge_inplace: the 32-bit payload d_vals[t] moves with the key
- * d_keys[t] (structure of arrays).  val_dtype must be IPM_UINT32 (any 4-byte payload
- * can be passed as IPM_UINT32; payloads are never compared).
+ * Key-value form of ipm_merge_inplace: the payload d_vals[t] moves with the key
+ * d_keys[t] (structure of arrays).  Payloads are never compared; val_dtype only gives
+ * their width: a 4-byte type (IPM_UINT32, IPM_INT32, IPM_FLOAT32) or an 8-byte type
+ * (IPM_UINT64, IPM_INT64; any 8-byte record can be passed as IPM_UINT64).  d_vals is
+ * aligned to that width.  The workspace comes from ipm_merge_workspace_bytes with
+ * with_values = the payload width.  Key-value tiles hold fewer elements (the
+ * shared-memory tile is shared by keys and payloads), so more pairs are used.
  */
 ipm_status ipm_merge_inplace_kv(void *d_keys, void *d_vals, uint64_t len_a,
                                 uint64_t len_b, ipm_dtype key_dtype, ipm_dtype val_dtype,

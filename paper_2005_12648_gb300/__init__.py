@@ -189,19 +189,29 @@ def ipm_version() -> int:
     return int(load().ipm_version())
 
 
-def ipm_merge_plan(len_a: int, len_b: int, key_dtype, with_values: bool = False):
+def _payload(with_values) -> int:
+    """The with_values argument of the merge queries: False / 0 keys only, True / 1 / 4 a
+    4-byte payload, 8 an 8-byte payload; a dtype name gives its size."""
+    if isinstance(with_values, bool):
+        return int(with_values)
+    if isinstance(with_values, str):
+        return _ELEM[DTYPES[with_values]]
+    return int(with_values)
+
+
+def ipm_merge_plan(len_a: int, len_b: int, key_dtype, with_values=False):
     """Returns (log2_pairs, tile_capacity)."""
     g, t = _u32(0), _u64(0)
-    _check(load().ipm_merge_plan(len_a, len_b, _dt(key_dtype), int(bool(with_values)),
+    _check(load().ipm_merge_plan(len_a, len_b, _dt(key_dtype), _payload(with_values),
                                  ctypes.byref(g), ctypes.byref(t)), "ipm_merge_plan")
     return int(g.value), int(t.value)
 
 
-def ipm_merge_workspace_bytes(len_a: int, len_b: int, key_dtype, with_values: bool = False,
+def ipm_merge_workspace_bytes(len_a: int, len_b: int, key_dtype, with_values=False,
                               log2_pairs: int = 0) -> int:
     out = _sz(0)
     _check(load().ipm_merge_workspace_bytes(len_a, len_b, _dt(key_dtype),
-                                            int(bool(with_values)), log2_pairs,
+                                            _payload(with_values), log2_pairs,
                                             ctypes.byref(out)), "ipm_merge_workspace_bytes")
     return int(out.value)
 
@@ -492,11 +502,16 @@ def merge_inplace(buf, len_a: int, len_b: int, key_dtype, log2_pairs: int = 0, s
 
 
 def merge_inplace_kv(keys, vals, len_a: int, len_b: int, key_dtype, log2_pairs: int = 0,
-                     stream=None):
-    ws = workspace(ipm_merge_workspace_bytes(len_a, len_b, key_dtype, True, log2_pairs),
+                     stream=None, val_dtype=None):
+    """Allocate the workspace and merge keys with their payloads (4- or 8-byte: the
+    payload tensor's element size when val_dtype is not given)."""
+    if val_dtype is None:
+        val_dtype = "uint64" if vals.element_size() == 8 else "uint32"
+    vb = _ELEM[_dt(val_dtype)]
+    ws = workspace(ipm_merge_workspace_bytes(len_a, len_b, key_dtype, vb, log2_pairs),
                    keys.device)
-    ipm_merge_inplace_kv(keys, vals, len_a, len_b, key_dtype, ws, log2_pairs=log2_pairs,
-                         stream=stream)
+    ipm_merge_inplace_kv(keys, vals, len_a, len_b, key_dtype, ws, val_dtype=val_dtype,
+                         log2_pairs=log2_pairs, stream=stream)
     return ws
 
 

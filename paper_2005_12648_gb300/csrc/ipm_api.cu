@@ -104,12 +104,14 @@ uint32_t auto_log2_pairs(uint64_t n, uint64_t tile) {
 }
 
 // Checks shared by the merge entry points; resolves G.
-ipm_status check_merge_args(uint64_t la, uint64_t lb, ipm_dtype key, bool kv,
+// vb: payload bytes per element (0 keys only, 4 or 8).
+ipm_status check_merge_args(uint64_t la, uint64_t lb, ipm_dtype key, uint32_t vb,
                             uint32_t log2_pairs, uint32_t *G_out) {
     if (!valid_key(key)) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (vb != 0 && vb != 4 && vb != 8) return IPM_ERR_UNSUPPORTED_DTYPE;
     if (la > (uint64_t(1) << 40) || lb > (uint64_t(1) << 40)) return IPM_ERR_INVALID_ARG;
     const uint64_t n = la + lb;
-    const uint64_t tile = tile_capacity(key, kv);
+    const uint64_t tile = tile_capacity(key, vb);
     const uint32_t G = log2_pairs ? log2_pairs : auto_log2_pairs(n, tile);
     if (G > kMaxLog2Pairs) return IPM_ERR_INVALID_ARG;
     // every pair must fit one tile: ceil(n / 2^G) <= tile
@@ -136,27 +138,35 @@ struct MergeLayout {
 };
 
 // status block | split table (P+1) | group counters (P) | exchange plans
-MergeLayout merge_layout(uint32_t G, uint64_t n, ipm_dtype key, bool kv) {
+MergeLayout merge_layout(uint32_t G, uint64_t n, ipm_dtype key, uint32_t vb) {
     MergeLayout L;
     const uint64_t P = uint64_t(1) << G;
     L.split_off = kStatusBytes;
     L.group_off = L.split_off + align_up(sizeof(uint64_t) * (P + 1), 256);
     L.plan_off = L.group_off + align_up(sizeof(uint32_t) * P, 256);
-    L.total = L.plan_off + xplan_area_bytes(G, n, key, kv);
+    L.total = L.plan_off + xplan_area_bytes(G, n, key, vb);
     return L;
 }
 
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-ipm_status merge_core(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_dtype key,
-                      uint32_t log2_pairs, void *ws, size_t ws_bytes, cudaStream_t stream,
-                      const ipm_split_model *model = nullptr) {
-    const bool kv = vals != nullptr;
+// The with_values argument of the queries: 0 keys only, 1 or 4 a 4-byte payload, 8 an
+// 8-byte payload; anything else is returned as 1 (rejected by check_merge_args).
+uint32_t payload_bytes(int with_values) {
+    if (with_values == 0) return 0;
+    if (with_values == 1 || with_values == 4) return 4;
+    return with_values == 8 ? 8u : 1u;
+}
+
+ipm_status merge_core(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t lb,
+                      ipm_dtype key, uint32_t log2_pairs, void *ws, size_t ws_bytes,
+                      cudaStream_t stream, const ipm_split_model *model = nullptr) {
+    if (vals == nullptr) vb = 0;
     uint32_t G = 0;
-    IPM_TRY(check_merge_args(la, lb, key, kv, log2_pairs, &G));
+    IPM_TRY(check_merge_args(la, lb, key, vb, log2_pairs, &G));
     if (la + lb == 0) return IPM_OK;
     if (buf == nullptr || ws == nullptr) return buf ? IPM_ERR_WORKSPACE : IPM_ERR_INVALID_ARG;
-    if (!aligned(buf, size_t(dtype_bytes(key))) || (kv && !aligned(vals, 4)))
+    if (!aligned(buf, size_t(dtype_bytes(key))) || (vb && !aligned(vals, vb)))
         return IPM_ERR_ALIGNMENT;
     if (!aligned(ws, 256)) return IPM_ERR_ALIGNMENT;
     const uint64_t n = la + lb;
@@ -164,16 +174,17 @@ ipm_status merge_core(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_d
     // thread-block clusters for F <= 4 when selected, else global-memory group
     // barriers) splits one level deeper: every pair then fits the half tile.
     const uint32_t Fwant = g_fused_levels < G + 1 ? g_fused_levels : G + 1;
-    const bool use_clusters = g_fused_engine == 0;
-    const uint32_t F = use_clusters ? usable_fused_levels(key, kv, Fwant > 4 ? 4 : Fwant)
-                                    : usable_group_levels(key, kv, Fwant);
+    // (the cluster kernels move 4-byte payloads; 8-byte ones take the group barrier)
+    const bool use_clusters = g_fused_engine == 0 && vb != 8;
+    const uint32_t F = use_clusters ? usable_fused_levels(key, vb != 0, Fwant > 4 ? 4 : Fwant)
+                                    : usable_group_levels(key, vb, Fwant);
     const uint32_t Gs = F > 0 ? G + 1 : G;  // depth of the split table
-    const MergeLayout L = merge_layout(Gs, n, key, kv);
+    const MergeLayout L = merge_layout(Gs, n, key, vb);
     if (ws_bytes < L.total) return IPM_ERR_WORKSPACE;
     char *w = static_cast<char *>(ws);
     StatusBlock *sb = reinterpret_cast<StatusBlock *>(w);
     uint64_t *split = reinterpret_cast<uint64_t *>(w + L.split_off);
-    const XPlanArea pa = xplan_area_at(w + L.plan_off, Gs, n, key, kv);
+    const XPlanArea pa = xplan_area_at(w + L.plan_off, Gs, n, key, vb);
     const uint64_t P = uint64_t(1) << Gs;
 
     {
@@ -192,20 +203,21 @@ ipm_status merge_core(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, ipm_d
     // with the pair merge (clusters of 2^F CTAs)
     if (Gs > F) {
         PhaseScope ps(1, 1, stream);
-        IPM_TRY(launch_xplan_levels(split, n, Gs, Gs - F, pa, key, kv, sb, stream));
+        IPM_TRY(launch_xplan_levels(split, n, Gs, Gs - F, pa, key, vb, sb, stream));
     }
     for (uint32_t l = 0; l + F < Gs; ++l) {
         PhaseScope ps(2, 1, stream);
-        IPM_TRY(launch_exchange_level(buf, vals, key, n, l, pa, sb, stream));
+        IPM_TRY(launch_exchange_level(buf, vals, vb, key, n, l, pa, sb, stream));
     }
     // a3: pair merge (fused with the last F levels when F > 0)
     PhaseScope ps(3, 1, stream);
     if (F > 0 && use_clusters)
-        return launch_cluster_merge(buf, vals, la, lb, key, split, Gs, F, sb, stream);
+        return launch_cluster_merge(buf, static_cast<uint32_t *>(vals), la, lb, key, split, Gs,
+                                    F, sb, stream);
     if (F > 0)
-        return launch_group_merge(buf, vals, la, lb, key, split, Gs, F,
+        return launch_group_merge(buf, vals, vb, la, lb, key, split, Gs, F,
                                   reinterpret_cast<uint32_t *>(w + L.group_off), sb, stream);
-    return launch_tile_merge(buf, vals, la, lb, key, split, G, sb, stream);
+    return launch_tile_merge(buf, vals, vb, la, lb, key, split, G, sb, stream);
 }
 
 }  // namespace
@@ -242,9 +254,10 @@ int ipm_version(void) { return 100; }
 ipm_status ipm_merge_plan(uint64_t len_a, uint64_t len_b, ipm_dtype key_dtype,
                           int with_values, uint32_t *log2_pairs, uint64_t *tile_cap) {
     uint32_t G = 0;
-    IPM_TRY(check_merge_args(len_a, len_b, key_dtype, with_values != 0, 0, &G));
+    const uint32_t vb = payload_bytes(with_values);
+    IPM_TRY(check_merge_args(len_a, len_b, key_dtype, vb, 0, &G));
     if (log2_pairs) *log2_pairs = G;
-    if (tile_cap) *tile_cap = tile_capacity(key_dtype, with_values != 0);
+    if (tile_cap) *tile_cap = tile_capacity(key_dtype, vb);
     return IPM_OK;
 }
 
@@ -252,16 +265,17 @@ ipm_status ipm_merge_workspace_bytes(uint64_t len_a, uint64_t len_b, ipm_dtype k
                                      int with_values, uint32_t log2_pairs, size_t *bytes) {
     if (bytes == nullptr) return IPM_ERR_INVALID_ARG;
     uint32_t G = 0;
-    IPM_TRY(check_merge_args(len_a, len_b, key_dtype, with_values != 0, log2_pairs, &G));
+    const uint32_t vb = payload_bytes(with_values);
+    IPM_TRY(check_merge_args(len_a, len_b, key_dtype, vb, log2_pairs, &G));
     // room for the fused path's split table one level deeper
-    *bytes = merge_layout(G + 1, len_a + len_b, key_dtype, with_values != 0).total;
+    *bytes = merge_layout(G + 1, len_a + len_b, key_dtype, vb).total;
     return IPM_OK;
 }
 
 ipm_status ipm_merge_inplace(void *d_buf, uint64_t len_a, uint64_t len_b,
                              ipm_dtype key_dtype, uint32_t log2_pairs, void *d_ws,
                              size_t ws_bytes, ipm_stream_t stream) {
-    return merge_core(d_buf, nullptr, len_a, len_b, key_dtype, log2_pairs, d_ws, ws_bytes,
+    return merge_core(d_buf, nullptr, 0, len_a, len_b, key_dtype, log2_pairs, d_ws, ws_bytes,
                       (cudaStream_t)stream);
 }
 
@@ -269,11 +283,13 @@ ipm_status ipm_merge_inplace_kv(void *d_keys, void *d_vals, uint64_t len_a,
                                 uint64_t len_b, ipm_dtype key_dtype, ipm_dtype val_dtype,
                                 uint32_t log2_pairs, void *d_ws, size_t ws_bytes,
                                 ipm_stream_t stream) {
-    if (val_dtype != IPM_UINT32) return IPM_ERR_UNSUPPORTED_DTYPE;
+    // payloads are moved, never compared: any 4- or 8-byte type
+    if (!valid_key(val_dtype)) return IPM_ERR_UNSUPPORTED_DTYPE;
+    const uint32_t vb = uint32_t(dtype_bytes(val_dtype));
     if (d_vals == nullptr && len_a + len_b > 0) return IPM_ERR_INVALID_ARG;
     if (len_a + len_b == 0) return valid_key(key_dtype) ? IPM_OK : IPM_ERR_UNSUPPORTED_DTYPE;
-    return merge_core(d_keys, static_cast<uint32_t *>(d_vals), len_a, len_b, key_dtype,
-                      log2_pairs, d_ws, ws_bytes, (cudaStream_t)stream);
+    return merge_core(d_keys, d_vals, vb, len_a, len_b, key_dtype, log2_pairs, d_ws, ws_bytes,
+                      (cudaStream_t)stream);
 }
 
 ipm_status ipm_merge_splits(const void *d_buf, uint64_t len_a, uint64_t len_b,
@@ -308,17 +324,17 @@ ipm_status ipm_merge_rearrange(void *d_buf, void *d_vals, uint64_t len_a, uint64
         !aligned(d_ws, 256))
         return IPM_ERR_ALIGNMENT;
     const uint64_t n = len_a + len_b;
-    const MergeLayout L = merge_layout(G, n, key_dtype, kv);
+    const uint32_t vb = kv ? 4u : 0u;  // uint32 payloads
+    const MergeLayout L = merge_layout(G, n, key_dtype, vb);
     if (ws_bytes < L.total) return IPM_ERR_WORKSPACE;
     cudaStream_t st = (cudaStream_t)stream;
     char *w = static_cast<char *>(d_ws);
     StatusBlock *sb = reinterpret_cast<StatusBlock *>(w);
     IPM_CUDA_TRY(cudaMemsetAsync(sb, 0, kStatusBytes, st));
-    const XPlanArea pa = xplan_area_at(w + L.plan_off, G, n, key_dtype, kv);
-    IPM_TRY(launch_xplan_levels(d_split_a, n, G, G, pa, key_dtype, kv, sb, st));
+    const XPlanArea pa = xplan_area_at(w + L.plan_off, G, n, key_dtype, vb);
+    IPM_TRY(launch_xplan_levels(d_split_a, n, G, G, pa, key_dtype, vb, sb, st));
     for (uint32_t l = 0; l < G; ++l)
-        IPM_TRY(launch_exchange_level(d_buf, static_cast<uint32_t *>(d_vals), key_dtype, n, l,
-                                      pa, sb, st));
+        IPM_TRY(launch_exchange_level(d_buf, d_vals, vb, key_dtype, n, l, pa, sb, st));
     return IPM_OK;
 }
 
@@ -327,14 +343,15 @@ ipm_status ipm_merge_pairs(void *d_buf, void *d_vals, uint64_t len_a, uint64_t l
                            uint32_t log2_pairs, ipm_stream_t stream) {
     const bool kv = d_vals != nullptr;
     uint32_t G = 0;
-    IPM_TRY(check_merge_args(len_a, len_b, key_dtype, kv, log2_pairs, &G));
+    const uint32_t vb = kv ? 4u : 0u;  // uint32 payloads
+    IPM_TRY(check_merge_args(len_a, len_b, key_dtype, vb, log2_pairs, &G));
     if (G != log2_pairs) return IPM_ERR_INVALID_ARG;
     if (len_a + len_b == 0) return IPM_OK;
     if (d_buf == nullptr || d_split_a == nullptr) return IPM_ERR_INVALID_ARG;
     if (!aligned(d_buf, size_t(dtype_bytes(key_dtype))) || (kv && !aligned(d_vals, 4)))
         return IPM_ERR_ALIGNMENT;
-    return launch_tile_merge(d_buf, static_cast<uint32_t *>(d_vals), len_a, len_b, key_dtype,
-                             d_split_a, G, nullptr, (cudaStream_t)stream);
+    return launch_tile_merge(d_buf, d_vals, vb, len_a, len_b, key_dtype, d_split_a, G, nullptr,
+                             (cudaStream_t)stream);
 }
 
 ipm_status ipm_rotate_workspace_bytes(uint64_t len_x, uint64_t len_y, uint32_t elem_bytes,
@@ -343,7 +360,7 @@ ipm_status ipm_rotate_workspace_bytes(uint64_t len_x, uint64_t len_y, uint32_t e
     if (elem_bytes != 4 && elem_bytes != 8) return IPM_ERR_UNSUPPORTED_DTYPE;
     if (len_x > (uint64_t(1) << 40) || len_y > (uint64_t(1) << 40)) return IPM_ERR_INVALID_ARG;
     const ipm_dtype t = elem_bytes == 4 ? IPM_UINT32 : IPM_UINT64;
-    *bytes = kStatusBytes + xplan_area_bytes(1, 2 * (len_x + len_y), t, false);
+    *bytes = kStatusBytes + xplan_area_bytes(1, 2 * (len_x + len_y), t, 0u);
     return IPM_OK;
 }
 
@@ -362,9 +379,9 @@ ipm_status ipm_rotate(void *d_ptr, uint64_t len_x, uint64_t len_y, uint32_t elem
     IPM_CUDA_TRY(cudaMemsetAsync(sb, 0, kStatusBytes, st));
     // one exchange at offset 0: level 0 of a layout sized for 2(len_x + len_y) keys, so
     // the flag area covers every item of this exchange
-    const XPlanArea pa = xplan_area_at(w + kStatusBytes, 1, 2 * (len_x + len_y), t, false);
+    const XPlanArea pa = xplan_area_at(w + kStatusBytes, 1, 2 * (len_x + len_y), t, 0u);
     IPM_TRY(launch_xplan_single(len_x, len_y, pa, t, st));
-    return launch_exchange_level(d_ptr, nullptr, t, len_x + len_y, 0, pa, sb, st);
+    return launch_exchange_level(d_ptr, nullptr, 0u, t, len_x + len_y, 0, pa, sb, st);
 }
 
 ipm_status ipm_division_splits(const void *d_buf, uint64_t len_a, uint64_t len_b,
@@ -552,7 +569,7 @@ ipm_status ipm_merge_inplace_learned(void *d_buf, uint64_t len_a, uint64_t len_b
                                      size_t ws_bytes, ipm_stream_t stream) {
     if (d_model == nullptr) return IPM_ERR_INVALID_ARG;
     if (!aligned(d_model, 4)) return IPM_ERR_ALIGNMENT;
-    return merge_core(d_buf, nullptr, len_a, len_b, key_dtype, log2_pairs, d_ws, ws_bytes,
+    return merge_core(d_buf, nullptr, 0, len_a, len_b, key_dtype, log2_pairs, d_ws, ws_bytes,
                       (cudaStream_t)stream, d_model);
 }
 

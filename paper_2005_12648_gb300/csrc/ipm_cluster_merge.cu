@@ -41,12 +41,13 @@ __device__ __forceinline__ void cluster_sync_all() {
             : "memory");
 }
 
-template <typename K, bool KV, int THREADS, int E>
+template <typename K, bool KV, int THREADS, int E, typename V = uint32_t>
 struct ClusterShape {
     static constexpr int kTile = THREADS * E;
     static constexpr int kSlack = 16;  // phase offsets of the three ranges
     static constexpr size_t kKeyBytes = (size_t(kTile + kSlack) * sizeof(K) + 15) / 16 * 16;
-    static constexpr size_t kValBytes = KV ? (size_t(kTile + kSlack) * 4 + 15) / 16 * 16 : 0;
+    static constexpr size_t kValBytes =
+        KV ? (size_t(kTile + kSlack) * sizeof(V) + 15) / 16 * 16 : 0;
     static constexpr size_t kSmem = 128 + kKeyBytes + kValBytes;
 };
 
@@ -91,10 +92,10 @@ __device__ __forceinline__ void store_range(T *dst, const T *src, uint32_t len) 
 
 // Geometry of one CTA's pair in the current group, computed by thread 0 into shared
 // memory (so the merge does not have to keep it in registers).
-template <typename K>
+template <typename K, typename V = uint32_t>
 struct PairGeo {
     K *gA, *gB, *gO;              // the A slice, the B slice, the output range
-    uint32_t *vA, *vB, *vO;       // payload ranges (key-value)
+    V *vA, *vB, *vO;              // payload ranges (key-value)
     uint32_t a, b;                // run lengths
     uint32_t offA, offB, oo;      // staged offsets (keys)
     uint32_t offAV, offBV, ooV;   // staged offsets (payloads)
@@ -241,13 +242,13 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
 
 // Claim the next pair (thread 0): its ticket and, when it is a pair, its geometry
 // within its group's region.  Returns the ticket.
-template <typename K, bool KV, uint32_t TILE>
-__device__ __forceinline__ uint32_t group_claim(PairGeo<K> &pg, K *buf, uint32_t *vals,
+template <typename K, bool KV, uint32_t TILE, typename V>
+__device__ __forceinline__ uint32_t group_claim(PairGeo<K, V> &pg, K *buf, V *vals,
                                                 uint64_t la, uint64_t lb,
                                                 const uint64_t *__restrict__ split,
                                                 uint32_t G, uint32_t F, StatusBlock *sb) {
     constexpr uint32_t VK = 16u / uint32_t(sizeof(K));
-    constexpr uint32_t VV = 4u;
+    constexpr uint32_t VV = 16u / uint32_t(sizeof(V));
     const uint32_t t = atomicAdd(&sb->counters[kGroupTicket], 1u);
     if (uint64_t(t) >= (1ull << G)) return t;
     const uint64_t n = la + lb;
@@ -277,7 +278,7 @@ __device__ __forceinline__ uint32_t group_claim(PairGeo<K> &pg, K *buf, uint32_t
     pg.offB = offA + a + ((phase_of(gB) + VK - (offA + a) % VK) % VK);
     pg.oo = oo;
     if (KV) {
-        uint32_t *vA = vals + posA, *vB = vals + posB, *vO = vals + d0;
+        V *vA = vals + posA, *vB = vals + posB, *vO = vals + d0;
         const uint32_t ooV = phase_of(vO);
         const uint32_t offAV = ooV + ((phase_of(vA) + VV - ooV) % VV);
         pg.vA = vA;
@@ -290,19 +291,19 @@ __device__ __forceinline__ uint32_t group_claim(PairGeo<K> &pg, K *buf, uint32_t
     return t;
 }
 
-template <typename K, bool KV, int THREADS, int E>
+template <typename K, bool KV, int THREADS, int E, typename V>
 __global__ void __launch_bounds__(THREADS, 2)
-    group_merge_kernel(K *__restrict__ buf, uint32_t *__restrict__ vals, uint64_t la,
+    group_merge_kernel(K *__restrict__ buf, V *__restrict__ vals, uint64_t la,
                        uint64_t lb, const uint64_t *__restrict__ split, uint32_t G, uint32_t F,
                        uint32_t *__restrict__ gctr, StatusBlock *sb) {
-    using Shape = ClusterShape<K, KV, THREADS, E>;
+    using Shape = ClusterShape<K, KV, THREADS, E, V>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);
     K *R = reinterpret_cast<K *>(smem_raw + 128);
-    uint32_t *RV = reinterpret_cast<uint32_t *>(smem_raw + 128 + Shape::kKeyBytes);
+    V *RV = reinterpret_cast<V *>(smem_raw + 128 + Shape::kKeyBytes);
     __shared__ int abort_flag;
     __shared__ uint32_t s_t[2];
-    __shared__ PairGeo<K> pgs[2];  // the current pair and the next one
+    __shared__ PairGeo<K, V> pgs[2];  // the current pair and the next one
     if (sb == nullptr || *((volatile unsigned int *)&sb->done)) return;
     const uint32_t tid = threadIdx.x;
     const uint64_t P = 1ull << G;
@@ -311,7 +312,7 @@ __global__ void __launch_bounds__(THREADS, 2)
         mbar_init(mbar, 1);
         mbar_fence_init();
         abort_flag = 0;
-        s_t[0] = group_claim<K, KV, Shape::kTile>(pgs[0], buf, vals, la, lb, split, G, F, sb);
+        s_t[0] = group_claim<K, KV, Shape::kTile, V>(pgs[0], buf, vals, la, lb, split, G, F, sb);
     }
     __syncthreads();
     uint32_t parity = 0, cur = 0;
@@ -319,7 +320,7 @@ __global__ void __launch_bounds__(THREADS, 2)
     for (;;) {
         const uint32_t t = s_t[cur];
         if (t >= P) break;
-        volatile PairGeo<K> &vg = pgs[cur];
+        volatile PairGeo<K, V> &vg = pgs[cur];
         const uint32_t a = vg.a, b = vg.b;
 
         // ---- stage both slices
@@ -332,8 +333,8 @@ __global__ void __launch_bounds__(THREADS, 2)
             stage_range<K, THREADS>(R + vg.offA, vg.gA, a, mbar);
             stage_range<K, THREADS>(R + vg.offB, vg.gB, b, mbar);
             if (KV) {
-                stage_range<uint32_t, THREADS>(RV + vg.offAV, vg.vA, a, mbar);
-                stage_range<uint32_t, THREADS>(RV + vg.offBV, vg.vB, b, mbar);
+                stage_range<V, THREADS>(RV + vg.offAV, vg.vA, a, mbar);
+                stage_range<V, THREADS>(RV + vg.offBV, vg.vB, b, mbar);
             }
             if (!mbar_wait_bounded(mbar, parity)) atomicOr(&abort_flag, 1);
             parity ^= 1u;
@@ -347,7 +348,7 @@ __global__ void __launch_bounds__(THREADS, 2)
         // ---- merge on chip into the output's phase (a move when a run is empty); only
         // shared memory is written, so this needs no barrier
         if (a + b > 0 && !abort_flag)
-            merge_two<K, KV, THREADS, E, true>(R + vg.offA, RV + vg.offAV, a,
+            merge_two<K, KV, THREADS, E, true, V>(R + vg.offA, RV + vg.offAV, a,
                                                vg.offB - vg.offA, vg.offBV - vg.offAV, b,
                                                R + vg.oo, RV + vg.ooV);
         fence_proxy_async_smem();
@@ -378,12 +379,12 @@ __global__ void __launch_bounds__(THREADS, 2)
         // ---- store, and claim the next pair while the bulk store reads shared memory
         if (a + b > 0) {
             store_range<K, THREADS>(vg.gO, R + vg.oo, a + b);
-            if (KV) store_range<uint32_t, THREADS>(vg.vO, RV + vg.ooV, a + b);
+            if (KV) store_range<V, THREADS>(vg.vO, RV + vg.ooV, a + b);
         }
         if (tid == 0) {
             bulk_commit();
             s_t[cur ^ 1u] =
-                group_claim<K, KV, Shape::kTile>(pgs[cur ^ 1u], buf, vals, la, lb, split, G, F, sb);
+                group_claim<K, KV, Shape::kTile, V>(pgs[cur ^ 1u], buf, vals, la, lb, split, G, F, sb);
             bulk_wait_read0();
         }
         fence_proxy_async_smem();
@@ -393,10 +394,10 @@ __global__ void __launch_bounds__(THREADS, 2)
     if (tid == 0) bulk_wait_all0();
 }
 
-template <typename K, bool KV, int THREADS, int E>
+template <typename K, bool KV, int THREADS, int E, typename V>
 int group_grid() {
-    using Shape = ClusterShape<K, KV, THREADS, E>;
-    auto kern = group_merge_kernel<K, KV, THREADS, E>;
+    using Shape = ClusterShape<K, KV, THREADS, E, V>;
+    auto kern = group_merge_kernel<K, KV, THREADS, E, V>;
     static int cached = -1;
     if (cached >= 0) return cached;
     cached = 0;
@@ -415,17 +416,17 @@ int group_grid() {
     return cached;
 }
 
-template <typename K, bool KV, int THREADS, int E>
-ipm_status group_merge_t(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
+template <typename K, bool KV, int THREADS, int E, typename V>
+ipm_status group_merge_t(void *buf, void *vals, uint64_t la, uint64_t lb,
                          const uint64_t *split, uint32_t G, uint32_t F, uint32_t *gctr,
                          StatusBlock *sb, cudaStream_t stream) {
-    using Shape = ClusterShape<K, KV, THREADS, E>;
-    const int grid = group_grid<K, KV, THREADS, E>();
+    using Shape = ClusterShape<K, KV, THREADS, E, V>;
+    const int grid = group_grid<K, KV, THREADS, E, V>();
     if (grid < (1 << F)) return IPM_ERR_CUDA;
     const uint64_t P = 1ull << G;
     const unsigned g = unsigned(P < uint64_t(grid) ? P : uint64_t(grid));
-    group_merge_kernel<K, KV, THREADS, E><<<g, THREADS, Shape::kSmem, stream>>>(
-        (K *)buf, vals, la, lb, split, G, F, gctr, sb);
+    group_merge_kernel<K, KV, THREADS, E, V><<<g, THREADS, Shape::kSmem, stream>>>(
+        (K *)buf, (V *)vals, la, lb, split, G, F, gctr, sb);
     return last_launch_status();
 }
 
@@ -495,9 +496,12 @@ ipm_status cluster_merge_t(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
 // Half the plain merge's tile (two CTAs per SM, so one CTA's merge overlaps the
 // other's staging): 4-byte keys 512 x 33, 8-byte keys and key-value 256 x 33.  The
 // caller splits one level deeper so that every pair fits.
-template <typename K, bool KV>
+// Half the plain merge's tile: 4-byte keys alone 512 x 33; up to 12 bytes per element
+// 256 x 33; 16 bytes (8-byte keys with an 8-byte payload) 128 x 33.
+template <typename K, bool KV, typename V = uint32_t>
 struct ClusterTileOf {
-    static constexpr int T = (sizeof(K) == 4 && !KV) ? 512 : 256, E = 33;
+    static constexpr int kElem = int(sizeof(K)) + (KV ? int(sizeof(V)) : 0);
+    static constexpr int T = kElem == 4 ? 512 : (kElem <= 12 ? 256 : 128), E = 33;
 };
 
 template <typename K, int C>
@@ -554,54 +558,71 @@ ipm_status cluster_by_key(void *buf, uint32_t *vals, uint64_t la, uint64_t lb, i
     return IPM_ERR_UNSUPPORTED_DTYPE;
 }
 
-template <typename K>
-ipm_status group_dispatch(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
-                          const uint64_t *split, uint32_t G, uint32_t F, uint32_t *gctr,
-                          StatusBlock *sb, cudaStream_t stream) {
-    if (vals != nullptr)
-        return group_merge_t<K, true, ClusterTileOf<K, true>::T, ClusterTileOf<K, true>::E>(
-            buf, vals, la, lb, split, G, F, gctr, sb, stream);
-    return group_merge_t<K, false, ClusterTileOf<K, false>::T, ClusterTileOf<K, false>::E>(
-        buf, nullptr, la, lb, split, G, F, gctr, sb, stream);
+template <typename K, bool KV, typename V>
+ipm_status group_shape_t(void *buf, void *vals, uint64_t la, uint64_t lb,
+                         const uint64_t *split, uint32_t G, uint32_t F, uint32_t *gctr,
+                         StatusBlock *sb, cudaStream_t stream) {
+    return group_merge_t<K, KV, ClusterTileOf<K, KV, V>::T, ClusterTileOf<K, KV, V>::E, V>(
+        buf, vals, la, lb, split, G, F, gctr, sb, stream);
 }
 
 template <typename K>
-int group_grid_kv(bool kv) {
-    return kv ? group_grid<K, true, ClusterTileOf<K, true>::T, ClusterTileOf<K, true>::E>()
-              : group_grid<K, false, ClusterTileOf<K, false>::T, ClusterTileOf<K, false>::E>();
+ipm_status group_dispatch(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t lb,
+                          const uint64_t *split, uint32_t G, uint32_t F, uint32_t *gctr,
+                          StatusBlock *sb, cudaStream_t stream) {
+    if (vb == 8)
+        return group_shape_t<K, true, uint64_t>(buf, vals, la, lb, split, G, F, gctr, sb,
+                                                stream);
+    if (vb != 0)
+        return group_shape_t<K, true, uint32_t>(buf, vals, la, lb, split, G, F, gctr, sb,
+                                                stream);
+    return group_shape_t<K, false, uint32_t>(buf, nullptr, la, lb, split, G, F, gctr, sb,
+                                             stream);
+}
+
+template <typename K>
+int group_grid_kv(uint32_t vb) {
+    if (vb == 8)
+        return group_grid<K, true, ClusterTileOf<K, true, uint64_t>::T,
+                          ClusterTileOf<K, true, uint64_t>::E, uint64_t>();
+    if (vb != 0)
+        return group_grid<K, true, ClusterTileOf<K, true>::T, ClusterTileOf<K, true>::E,
+                          uint32_t>();
+    return group_grid<K, false, ClusterTileOf<K, false>::T, ClusterTileOf<K, false>::E,
+                      uint32_t>();
 }
 
 }  // namespace
 
-uint32_t usable_group_levels(ipm_dtype key, bool with_values, uint32_t wanted) {
+uint32_t usable_group_levels(ipm_dtype key, uint32_t vb, uint32_t wanted) {
     int grid = 0;
     switch (key) {
-    case IPM_INT32: grid = group_grid_kv<int32_t>(with_values); break;
-    case IPM_UINT32: grid = group_grid_kv<uint32_t>(with_values); break;
-    case IPM_UINT64: grid = group_grid_kv<uint64_t>(with_values); break;
-    case IPM_INT64: grid = group_grid_kv<int64_t>(with_values); break;
-    case IPM_FLOAT32: grid = group_grid_kv<float>(with_values); break;
+    case IPM_INT32: grid = group_grid_kv<int32_t>(vb); break;
+    case IPM_UINT32: grid = group_grid_kv<uint32_t>(vb); break;
+    case IPM_UINT64: grid = group_grid_kv<uint64_t>(vb); break;
+    case IPM_INT64: grid = group_grid_kv<int64_t>(vb); break;
+    case IPM_FLOAT32: grid = group_grid_kv<float>(vb); break;
     }
     uint32_t f = wanted;
     while (f > 0 && (1 << f) > grid) --f;  // a whole group must fit the resident CTAs
     return f;
 }
 
-ipm_status launch_group_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
+ipm_status launch_group_merge(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t lb,
                               ipm_dtype key, const uint64_t *split, uint32_t G, uint32_t F,
                               uint32_t *gctr, StatusBlock *sb, cudaStream_t stream) {
     IPM_CUDA_TRY(cudaMemsetAsync(gctr, 0, sizeof(uint32_t) * size_t((1ull << G) >> F), stream));
     switch (key) {
     case IPM_INT32:
-        return group_dispatch<int32_t>(buf, vals, la, lb, split, G, F, gctr, sb, stream);
+        return group_dispatch<int32_t>(buf, vals, vb, la, lb, split, G, F, gctr, sb, stream);
     case IPM_UINT32:
-        return group_dispatch<uint32_t>(buf, vals, la, lb, split, G, F, gctr, sb, stream);
+        return group_dispatch<uint32_t>(buf, vals, vb, la, lb, split, G, F, gctr, sb, stream);
     case IPM_UINT64:
-        return group_dispatch<uint64_t>(buf, vals, la, lb, split, G, F, gctr, sb, stream);
+        return group_dispatch<uint64_t>(buf, vals, vb, la, lb, split, G, F, gctr, sb, stream);
     case IPM_INT64:
-        return group_dispatch<int64_t>(buf, vals, la, lb, split, G, F, gctr, sb, stream);
+        return group_dispatch<int64_t>(buf, vals, vb, la, lb, split, G, F, gctr, sb, stream);
     case IPM_FLOAT32:
-        return group_dispatch<float>(buf, vals, la, lb, split, G, F, gctr, sb, stream);
+        return group_dispatch<float>(buf, vals, vb, la, lb, split, G, F, gctr, sb, stream);
     }
     return IPM_ERR_UNSUPPORTED_DTYPE;
 }
@@ -641,9 +662,9 @@ ipm_status launch_cluster_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t
 
 namespace ipm {
 
-uint64_t cluster_tile_capacity(ipm_dtype key, bool with_values) {
-    const bool four = key == IPM_INT32 || key == IPM_UINT32 || key == IPM_FLOAT32;
-    return uint64_t((four && !with_values) ? 512 : 256) * 33u;
+uint64_t cluster_tile_capacity(ipm_dtype key, uint32_t vb) {
+    const uint32_t elem = uint32_t(dtype_bytes(key)) + vb;
+    return uint64_t(elem == 4 ? 512 : (elem <= 12 ? 256 : 128)) * 33u;
 }
 
 }  // namespace ipm

@@ -182,20 +182,22 @@ __device__ bool wait_count(const uint32_t *ctr, uint32_t target) {
 // (physical ranges: a mirrored primed range is still contiguous and keeps its order),
 // each staged in one slot (a SHIFT tile, stash chunk or SINGLE exchange spans both).
 
-template <typename K, bool KV>
+// V: the payload type (4- or 8-byte; moved like the keys).
+template <typename K, bool KV, typename V = uint32_t>
 struct XCfg {
     static constexpr int kThreads = 512;
     static constexpr uint32_t kStageBytes = 104u * 1024u;
-    static constexpr uint32_t kElemBytes = uint32_t(sizeof(K)) + (KV ? 4u : 0u);
+    static constexpr uint32_t kElemBytes = uint32_t(sizeof(K)) + (KV ? uint32_t(sizeof(V)) : 0u);
     static constexpr uint32_t kKPad = 16u / uint32_t(sizeof(K));  // phase slack, keys
-    static constexpr uint32_t kVPad = 4u;                         // phase slack, values
+    static constexpr uint32_t kVPad = 16u / uint32_t(sizeof(V));  // phase slack, values
     // elements per slot, a multiple of 32
     static constexpr uint32_t kSlot =
         ((kStageBytes / (2u * kElemBytes)) - (kKPad > kVPad ? kKPad : kVPad) - 16u) / 32u * 32u;
     static constexpr uint32_t kSlotK = kSlot + kKPad;  // key slot stride (elements)
     static constexpr uint32_t kSlotV = kSlot + kVPad;  // value slot stride (elements)
     static constexpr size_t kStageKBytes = (size_t(2) * kSlotK * sizeof(K) + 15) / 16 * 16;
-    static constexpr size_t kStageVBytes = KV ? (size_t(2) * kSlotV * 4 + 15) / 16 * 16 : 0;
+    static constexpr size_t kStageVBytes =
+        KV ? (size_t(2) * kSlotV * sizeof(V) + 15) / 16 * 16 : 0;
     static constexpr size_t kStageSize = kStageKBytes + kStageVBytes;
     static constexpr size_t kSmem = 2 * kStageSize + 64;  // two stages + two mbarriers
     // pair tile = one slot per block; shift tile, stash chunk and SINGLE exchange = two
@@ -400,11 +402,11 @@ __device__ __forceinline__ K *stage_keys(const Item &it, unsigned char *stage,
                                          unsigned char *base) {
     return reinterpret_cast<K *>(it.single ? base : stage);
 }
-template <typename K, bool KV>
-__device__ __forceinline__ uint32_t *stage_vals(const Item &it, unsigned char *stage,
-                                                unsigned char *base) {
-    using C = XCfg<K, KV>;
-    return reinterpret_cast<uint32_t *>(
+template <typename K, bool KV, typename V = uint32_t>
+__device__ __forceinline__ V *stage_vals(const Item &it, unsigned char *stage,
+                                         unsigned char *base) {
+    using C = XCfg<K, KV, V>;
+    return reinterpret_cast<V *>(
         it.single ? base + (size_t(C::kSingleCap + C::kKPad) * sizeof(K) + 15) / 16 * 16
                   : stage + C::kStageKBytes);
 }
@@ -806,13 +808,13 @@ __device__ __forceinline__ void load_line_span(T *slot, const T *g, uint32_t len
                   bytes, full);
 }
 
-template <typename K, bool KV>
-__device__ __forceinline__ void stage_load_ws(const Item &it, const K *buf, const uint32_t *vals,
+template <typename K, bool KV, typename V>
+__device__ __forceinline__ void stage_load_ws(const Item &it, const K *buf, const V *vals,
                                               unsigned char *stage, unsigned char *base,
                                               uint64_t *full) {
-    using C = XCfg<K, KV>;
+    using C = XCfg<K, KV, V>;
     K *sk = stage_keys<K, KV>(it, stage, base);
-    uint32_t *sv = stage_vals<K, KV>(it, stage, base);
+    V *sv = stage_vals<K, KV, V>(it, stage, base);
     if ((threadIdx.x & 31u) != 0) return;
     uint32_t tx = 0;
     for (uint32_t i = 0; i < it.nmoves; ++i) {
@@ -844,13 +846,13 @@ __device__ __forceinline__ void copy_out_ws(const T *src, T *dst, uint32_t len, 
     for (uint32_t j = j0 + ctid; j < len; j += NT) dst[j] = src[j];
 }
 
-template <typename K, bool KV>
-__device__ __forceinline__ void stage_store_ws(const Item &it, K *buf, uint32_t *vals,
+template <typename K, bool KV, typename V>
+__device__ __forceinline__ void stage_store_ws(const Item &it, K *buf, V *vals,
                                                unsigned char *stage, unsigned char *base,
                                                uint32_t ctid) {
-    using C = XCfg<K, KV>;
+    using C = XCfg<K, KV, V>;
     const K *sk = stage_keys<K, KV>(it, stage, base);
-    const uint32_t *sv = stage_vals<K, KV>(it, stage, base);
+    const V *sv = stage_vals<K, KV, V>(it, stage, base);
     if (it.single) {  // the whole exchange [X|Y] is staged; write it rotated by |X|
         const Move &mv = it.mv[0];
         const Geo<int(sizeof(K))> gk(buf + mv.src, uint32_t(mv.len));
@@ -863,9 +865,9 @@ __device__ __forceinline__ void stage_store_ws(const Item &it, K *buf, uint32_t 
             dst[t] = k0[src];
         }
         if (KV) {
-            const Geo<4> gv(vals + mv.src, uint32_t(mv.len));
-            const uint32_t *v0 = sv + gv.off;
-            uint32_t *vd = vals + mv.dst;
+            const Geo<int(sizeof(V))> gv(vals + mv.src, uint32_t(mv.len));
+            const V *v0 = sv + gv.off;
+            V *vd = vals + mv.dst;
             for (uint32_t t = ctid; t < m; t += kWsConsumers) {
                 uint32_t src = t + a;
                 if (src >= m) src -= m;
@@ -880,8 +882,8 @@ __device__ __forceinline__ void stage_store_ws(const Item &it, K *buf, uint32_t 
         const Geo<int(sizeof(K))> gk(buf + mv.src, len);
         copy_out_ws<K>(sk + i * C::kSlotK + gk.off, buf + mv.dst, len, ctid);
         if (KV) {
-            const Geo<4> gv(vals + mv.src, len);
-            copy_out_ws<uint32_t>(sv + i * C::kSlotV + gv.off, vals + mv.dst, len, ctid);
+            const Geo<int(sizeof(V))> gv(vals + mv.src, len);
+            copy_out_ws<V>(sv + i * C::kSlotV + gv.off, vals + mv.dst, len, ctid);
         }
     }
 }
@@ -931,14 +933,14 @@ __device__ bool ws_wait_deps(const uint32_t *flags, uint32_t lo, uint32_t hi, ui
     return true;
 }
 
-template <typename K, bool KV>
+template <typename K, bool KV, typename V>
 __global__ void __launch_bounds__(512, 1)
-    exchange_level_ws_kernel(K *__restrict__ buf, uint32_t *__restrict__ vals, uint64_t n,
+    exchange_level_ws_kernel(K *__restrict__ buf, V *__restrict__ vals, uint64_t n,
                              const RotPlan *__restrict__ plans, const uint32_t *__restrict__ pf,
                              uint32_t nrot, uint32_t *__restrict__ flags,
                              uint32_t *__restrict__ join, uint32_t tag, uint32_t ctr_index,
                              uint32_t holders, StatusBlock *sb) {
-    using C = XCfg<K, KV>;
+    using C = XCfg<K, KV, V>;
     extern __shared__ __align__(128) unsigned char xsmem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(xsmem + 2 * C::kStageSize);
     uint64_t *empty = full + 2;
@@ -1064,7 +1066,7 @@ __global__ void __launch_bounds__(512, 1)
             }
             __syncwarp();
             unsigned char *stage = xsmem + (st ? C::kStageSize : 0);
-            stage_load_ws<K, KV>(it, buf, vals, stage, xsmem, &full[st]);
+            stage_load_ws<K, KV, V>(it, buf, vals, stage, xsmem, &full[st]);
             if (lane == 0 && it.flag) {
                 pend_on[st] = true;
                 pend_par[st] = arrivals[st] & 1u;
@@ -1139,7 +1141,7 @@ __global__ void __launch_bounds__(512, 1)
         consumers_sync();
         if (sh.stop_deps) break;
         unsigned char *stage = xsmem + (st ? C::kStageSize : 0);
-        stage_store_ws<K, KV>(it, buf, vals, stage, xsmem, ctid);
+        stage_store_ws<K, KV, V>(it, buf, vals, stage, xsmem, ctid);
         if (!it.final_phase) __threadfence();  // an LS step: writes visible device-wide
         fence_proxy_async_smem();  // our reads of the stage precede the next bulk copy into it
         consumers_sync();
@@ -1156,11 +1158,20 @@ __global__ void __launch_bounds__(512, 1)
 // per-level holder count; the same on the plan side.
 uint32_t holder_cap() { return uint32_t(num_sms()) / 2u; }
 
-template <typename E, bool KV, bool WS>
-ipm_status exchange_level_t(void *buf, uint32_t *vals, uint64_t n, uint32_t l,
+// WS: the warp-specialized executor; the single-role one moves 4-byte payloads only.
+template <typename E, bool KV, bool WS, typename V = uint32_t>
+ipm_status exchange_level_t(void *buf, void *vals, uint64_t n, uint32_t l,
                             XPlanArea pa, StatusBlock *sb, cudaStream_t stream) {
-    using C = XCfg<E, KV>;
-    auto kern = WS ? exchange_level_ws_kernel<E, KV> : exchange_level_kernel<E, KV>;
+    static_assert(WS || sizeof(V) == 4, "the single-role executor moves 4-byte payloads");
+    using C = XCfg<E, KV, V>;
+    using Kern = void (*)(E *, V *, uint64_t, const RotPlan *, const uint32_t *, uint32_t,
+                          uint32_t *, uint32_t *, uint32_t, uint32_t, uint32_t,
+                          StatusBlock *);
+    Kern kern;
+    if constexpr (WS)
+        kern = exchange_level_ws_kernel<E, KV, V>;
+    else
+        kern = exchange_level_kernel<E, KV>;
     static int grid = 0;
     if (grid == 0) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1180,7 +1191,7 @@ ipm_status exchange_level_t(void *buf, uint32_t *vals, uint64_t n, uint32_t l,
     const uint64_t R = 1ull << l;
     const RotPlan *plans = reinterpret_cast<const RotPlan *>(pa.plans) + (R - 1);
     const uint32_t *pf = pa.item_pf + (R - 1) + l;
-    kern<<<grid, C::kThreads, C::kSmem, stream>>>((E *)buf, vals, n, plans, pf, uint32_t(R),
+    kern<<<grid, C::kThreads, C::kSmem, stream>>>((E *)buf, (V *)vals, n, plans, pf, uint32_t(R),
                                                   pa.flags, pa.join + (R - 1), l + 1,
                                                   kTicketCounter0 + l,
                                                   level_holders(l, holder_cap()), sb);
@@ -1189,23 +1200,30 @@ ipm_status exchange_level_t(void *buf, uint32_t *vals, uint64_t n, uint32_t l,
 
 }  // namespace
 
-XParams exchange_params(ipm_dtype key, bool with_values) {
+template <typename E>
+XParams params_by_payload(uint32_t vb) {
+    return vb == 8   ? XCfg<E, true, uint64_t>::params()
+           : vb != 0 ? XCfg<E, true, uint32_t>::params()
+                     : XCfg<E, false>::params();
+}
+
+XParams exchange_params(ipm_dtype key, uint32_t vb) {
     switch (key) {
     case IPM_INT32:
     case IPM_UINT32:
     case IPM_FLOAT32:
-        return with_values ? XCfg<int32_t, true>::params() : XCfg<int32_t, false>::params();
+        return params_by_payload<int32_t>(vb);
     case IPM_UINT64:
     case IPM_INT64:  // moved, never compared
-        return with_values ? XCfg<uint64_t, true>::params() : XCfg<uint64_t, false>::params();
+        return params_by_payload<uint64_t>(vb);
     }
     return XParams{1, 2, 1, 1, 1};
 }
 
-size_t xplan_area_bytes(uint32_t G, uint64_t n, ipm_dtype key, bool with_values) {
+size_t xplan_area_bytes(uint32_t G, uint64_t n, ipm_dtype key, uint32_t vb) {
     if (G == 0) G = 1;
     const uint64_t P = 1ull << G;
-    const XParams prm = exchange_params(key, with_values);
+    const XParams prm = exchange_params(key, vb);
     size_t b = 0;
     b += align_up(sizeof(RotPlan) * P, 256);                  // plans of all levels
     b += align_up(sizeof(uint32_t) * (P + G + 1), 256);       // item prefixes
@@ -1224,10 +1242,10 @@ uint64_t max_level_items(uint32_t G, uint64_t n, const XParams &prm) {
            R * (kMinHolders + 6) + kMaxHoldersCap + 16;
 }
 
-XPlanArea xplan_area_at(void *base, uint32_t G, uint64_t n, ipm_dtype key, bool with_values) {
+XPlanArea xplan_area_at(void *base, uint32_t G, uint64_t n, ipm_dtype key, uint32_t vb) {
     if (G == 0) G = 1;
     const uint64_t P = 1ull << G;
-    const XParams prm = exchange_params(key, with_values);
+    const XParams prm = exchange_params(key, vb);
     char *p = static_cast<char *>(base);
     XPlanArea pa;
     pa.plans = p;
@@ -1244,15 +1262,15 @@ XPlanArea xplan_area_at(void *base, uint32_t G, uint64_t n, ipm_dtype key, bool 
 }
 
 ipm_status launch_xplan_levels(const uint64_t *split, uint64_t n, uint32_t G,
-                               uint32_t levels, XPlanArea pa, ipm_dtype key, bool with_values,
+                               uint32_t levels, XPlanArea pa, ipm_dtype key, uint32_t vb,
                                StatusBlock *sb, cudaStream_t stream) {
     if (G == 0 || levels == 0) return IPM_OK;
     if (levels > G) levels = G;
     // completion counters and read flags start at zero on every call
     IPM_CUDA_TRY(cudaMemsetAsync(pa.join, 0, pa.zero_bytes, stream));
-    const uint32_t elem = uint32_t(dtype_bytes(key)) + (with_values ? 4u : 0u);
+    const uint32_t elem = uint32_t(dtype_bytes(key)) + vb;
     xplan_levels_kernel<<<levels, kPlanThreads, 0, stream>>>(split, n, G, pa,
-                                                             exchange_params(key, with_values),
+                                                             exchange_params(key, vb),
                                                              holder_cap(), elem, sb);
     return last_launch_status();
 }
@@ -1260,36 +1278,39 @@ ipm_status launch_xplan_levels(const uint64_t *split, uint64_t n, uint32_t G,
 ipm_status launch_xplan_single(uint64_t lx, uint64_t ly, XPlanArea pa, ipm_dtype key,
                                cudaStream_t stream) {
     IPM_CUDA_TRY(cudaMemsetAsync(pa.join, 0, pa.zero_bytes, stream));
-    xplan_single_kernel<<<1, 32, 0, stream>>>(lx, ly, pa, exchange_params(key, false),
+    xplan_single_kernel<<<1, 32, 0, stream>>>(lx, ly, pa, exchange_params(key, 0u),
                                                holder_cap());
     return last_launch_status();
 }
 
 uint32_t g_exchange_engine = 1;
 
-ipm_status launch_exchange_level(void *buf, uint32_t *vals, ipm_dtype key, uint64_t n,
-                                 uint32_t l, XPlanArea pa, StatusBlock *sb,
+ipm_status launch_exchange_level(void *buf, void *vals, uint32_t vb, ipm_dtype key,
+                                 uint64_t n, uint32_t l, XPlanArea pa, StatusBlock *sb,
                                  cudaStream_t stream) {
-    const bool kv = vals != nullptr;
-    const bool ws = g_exchange_engine == 1;
-    switch (key) {
-    case IPM_INT32:
-    case IPM_UINT32:
-    case IPM_FLOAT32:
+    // 8-byte payloads always go through the warp-specialized executor
+    const bool ws = g_exchange_engine == 1 || vb == 8;
+    const bool four = dtype_bytes(key) == 4;
+    if (dtype_bytes(key) == 0) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (vb == 8)
+        return four ? exchange_level_t<int32_t, true, true, uint64_t>(buf, vals, n, l, pa, sb,
+                                                                      stream)
+                    : exchange_level_t<uint64_t, true, true, uint64_t>(buf, vals, n, l, pa, sb,
+                                                                       stream);
+    const bool kv = vb != 0;
+    if (four) {
         if (ws)
             return kv ? exchange_level_t<int32_t, true, true>(buf, vals, n, l, pa, sb, stream)
                       : exchange_level_t<int32_t, false, true>(buf, vals, n, l, pa, sb, stream);
         return kv ? exchange_level_t<int32_t, true, false>(buf, vals, n, l, pa, sb, stream)
                   : exchange_level_t<int32_t, false, false>(buf, vals, n, l, pa, sb, stream);
-    case IPM_UINT64:
-    case IPM_INT64:  // moved, never compared
-        if (ws)
-            return kv ? exchange_level_t<uint64_t, true, true>(buf, vals, n, l, pa, sb, stream)
-                      : exchange_level_t<uint64_t, false, true>(buf, vals, n, l, pa, sb, stream);
-        return kv ? exchange_level_t<uint64_t, true, false>(buf, vals, n, l, pa, sb, stream)
-                  : exchange_level_t<uint64_t, false, false>(buf, vals, n, l, pa, sb, stream);
     }
-    return IPM_ERR_UNSUPPORTED_DTYPE;
+    // 8-byte keys (uint64, int64): moved, never compared
+    if (ws)
+        return kv ? exchange_level_t<uint64_t, true, true>(buf, vals, n, l, pa, sb, stream)
+                  : exchange_level_t<uint64_t, false, true>(buf, vals, n, l, pa, sb, stream);
+    return kv ? exchange_level_t<uint64_t, true, false>(buf, vals, n, l, pa, sb, stream)
+              : exchange_level_t<uint64_t, false, false>(buf, vals, n, l, pa, sb, stream);
 }
 
 }  // namespace ipm

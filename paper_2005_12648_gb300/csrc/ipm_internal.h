@@ -16,13 +16,14 @@ struct XPlanArea {
 };
 
 struct XParams;
-XParams exchange_params(ipm_dtype key, bool with_values);
+// vb: payload bytes per element (0: keys only, 4, 8); payloads are moved, never compared.
+XParams exchange_params(ipm_dtype key, uint32_t vb);
 uint64_t max_level_items(uint32_t G, uint64_t n, const XParams &prm);
-size_t xplan_area_bytes(uint32_t G, uint64_t n, ipm_dtype key, bool with_values);
-XPlanArea xplan_area_at(void *base, uint32_t G, uint64_t n, ipm_dtype key, bool with_values);
+size_t xplan_area_bytes(uint32_t G, uint64_t n, ipm_dtype key, uint32_t vb);
+XPlanArea xplan_area_at(void *base, uint32_t G, uint64_t n, ipm_dtype key, uint32_t vb);
 
 // Tile (pair) capacity of the shared-memory merge, in elements.
-uint64_t tile_capacity(ipm_dtype key, bool with_values);
+uint64_t tile_capacity(ipm_dtype key, uint32_t vb);
 
 // ---- launchers (all asynchronous on `stream`; return IPM_ERR_CUDA on launch failure)
 
@@ -39,7 +40,7 @@ ipm_status launch_splits(const void *buf, uint64_t la, uint64_t lb, ipm_dtype ke
 // Plans (and zeroed flags) of the first `levels` of the G levels of a split table with
 // P = 2^G; only the planned levels add to the status block's exchange bytes.
 ipm_status launch_xplan_levels(const uint64_t *split, uint64_t n, uint32_t G,
-                               uint32_t levels, XPlanArea pa, ipm_dtype key, bool with_values,
+                               uint32_t levels, XPlanArea pa, ipm_dtype key, uint32_t vb,
                                StatusBlock *sb, cudaStream_t stream);
 
 // Plan of a single exchange [X|Y] at offset 0 (level 0 of a G = 1 layout).
@@ -51,26 +52,27 @@ ipm_status launch_xplan_single(uint64_t lx, uint64_t ly, XPlanArea pa, ipm_dtype
 extern uint32_t g_exchange_engine;
 
 // The exchanges of level l, one persistent launch.
-ipm_status launch_exchange_level(void *buf, uint32_t *vals, ipm_dtype key, uint64_t n,
-                                 uint32_t l, XPlanArea pa, StatusBlock *sb,
+ipm_status launch_exchange_level(void *buf, void *vals, uint32_t vb, ipm_dtype key,
+                                 uint64_t n, uint32_t l, XPlanArea pa, StatusBlock *sb,
                                  cudaStream_t stream);
 
 // The last log2_cluster levels fused with the pair merge (ipm_cluster_merge.cu): run
 // after levels 0 .. G - log2_cluster - 1; clusters of 2^log2_cluster CTAs.
+// (4-byte payloads only: vals is NULL or uint32_t *.)
 ipm_status launch_cluster_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
                                 ipm_dtype key, const uint64_t *split, uint32_t G,
                                 uint32_t log2_cluster, StatusBlock *sb, cudaStream_t stream);
 // The largest F <= wanted whose clusters of 2^F CTAs the device can schedule (0: none).
 uint32_t usable_fused_levels(ipm_dtype key, bool with_values, uint32_t wanted);
-// Pair capacity of the fused kernel's tile (half the plain merge's tile).
-uint64_t cluster_tile_capacity(ipm_dtype key, bool with_values);
+// Pair capacity of the fused kernels' tile (half the plain merge's tile).
+uint64_t cluster_tile_capacity(ipm_dtype key, uint32_t vb);
 // The same fusion with a group barrier in global memory: groups of 2^F pairs taken from
 // a ticket (gctr: (2^G >> F) uint32 group counters in the workspace, zeroed here).
-ipm_status launch_group_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
+ipm_status launch_group_merge(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t lb,
                               ipm_dtype key, const uint64_t *split, uint32_t G, uint32_t F,
                               uint32_t *gctr, StatusBlock *sb, cudaStream_t stream);
 // The largest F <= wanted with at least 2^F resident CTAs of the group kernel.
-uint32_t usable_group_levels(ipm_dtype key, bool with_values, uint32_t wanted);
+uint32_t usable_group_levels(ipm_dtype key, uint32_t vb, uint32_t wanted);
 
 // Division of Alg. 3 to 2^depth pairs (ipm_division.cu): the pair boundaries only.
 ipm_status launch_division(const void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
@@ -89,7 +91,7 @@ ipm_status launch_cs_rotate(void *ptr, uint32_t elem_bytes, const CsPlan &pl, vo
                             cudaStream_t stream);
 
 // Per-pair shared-memory merge of an arranged buffer.
-ipm_status launch_tile_merge(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
+ipm_status launch_tile_merge(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t lb,
                              ipm_dtype key, const uint64_t *split, uint32_t G,
                              StatusBlock *sb, cudaStream_t stream);
 

@@ -17,12 +17,15 @@
 
 namespace ipm {
 
-template <typename K, bool KV, int THREADS, int E>
+// V: the payload type (4- or 8-byte; moved, never compared).
+template <typename K, bool KV, int THREADS, int E, typename V = uint32_t>
 struct TileShape {
     static constexpr int kTile = THREADS * E;
     static constexpr int kKeyPad = 16 / int(sizeof(K));
+    static constexpr int kValPad = 16 / int(sizeof(V));
     static constexpr size_t kKeyBytes = ((size_t(kTile + kKeyPad) * sizeof(K)) + 15) / 16 * 16;
-    static constexpr size_t kValBytes = KV ? ((size_t(kTile + 4) * 4 + 15) / 16 * 16) : 0;
+    static constexpr size_t kValBytes =
+        KV ? ((size_t(kTile + kValPad) * sizeof(V) + 15) / 16 * 16) : 0;
     static constexpr size_t kSmem = 128 + kKeyBytes + kValBytes;
 };
 
@@ -36,10 +39,11 @@ enum : int { kPairAbort = 0, kPairMerged = 1, kPairInOrder = 2, kPairTrivial = 3
 // and, after a barrier, writes them to dk[0, a + b) (dv for payloads), which may overlap
 // the sources (EC odd keeps the blocked writes conflict-free across banks).  Both runs
 // are addressed from one base so the merge loop keeps a single pointer.
-template <typename K, bool KV, int THREADS, int EC, bool MAY_BE_EMPTY = false>
-__device__ __forceinline__ void merge_two(const K *sk, const uint32_t *sv, uint32_t a,
+template <typename K, bool KV, int THREADS, int EC, bool MAY_BE_EMPTY = false,
+          typename V = uint32_t>
+__device__ __forceinline__ void merge_two(const K *sk, const V *sv, uint32_t a,
                                           uint32_t bo, uint32_t bov, uint32_t b, K *dk,
-                                          uint32_t *dv) {
+                                          V *dv) {
     const uint32_t tid = threadIdx.x;
     const uint32_t c = a + b;
     const uint32_t dt = tid * uint32_t(EC);
@@ -90,7 +94,7 @@ __device__ __forceinline__ void merge_two(const K *sk, const uint32_t *sv, uint3
             vb2 = takeA ? vb2 : nv;
         }
     }
-    uint32_t ov[KV ? EC : 1];
+    V ov[KV ? EC : 1];
     if (KV && dt < c) {
 #pragma unroll
         for (int e = 0; e < EC; ++e) {
@@ -114,8 +118,8 @@ __device__ __forceinline__ void merge_two(const K *sk, const uint32_t *sv, uint3
 // Step 2 of merge_pair_smem: the staged pair tk[0, c) = [A (a) | B (c - a)] merged onto
 // itself (a, c - a >= 1) by the whole CTA with EC outputs per thread, the same
 // algorithm as merge_two for the contiguous layout (A and B as two pointers).
-template <typename K, bool KV, int THREADS, int EC>
-__device__ __forceinline__ void merge_staged(K *tk, uint32_t *tv, uint32_t a, uint32_t c) {
+template <typename K, bool KV, int THREADS, int EC, typename V = uint32_t>
+__device__ __forceinline__ void merge_staged(K *tk, V *tv, uint32_t a, uint32_t c) {
     const uint32_t tid = threadIdx.x;
     const uint32_t b = c - a;
     const K *sA = tk;
@@ -159,7 +163,7 @@ __device__ __forceinline__ void merge_staged(K *tk, uint32_t *tv, uint32_t a, ui
             vb2 = takeA ? vb2 : nv;
         }
     }
-    uint32_t ov[KV ? EC : 1];
+    V ov[KV ? EC : 1];
     if (KV && dt < c) {
 #pragma unroll
         for (int e = 0; e < EC; ++e) {
@@ -190,23 +194,23 @@ __device__ __forceinline__ void merge_staged(K *tk, uint32_t *tv, uint32_t a, ui
 //                 to IPM_ERR_TIMEOUT); the pair is left untouched.
 // On return the shared buffers are free again (the bulk store has finished reading
 // them).
-template <typename K, bool KV, int THREADS, int E>
-__device__ __forceinline__ int merge_pair_smem(K *g, uint32_t *gv, uint32_t a, uint32_t c,
-                                               K *skeys, uint32_t *svals, uint64_t *mbar,
+template <typename K, bool KV, int THREADS, int E, typename V = uint32_t>
+__device__ __forceinline__ int merge_pair_smem(K *g, V *gv, uint32_t a, uint32_t c,
+                                               K *skeys, V *svals, uint64_t *mbar,
                                                uint32_t &parity, int &abort_flag,
                                                StatusBlock *sb) {
     const uint32_t tid = threadIdx.x;
     const uint32_t b = c - a;
     if (a == 0 || b == 0) return kPairTrivial;
     const Geo<int(sizeof(K))> gk(g, c);
-    const Geo<4> gvv(KV ? (const void *)gv : (const void *)g, KV ? c : 0u);
-    K *tk = skeys + gk.off;          // staged keys: tk[0, c)
-    uint32_t *tv = svals + gvv.off;  // staged values: tv[0, c)
+    const Geo<int(sizeof(V))> gvv(KV ? (const void *)gv : (const void *)g, KV ? c : 0u);
+    K *tk = skeys + gk.off;   // staged keys: tk[0, c)
+    V *tv = svals + gvv.off;  // staged values: tv[0, c)
 
     // ---- 1. stage
     if (tid == 0) {
         const uint32_t kb = gk.body * uint32_t(sizeof(K));
-        const uint32_t vb = KV ? gvv.body * 4u : 0u;
+        const uint32_t vb = KV ? gvv.body * uint32_t(sizeof(V)) : 0u;
         mbar_arrive_expect_tx(mbar, kb + vb);
         if (kb) bulk_load(tk + gk.head, g + gk.head, kb, mbar);
         if (KV && vb) bulk_load(tv + gvv.head, gv + gvv.head, vb, mbar);
@@ -230,14 +234,14 @@ __device__ __forceinline__ int merge_pair_smem(K *g, uint32_t *gv, uint32_t a, u
     }
 
     // ---- 2. merge in shared memory
-    merge_staged<K, KV, THREADS, E>(tk, tv, a, c);
+    merge_staged<K, KV, THREADS, E, V>(tk, tv, a, c);
 
     // ---- 3. store the merged copy
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
         const uint32_t kb = gk.body * uint32_t(sizeof(K));
-        const uint32_t vb = KV ? gvv.body * 4u : 0u;
+        const uint32_t vb = KV ? gvv.body * uint32_t(sizeof(V)) : 0u;
         if (kb) bulk_store(g + gk.head, tk + gk.head, kb);
         if (KV && vb) bulk_store(gv + gvv.head, tv + gvv.head, vb);
         bulk_commit();

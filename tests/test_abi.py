@@ -86,8 +86,12 @@ def test_argument_errors_return_before_any_cuda_call(lib):
     assert L.ipm_merge_inplace(0x1000, 10, 10, 0, 0, 4096, 16, null) == 4
     # pairs that cannot fit one tile
     assert L.ipm_merge_inplace(0x1000, 1 << 28, 1 << 28, 0, 1, 4096, 1 << 30, null) == 1
-    # key-value needs a uint32 payload
-    assert L.ipm_merge_inplace_kv(0x1000, 0x2000, 4, 4, 0, 3, 0, 4096, 1 << 20, null) == 2
+    # key-value: the payload type is only a width (4 or 8 bytes); an unknown type code
+    # is rejected, and so is a payload pointer not aligned to its width
+    assert L.ipm_merge_inplace_kv(0x1000, 0x2000, 4, 4, 0, 9, 0, 4096, 1 << 20, null) == 2
+    assert L.ipm_merge_inplace_kv(0x1000, 0x2004, 4, 4, 0, 2, 0, 4096, 1 << 20, null) == 3
+    # with_values: 0, 1, 4 or 8
+    assert L.ipm_merge_workspace_bytes(100, 100, 0, 3, 0, ctypes.byref(ctypes.c_size_t())) == 2
     # splits: zero pairs
     assert L.ipm_merge_splits(0x1000, 4, 4, 0, 0, 0x2000, null) == 1
     # rotate: bad element size

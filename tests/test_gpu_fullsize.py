@@ -53,3 +53,23 @@ def test_kv_zipf_2p26_plus_2p26(ipm, dev, orc):
                           np.arange(la, la + lb, dtype=np.uint32))
     assert first_diff(from_dev(keys, np.uint32), wk) is None
     assert np.array_equal(from_dev(vals, np.uint32), wv)
+
+
+def test_int64_2p28_plus_2p28(ipm, dev, orc):
+    _run(ipm, dev, orc, "uniform", np.int64, 1 << 28, 1 << 28)
+
+
+def test_kv8_uint64_2p27_plus_2p27(ipm, dev, orc):
+    """uint64 keys with uint64 payloads (payload = original index, high bits set)."""
+    import torch
+
+    la = lb = 1 << 27
+    keys = W.make_buffer_torch(torch, "uniform", np.uint64, la, lb, 0, dev)
+    host = W.as_numpy_keys(keys, np.uint64)
+    pay = np.arange(la + lb, dtype=np.uint64) | np.uint64(0xABCD000000000000)
+    vals = torch.from_numpy(pay.view(np.int64).copy()).to(dev)
+    ipm.merge_inplace_kv(keys, vals, la, lb, "uint64", val_dtype="uint64")
+    torch.cuda.synchronize()
+    wk, wv = orc.merge_kvw(host[:la], pay[:la], host[la:], pay[la:])
+    assert first_diff(from_dev(keys, np.uint64), wk) is None
+    assert np.array_equal(vals.cpu().numpy().view(np.uint64), wv)

@@ -171,6 +171,58 @@ def test_merge_inplace_kv_stable(ipm, dev, orc, dt):
         assert np.array_equal(from_dev(vals, np.uint32), wv)
 
 
+@pytest.mark.parametrize("dt", DTYPES)
+@pytest.mark.parametrize("dist", ["zipf", "uniform", "dup16"])
+def test_merge_inplace_kv8_matches_oracle(ipm, dev, orc, dt, dist):
+    """8-byte payloads (every bit pattern: index in the high word, a hash in the low
+    word) move with their keys exactly as the oracle's wide-payload merge moves them."""
+    import torch
+
+    if dist == "zipf" and dt == np.float32:
+        dist = "dup16"
+    _, tile = ipm.ipm_merge_plan(1, 1, NAME[np.dtype(dt)], with_values=8)
+    for la, lb in [(1, 1), (0, 9), (9, 0), (tile // 3, tile // 2), (3 * tile + 5, 2 * tile + 1),
+                   (5 * tile + 3, 7 * tile + 11), (4 * tile, 17)]:
+        a, b = W.make_pair(dist, dt, la, lb, seed=la + 5 * lb)
+        n = la + lb
+        idx = np.arange(n, dtype=np.uint64)
+        pay = (idx << np.uint64(32)) | ((idx * np.uint64(2654435761)) & np.uint64(0xFFFFFFFF))
+        pay[::7] |= np.uint64(1 << 63)
+        keys = to_dev(np.concatenate([a, b]), dev)
+        vals = torch.from_numpy(pay.view(np.int64).copy()).to(dev)
+        ipm.merge_inplace_kv(keys, vals, la, lb, NAME[np.dtype(dt)], val_dtype="uint64")
+        torch.cuda.synchronize()
+        wk, wv = orc.merge_kvw(a, pay[:la], b, pay[la:])
+        assert first_diff(from_dev(keys, dt), wk) is None, (la, lb)
+        assert np.array_equal(vals.cpu().numpy().view(np.uint64), wv), (la, lb)
+
+
+@pytest.mark.parametrize("engine,fused", [(1, 0), (1, 2), (1, 5), (1, 8), (0, 4)])
+@pytest.mark.parametrize("dt", [np.uint32, np.int64])
+def test_kv8_fused_levels_match_oracle(ipm, dev, orc, engine, fused, dt):
+    """8-byte payloads through every fused-level setting (the cluster engine hands
+    8-byte payloads to the group barrier)."""
+    import torch
+
+    la, lb = 700_001, 655_357
+    a, b = W.make_pair("uniform", dt, la, lb, seed=3)
+    pay = np.arange(la + lb, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)
+    try:
+        ipm.ipm_set_fused_engine(engine)
+        ipm.ipm_set_fused_levels(fused)
+        keys = to_dev(np.concatenate([a, b]), dev)
+        vals = torch.from_numpy(pay.view(np.int64).copy()).to(dev)
+        ws = ipm.merge_inplace_kv(keys, vals, la, lb, NAME[np.dtype(dt)], val_dtype="uint64")
+        torch.cuda.synchronize()
+        assert ipm.ipm_read_device_status(ws) == 0
+    finally:
+        ipm.ipm_set_fused_engine(1)
+        ipm.ipm_set_fused_levels(8)
+    wk, wv = orc.merge_kvw(a, pay[:la], b, pay[la:])
+    assert first_diff(from_dev(keys, dt), wk) is None
+    assert np.array_equal(vals.cpu().numpy().view(np.uint64), wv)
+
+
 def test_async_on_a_side_stream(ipm, dev, orc):
     import torch
 
