@@ -817,6 +817,8 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
         "config": {"workload": args.workload, "description": desc,
                    "form": "key-value" if kv else "plain",
                    "log2_pairs": G, "tile_capacity": tile,
+                   "fused": dict(zip(("engine", "levels"),
+                                     ipm.ipm_merge_fused_plan(la, lb, dt, vbytes))),
                    "l2": "inputs larger than L2 (%.1f GiB buffer)" % (n * w / 2**30)
                    if n * w > (129 << 20) else "L2-resident input (no flush)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -221,7 +221,8 @@ ipm_status ipm_read_exchange_bytes(const void *d_ws, ipm_stream_t stream, uint64
 
 /*
  * How many of the last levels of the division stage the merge entry points fuse with
- * the pair merge (process-wide, default 8).  With F fused levels the exchange levels
+ * the pair merge (process-wide, default 10: as many as the engine can, 8 or 9 on a
+ * 152-SM GB300).  With F fused levels the exchange levels
  * stop F levels short, and each group of 2^F consecutive pairs is finished by 2^F CTAs
  * together: the group's region holds exactly those pairs' A and B slices, so each CTA
  * stages its pair's two slices, the group synchronises once the whole group has been
@@ -234,8 +235,19 @@ ipm_status ipm_read_exchange_bytes(const void *d_ws, ipm_stream_t stream, uint64
  *
  * ipm_set_fused_engine selects how a group synchronises: 0 = one thread-block cluster
  * per group (cluster barrier; F <= 4), 1 = CTAs taken from a ticket in order and a
- * group barrier in global memory (the default).
+ * group barrier in global memory, 2 = the same with two pairs per CTA, the first
+ * merged pair parked in tensor memory (TMEM) until the group barrier, which fuses one
+ * level more (the default; it takes 4-byte keys without payload, other inputs use
+ * engine 1).  ipm_merge_fused_plan reports what a merge will use.
  */
+/*
+ * The fused engine (0, 1, 2 as above; 0xFFFFFFFF when no level is fused) and the number
+ * of fused levels ipm_merge_inplace / _kv would use for these sizes, key type and payload
+ * width (with_values as for ipm_merge_plan) under the current settings and device.
+ * Either output may be NULL.  Host only (queries the device's occupancy once).
+ */
+ipm_status ipm_merge_fused_plan(uint64_t len_a, uint64_t len_b, ipm_dtype key_dtype,
+                                int with_values, uint32_t *engine, uint32_t *levels);
 ipm_status ipm_set_fused_levels(uint32_t levels);
 ipm_status ipm_get_fused_levels(uint32_t *levels);
 ipm_status ipm_set_fused_engine(uint32_t engine);

@@ -36,7 +36,7 @@ __all__ = [
     "ipm_split_model_loss_grad", "ipm_merge_splits_learned", "ipm_merge_inplace_learned",
     "split_model_initial_params", "split_model_to_device", "split_model_from_device",
     "train_split_model", "ipm_set_fused_levels", "ipm_get_fused_levels",
-    "ipm_set_exchange_engine", "ipm_set_fused_engine",
+    "ipm_set_exchange_engine", "ipm_set_fused_engine", "ipm_merge_fused_plan",
 ]
 
 DTYPES = {"int32": 0, "uint32": 1, "uint64": 2, "float32": 3, "int64": 4}
@@ -91,6 +91,7 @@ _SIGS = {
     "ipm_merge_inplace_learned": (_i, [_vp, _u64, _u64, _i, _u32, _vp, _vp, _sz, _vp]),
     "ipm_set_fused_levels": (_i, [_u32]),
     "ipm_get_fused_levels": (_i, [ctypes.POINTER(_u32)]),
+    "ipm_merge_fused_plan": (_i, [_u64, _u64, _i, _i, ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
     "ipm_set_exchange_engine": (_i, [_u32]),
     "ipm_set_fused_engine": (_i, [_u32]),
 }
@@ -476,6 +477,15 @@ def ipm_set_exchange_engine(engine: int) -> None:
 
 def ipm_set_fused_engine(engine: int) -> None:
     _check(load().ipm_set_fused_engine(engine), "ipm_set_fused_engine")
+
+
+def ipm_merge_fused_plan(len_a: int, len_b: int, key_dtype, with_values=False):
+    """(engine, fused levels) a merge of these sizes would use (engine None: none)."""
+    e, f = _u32(0), _u32(0)
+    _check(load().ipm_merge_fused_plan(len_a, len_b, _dt(key_dtype), _payload(with_values),
+                                       ctypes.byref(e), ctypes.byref(f)),
+           "ipm_merge_fused_plan")
+    return (None if e.value == 0xFFFFFFFF else int(e.value)), int(f.value)
 
 
 def ipm_get_fused_levels() -> int:

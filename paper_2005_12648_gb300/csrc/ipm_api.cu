@@ -88,8 +88,8 @@ constexpr uint32_t kMaxLog2Pairs = 22;
 // Bottom levels of the division stage fused with the pair merge (ipm_set_fused_levels)
 // and how the groups synchronise: 0 = thread-block clusters (F <= 4), 1 = group
 // barriers in global memory (ipm_set_fused_engine).
-uint32_t g_fused_levels = 8;
-uint32_t g_fused_engine = 1;
+uint32_t g_fused_levels = 10;  // as many as the engine can (8 or 9 on GB300)
+uint32_t g_fused_engine = 2;  // TMEM two-pairs kernel where it applies, else 1
 
 bool valid_key(ipm_dtype t) {
     return t == IPM_INT32 || t == IPM_UINT32 || t == IPM_UINT64 || t == IPM_FLOAT32 ||
@@ -158,6 +158,24 @@ uint32_t payload_bytes(int with_values) {
     return with_values == 8 ? 8u : 1u;
 }
 
+// The fused engine and level count a merge with 2^G plain pairs uses: the selected
+// engine where it applies (the cluster kernels move 4-byte payloads, so 8-byte ones take
+// the group barrier; the two-pairs TMEM kernel takes 4-byte keys without payload, the
+// rest the group barrier), and the most levels it can fuse up to the setting.
+struct FusedChoice {
+    uint32_t engine, levels;
+};
+FusedChoice fused_choice(ipm_dtype key, uint32_t vb, uint32_t G) {
+    const uint32_t Fwant = g_fused_levels < G + 1 ? g_fused_levels : G + 1;
+    if (g_fused_engine == 0 && vb != 8)
+        return {0u, usable_fused_levels(key, vb != 0, Fwant > 4 ? 4 : Fwant)};
+    if (g_fused_engine == 2) {
+        const uint32_t f2 = usable_group2_levels(key, vb, Fwant);
+        if (f2 > 0) return {2u, f2};
+    }
+    return {1u, usable_group_levels(key, vb, Fwant)};
+}
+
 ipm_status merge_core(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t lb,
                       ipm_dtype key, uint32_t log2_pairs, void *ws, size_t ws_bytes,
                       cudaStream_t stream, const ipm_split_model *model = nullptr) {
@@ -173,11 +191,9 @@ ipm_status merge_core(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t 
     // The fused path (the last F levels done by groups of CTAs with half-size tiles:
     // thread-block clusters for F <= 4 when selected, else global-memory group
     // barriers) splits one level deeper: every pair then fits the half tile.
-    const uint32_t Fwant = g_fused_levels < G + 1 ? g_fused_levels : G + 1;
-    // (the cluster kernels move 4-byte payloads; 8-byte ones take the group barrier)
-    const bool use_clusters = g_fused_engine == 0 && vb != 8;
-    const uint32_t F = use_clusters ? usable_fused_levels(key, vb != 0, Fwant > 4 ? 4 : Fwant)
-                                    : usable_group_levels(key, vb, Fwant);
+    const FusedChoice fc = fused_choice(key, vb, G);
+    const bool use_clusters = fc.engine == 0, use_tmem = fc.engine == 2;
+    const uint32_t F = fc.levels;
     const uint32_t Gs = F > 0 ? G + 1 : G;  // depth of the split table
     const MergeLayout L = merge_layout(Gs, n, key, vb);
     if (ws_bytes < L.total) return IPM_ERR_WORKSPACE;
@@ -214,6 +230,9 @@ ipm_status merge_core(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t 
     if (F > 0 && use_clusters)
         return launch_cluster_merge(buf, static_cast<uint32_t *>(vals), la, lb, key, split, Gs,
                                     F, sb, stream);
+    if (F > 0 && use_tmem)
+        return launch_group2_merge(buf, la, lb, key, split, Gs, F,
+                                   reinterpret_cast<uint32_t *>(w + L.group_off), sb, stream);
     if (F > 0)
         return launch_group_merge(buf, vals, vb, la, lb, key, split, Gs, F,
                                   reinterpret_cast<uint32_t *>(w + L.group_off), sb, stream);
@@ -573,8 +592,19 @@ ipm_status ipm_merge_inplace_learned(void *d_buf, uint64_t len_a, uint64_t len_b
                       (cudaStream_t)stream, d_model);
 }
 
+ipm_status ipm_merge_fused_plan(uint64_t len_a, uint64_t len_b, ipm_dtype key_dtype,
+                                int with_values, uint32_t *engine, uint32_t *levels) {
+    uint32_t G = 0;
+    const uint32_t vb = payload_bytes(with_values);
+    IPM_TRY(check_merge_args(len_a, len_b, key_dtype, vb, 0, &G));
+    const FusedChoice fc = fused_choice(key_dtype, vb, G);
+    if (engine) *engine = fc.levels > 0 ? fc.engine : 0xFFFFFFFFu;
+    if (levels) *levels = fc.levels;
+    return IPM_OK;
+}
+
 ipm_status ipm_set_fused_engine(uint32_t engine) {
-    if (engine > 1) return IPM_ERR_INVALID_ARG;
+    if (engine > 2) return IPM_ERR_INVALID_ARG;
     g_fused_engine = engine;
     return IPM_OK;
 }

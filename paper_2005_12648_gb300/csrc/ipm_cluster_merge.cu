@@ -13,6 +13,7 @@
 // disappear.  Pairs with an empty run are moved too (their data still changes place).
 #include "ipm_internal.h"
 #include "ipm_tile_merge.cuh"
+#include "ipm_tmem.cuh"
 
 namespace ipm {
 
@@ -242,17 +243,18 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
 
 // Claim the next pair (thread 0): its ticket and, when it is a pair, its geometry
 // within its group's region.  Returns the ticket.
+// The geometry of pair k within its group of 2^F pairs (the group's region holds A's
+// slices of the group, then B's): where its two slices are, where its output goes, and
+// their phases in the staging buffer.
 template <typename K, bool KV, uint32_t TILE, typename V>
-__device__ __forceinline__ uint32_t group_claim(PairGeo<K, V> &pg, K *buf, V *vals,
-                                                uint64_t la, uint64_t lb,
-                                                const uint64_t *__restrict__ split,
-                                                uint32_t G, uint32_t F, StatusBlock *sb) {
+__device__ __forceinline__ void pair_geometry(PairGeo<K, V> &pg, K *buf, V *vals, uint64_t la,
+                                              uint64_t lb, const uint64_t *__restrict__ split,
+                                              uint32_t G, uint32_t F, uint64_t k,
+                                              StatusBlock *sb) {
     constexpr uint32_t VK = 16u / uint32_t(sizeof(K));
     constexpr uint32_t VV = 16u / uint32_t(sizeof(V));
-    const uint32_t t = atomicAdd(&sb->counters[kGroupTicket], 1u);
-    if (uint64_t(t) >= (1ull << G)) return t;
     const uint64_t n = la + lb;
-    const uint64_t k = t, k0 = (k >> F) << F, k1 = k0 + (1ull << F);
+    const uint64_t k0 = (k >> F) << F, k1 = k0 + (1ull << F);
     const uint64_t dlo = (k0 * n) >> G, dhi = (k1 * n) >> G;
     const uint64_t ilo = split[k0], ihi = split[k1];
     const uint64_t d0 = (k * n) >> G, d1 = ((k + 1) * n) >> G;
@@ -288,6 +290,16 @@ __device__ __forceinline__ uint32_t group_claim(PairGeo<K, V> &pg, K *buf, V *va
         pg.offAV = offAV;
         pg.offBV = offAV + a + ((phase_of(vB) + VV - (offAV + a) % VV) % VV);
     }
+}
+
+template <typename K, bool KV, uint32_t TILE, typename V>
+__device__ __forceinline__ uint32_t group_claim(PairGeo<K, V> &pg, K *buf, V *vals,
+                                                uint64_t la, uint64_t lb,
+                                                const uint64_t *__restrict__ split,
+                                                uint32_t G, uint32_t F, StatusBlock *sb) {
+    const uint32_t t = atomicAdd(&sb->counters[kGroupTicket], 1u);
+    if (uint64_t(t) < (1ull << G))
+        pair_geometry<K, KV, TILE, V>(pg, buf, vals, la, lb, split, G, F, t, sb);
     return t;
 }
 
@@ -394,6 +406,191 @@ __global__ void __launch_bounds__(THREADS, 2)
     if (tid == 0) bulk_wait_all0();
 }
 
+// ---------------------------------------------------------------------------------
+// The group barrier with two pairs per CTA (4-byte keys, no payload): the first pair is
+// merged on chip and its output parked in tensor memory (TMEM, 256 columns of the
+// SM's 512 per CTA), then the second is staged and merged in shared memory, so a CTA
+// holds two merged pairs and a group of 2^F pairs needs 2^(F-1) resident CTAs: one
+// more level is fused than with one pair per CTA.  After the group barrier the second
+// pair is stored from shared memory and the first brought back from TMEM (each thread
+// its own lane and columns) and stored the same way.  Tickets cover pairs 2t and 2t+1
+// (one group: groups are aligned to 2^F >= 2 pairs); the ticket-order argument of the
+// one-pair kernel holds with 2^(F-1) claims per group.  Exactly two CTAs fit an SM
+// (shared memory is padded to kGroup2Smem), so the two allocations never wait.
+// ---------------------------------------------------------------------------------
+constexpr uint32_t kGroup2Cols = 256;
+// more than a third of the SM's 228 KB (no third CTA fits), less than half with each
+// CTA's static and reserved bytes (two fit the carveout)
+constexpr size_t kGroup2Smem = 78u << 10;
+
+template <typename K, int THREADS, int E>
+__global__ void __launch_bounds__(THREADS, 2)
+    group2_merge_kernel(K *__restrict__ buf, uint64_t la, uint64_t lb,
+                        const uint64_t *__restrict__ split, uint32_t G, uint32_t F,
+                        uint32_t *__restrict__ gctr, StatusBlock *sb) {
+    static_assert(sizeof(K) == 4 && E == 33 && THREADS % 128 == 0, "4-byte keys, 33 per thread");
+    // a warp's 33 columns start at a multiple of 64 (the 32-column access aligned to 32)
+    static_assert((THREADS / 128) * 64 <= int(kGroup2Cols), "a thread's outputs fit its columns");
+    using Shape = ClusterShape<K, false, THREADS, E>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);
+    K *R = reinterpret_cast<K *>(smem_raw + 128);
+    __shared__ int abort_flag;
+    __shared__ uint32_t s_t[2], s_taddr;
+    __shared__ PairGeo<K> pgs[2][2];  // [current / next claim][first / second pair]
+    if (sb == nullptr || *((volatile unsigned int *)&sb->done)) return;
+    const uint32_t tid = threadIdx.x, warp = tid >> 5;
+    const uint64_t claims = (1ull << G) >> 1;
+    const uint32_t gsize = 1u << (F - 1);  // claims per group
+    if (warp == 0) {
+        tmem_alloc<kGroup2Cols>(&s_taddr);
+        tmem_relinquish();
+    }
+    auto claim = [&](uint32_t q) {  // thread 0
+        const uint32_t t = atomicAdd(&sb->counters[kGroupTicket], 1u);
+        s_t[q] = t;
+        if (uint64_t(t) < claims) {
+            pair_geometry<K, false, Shape::kTile, uint32_t>(pgs[q][0], buf, nullptr, la, lb,
+                                                            split, G, F, 2ull * t, sb);
+            pair_geometry<K, false, Shape::kTile, uint32_t>(pgs[q][1], buf, nullptr, la, lb,
+                                                            split, G, F, 2ull * t + 1, sb);
+        }
+    };
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        mbar_fence_init();
+        abort_flag = 0;
+        claim(0);
+    }
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    // this thread's TMEM cells: its warp's lane quarter, columns 64 (warp / 4) + 0..32
+    // (recomputed from shared memory where used, so it is not live across the merge)
+    auto tcol = [&]() {
+        return tmem_warp_addr(*((volatile uint32_t *)&s_taddr), (warp >> 2) * 64u);
+    };
+    uint32_t parity = 0, cur = 0;
+
+    // stage one pair's two slices (bodies by bulk copy, heads / tails by plain loads)
+    auto stage = [&](volatile PairGeo<K> &vg) {
+        const uint32_t a = vg.a, b = vg.b;
+        if (a + b == 0) return;
+        if (tid == 0)
+            mbar_arrive_expect_tx(mbar, body_bytes(const_cast<K *>(vg.gA), a) +
+                                            body_bytes(const_cast<K *>(vg.gB), b));
+        stage_range<K, THREADS>(R + vg.offA, vg.gA, a, mbar);
+        stage_range<K, THREADS>(R + vg.offB, vg.gB, b, mbar);
+        if (!mbar_wait_bounded(mbar, parity)) atomicOr(&abort_flag, 1);
+        parity ^= 1u;
+    };
+
+    for (;;) {
+        if (uint64_t(*((volatile uint32_t *)&s_t[cur])) >= claims) break;
+        volatile PairGeo<K> &g0 = pgs[cur][0];
+        volatile PairGeo<K> &g1 = pgs[cur][1];
+
+        // ---- first pair: stage, merge into registers, park in TMEM
+        stage(g0);
+        __syncthreads();  // every thread's head / tail loads have landed too
+        {
+            K ok[E] = {};  // outputs past the pair's end are parked but never read back
+            uint32_t oi[1];
+            if (!abort_flag)
+                merge_path_regs<K, false, THREADS, E, true>(R + g0.offA, g0.a, g0.offB - g0.offA,
+                                                            g0.b, ok, oi);
+            uint32_t w[32];
+#pragma unroll
+            for (int e = 0; e < 32; ++e) memcpy(&w[e], &ok[e], 4);
+            uint32_t w32;
+            memcpy(&w32, &ok[32], 4);
+            const uint32_t ta = tcol();
+            tmem_st32(ta, w);
+            tmem_st1(ta + 32u, w32);
+            tmem_wait_st();
+        }
+        __syncthreads();  // the staging buffer is read: free for the second pair
+
+        // ---- second pair: stage, count in, merge on chip into the output's phase
+        stage(g1);
+        __syncthreads();
+        if (tid == 0)  // both pairs' slices have been read
+            atomicAdd(gctr + (*((volatile uint32_t *)&s_t[cur]) >> (F - 1)), 1u);
+        if (!abort_flag && g1.a + g1.b > 0)
+            merge_two<K, false, THREADS, E, true, uint32_t>(R + g1.offA, nullptr, g1.a,
+                                                            g1.offB - g1.offA, 0u, g1.b,
+                                                            R + g1.oo, nullptr);
+        fence_proxy_async_smem();
+
+        // ---- group barrier: the group's region may be written once every member has
+        // its slices on chip
+        if (tid == 0 && !abort_flag) {
+            const uint32_t *ctr = gctr + (*((volatile uint32_t *)&s_t[cur]) >> (F - 1));
+            unsigned long long t0 = 0;
+            uint32_t it = 0;
+            while (ld_acquire_u32(ctr) < gsize) {
+                if ((++it & 63u) == 0) {
+                    const unsigned long long now = globaltimer_ns();
+                    if (t0 == 0)
+                        t0 = now;
+                    else if (now - t0 > kWaitLimitNs) {
+                        abort_flag = 1;
+                        break;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (abort_flag) {
+            if (tid == 0) set_status(sb, IPM_ERR_TIMEOUT);
+            break;
+        }
+
+        // ---- store the second pair, then bring the first back from TMEM and store it
+        const uint32_t c1 = g1.a + g1.b;
+        if (c1 > 0) store_range<K, THREADS>(const_cast<K *>(g1.gO), R + g1.oo, c1);
+        if (tid == 0) {
+            bulk_commit();
+            bulk_wait_read0();
+        }
+        fence_proxy_async_smem();
+        __syncthreads();  // the staging buffer is free again
+        const uint32_t c0 = g0.a + g0.b;
+        {
+            uint32_t w[32];
+            const uint32_t ta = tcol();
+            tmem_ld32(ta, w);
+            const uint32_t w32 = tmem_ld1(ta + 32u);
+            tmem_wait_ld();
+            const uint32_t dt = tid * uint32_t(E);
+            K *out = R + g0.oo;
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+                if (dt + e < c0) memcpy(&out[dt + e], &w[e], 4);
+            if (dt + 32 < c0) memcpy(&out[dt + 32], &w32, 4);
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (c0 > 0) store_range<K, THREADS>(const_cast<K *>(g0.gO), R + g0.oo, c0);
+        if (tid == 0) {
+            bulk_commit();
+            claim(cur ^ 1u);  // the next claim, while the bulk store reads shared memory
+            bulk_wait_read0();
+        }
+        fence_proxy_async_smem();
+        tmem_fence_before_sync();
+        __syncthreads();
+        tmem_fence_after_sync();
+        cur ^= 1u;
+    }
+    if (tid == 0) bulk_wait_all0();
+    // every TMEM access of the CTA has completed (the waits above): free the columns
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if (warp == 0) tmem_dealloc<kGroup2Cols>(s_taddr);
+}
+
 template <typename K, bool KV, int THREADS, int E, typename V>
 int group_grid() {
     using Shape = ClusterShape<K, KV, THREADS, E, V>;
@@ -427,6 +624,56 @@ ipm_status group_merge_t(void *buf, void *vals, uint64_t la, uint64_t lb,
     const unsigned g = unsigned(P < uint64_t(grid) ? P : uint64_t(grid));
     group_merge_kernel<K, KV, THREADS, E, V><<<g, THREADS, Shape::kSmem, stream>>>(
         (K *)buf, (V *)vals, la, lb, split, G, F, gctr, sb);
+    return last_launch_status();
+}
+
+// Resident CTAs of the two-pairs kernel (0 unless exactly two fit an SM: each CTA
+// holds half of the SM's TMEM), computed once from its registers, shared memory and
+// threads against the SM's limits.  (The occupancy query answers one CTA per SM for any
+// kernel that allocates TMEM, whatever it allocates; two such CTAs do run side by side.)
+template <typename K>
+int group2_grid() {
+    auto kern = group2_merge_kernel<K, 512, 33>;
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    cached = 0;
+    int dev = 0, regs_sm = 0, smem_sm = 0, threads_sm = 0, reserved = 0;
+    cudaFuncAttributes fa;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(kGroup2Smem)) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             int(cudaSharedmemCarveoutMaxShared)) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+            cudaSuccess) {
+        (void)cudaGetLastError();
+        return cached;
+    }
+    const long regs_cta = long(fa.numRegs) * 512;
+    const long smem_cta = long(kGroup2Smem) + long(fa.sharedSizeBytes) + long(reserved);
+    long per_sm = threads_sm / 512;
+    if (regs_cta > 0 && regs_sm / regs_cta < per_sm) per_sm = regs_sm / regs_cta;
+    if (smem_sm / smem_cta < per_sm) per_sm = smem_sm / smem_cta;
+    cached = per_sm == 2 ? 2 * num_sms() : 0;
+    return cached;
+}
+
+template <typename K>
+ipm_status group2_merge_t(void *buf, uint64_t la, uint64_t lb, const uint64_t *split,
+                          uint32_t G, uint32_t F, uint32_t *gctr, StatusBlock *sb,
+                          cudaStream_t stream) {
+    const int grid = group2_grid<K>();
+    if (F < 1 || grid < (1 << (F - 1))) return IPM_ERR_CUDA;
+    const uint64_t claims = (1ull << G) >> 1;
+    const unsigned g = unsigned(claims < uint64_t(grid) ? claims : uint64_t(grid));
+    group2_merge_kernel<K, 512, 33><<<g, 512, kGroup2Smem, stream>>>((K *)buf, la, lb, split, G,
+                                                                     F, gctr, sb);
     return last_launch_status();
 }
 
@@ -625,6 +872,29 @@ ipm_status launch_group_merge(void *buf, void *vals, uint32_t vb, uint64_t la, u
         return group_dispatch<float>(buf, vals, vb, la, lb, split, G, F, gctr, sb, stream);
     }
     return IPM_ERR_UNSUPPORTED_DTYPE;
+}
+
+uint32_t usable_group2_levels(ipm_dtype key, uint32_t vb, uint32_t wanted) {
+    if (vb != 0 || dtype_bytes(key) != 4) return 0;
+    const int grid = key == IPM_FLOAT32 ? group2_grid<float>()
+                     : key == IPM_UINT32 ? group2_grid<uint32_t>()
+                                         : group2_grid<int32_t>();
+    if (grid == 0 || wanted == 0) return 0;
+    uint32_t f = wanted;
+    while (f > 1 && (1 << (f - 1)) > grid) --f;  // a group's claims must fit the residents
+    return f;
+}
+
+ipm_status launch_group2_merge(void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
+                               const uint64_t *split, uint32_t G, uint32_t F, uint32_t *gctr,
+                               StatusBlock *sb, cudaStream_t stream) {
+    IPM_CUDA_TRY(cudaMemsetAsync(gctr, 0, sizeof(uint32_t) * size_t((1ull << G) >> F), stream));
+    switch (key) {
+    case IPM_INT32: return group2_merge_t<int32_t>(buf, la, lb, split, G, F, gctr, sb, stream);
+    case IPM_UINT32: return group2_merge_t<uint32_t>(buf, la, lb, split, G, F, gctr, sb, stream);
+    case IPM_FLOAT32: return group2_merge_t<float>(buf, la, lb, split, G, F, gctr, sb, stream);
+    default: return IPM_ERR_UNSUPPORTED_DTYPE;
+    }
 }
 
 uint32_t usable_fused_levels(ipm_dtype key, bool with_values, uint32_t wanted) {

@@ -74,6 +74,14 @@ ipm_status launch_group_merge(void *buf, void *vals, uint32_t vb, uint64_t la, u
 // The largest F <= wanted with at least 2^F resident CTAs of the group kernel.
 uint32_t usable_group_levels(ipm_dtype key, uint32_t vb, uint32_t wanted);
 
+// The group barrier with two pairs per CTA, the first merged pair parked in TMEM
+// (4-byte keys without payload): groups of 2^F pairs need 2^(F-1) resident CTAs.
+ipm_status launch_group2_merge(void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
+                               const uint64_t *split, uint32_t G, uint32_t F, uint32_t *gctr,
+                               StatusBlock *sb, cudaStream_t stream);
+// The largest F <= wanted the two-pairs kernel can run (0: not for this key / payload).
+uint32_t usable_group2_levels(ipm_dtype key, uint32_t vb, uint32_t wanted);
+
 // Division of Alg. 3 to 2^depth pairs (ipm_division.cu): the pair boundaries only.
 ipm_status launch_division(const void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
                            uint32_t depth, uint32_t kind, uint64_t *ia, uint64_t *jb,

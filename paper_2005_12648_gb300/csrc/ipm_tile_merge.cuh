@@ -39,16 +39,14 @@ enum : int { kPairAbort = 0, kPairMerged = 1, kPairInOrder = 2, kPairTrivial = 3
 // and, after a barrier, writes them to dk[0, a + b) (dv for payloads), which may overlap
 // the sources (EC odd keeps the blocked writes conflict-free across banks).  Both runs
 // are addressed from one base so the merge loop keeps a single pointer.
-template <typename K, bool KV, int THREADS, int EC, bool MAY_BE_EMPTY = false,
-          typename V = uint32_t>
-__device__ __forceinline__ void merge_two(const K *sk, const V *sv, uint32_t a,
-                                          uint32_t bo, uint32_t bov, uint32_t b, K *dk,
-                                          V *dv) {
-    const uint32_t tid = threadIdx.x;
+// The merge-path part of merge_two for one thread: its EC outputs starting at output
+// position tid * EC, into registers: the keys (ok) and, for KV, the staged index of
+// each output (oi: A's at < a, B's at >= bo).  Threads past the end leave them unset.
+template <typename K, bool KV, int THREADS, int EC, bool MAY_BE_EMPTY = false>
+__device__ __forceinline__ void merge_path_regs(const K *sk, uint32_t a, uint32_t bo, uint32_t b,
+                                                K (&ok)[EC], uint32_t (&oi)[KV ? EC : 1]) {
     const uint32_t c = a + b;
-    const uint32_t dt = tid * uint32_t(EC);
-    K ok[EC];
-    uint32_t oi[KV ? EC : 1];
+    const uint32_t dt = threadIdx.x * uint32_t(EC);
     if (dt < c) {
         uint32_t lo = dt > b ? dt - b : 0u;
         uint32_t hi = dt < a ? dt : a;
@@ -94,6 +92,18 @@ __device__ __forceinline__ void merge_two(const K *sk, const V *sv, uint32_t a,
             vb2 = takeA ? vb2 : nv;
         }
     }
+}
+
+template <typename K, bool KV, int THREADS, int EC, bool MAY_BE_EMPTY = false,
+          typename V = uint32_t>
+__device__ __forceinline__ void merge_two(const K *sk, const V *sv, uint32_t a,
+                                          uint32_t bo, uint32_t bov, uint32_t b, K *dk,
+                                          V *dv) {
+    const uint32_t c = a + b;
+    const uint32_t dt = threadIdx.x * uint32_t(EC);
+    K ok[EC];
+    uint32_t oi[KV ? EC : 1];
+    merge_path_regs<K, KV, THREADS, EC, MAY_BE_EMPTY>(sk, a, bo, b, ok, oi);
     V ov[KV ? EC : 1];
     if (KV && dt < c) {
 #pragma unroll

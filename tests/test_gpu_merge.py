@@ -216,8 +216,8 @@ def test_kv8_fused_levels_match_oracle(ipm, dev, orc, engine, fused, dt):
         torch.cuda.synchronize()
         assert ipm.ipm_read_device_status(ws) == 0
     finally:
-        ipm.ipm_set_fused_engine(1)
-        ipm.ipm_set_fused_levels(8)
+        ipm.ipm_set_fused_engine(2)
+        ipm.ipm_set_fused_levels(10)
     wk, wv = orc.merge_kvw(a, pay[:la], b, pay[la:])
     assert first_diff(from_dev(keys, dt), wk) is None
     assert np.array_equal(vals.cpu().numpy().view(np.uint64), wv)
@@ -237,7 +237,8 @@ def test_async_on_a_side_stream(ipm, dev, orc):
 
 
 @pytest.mark.parametrize("engine,fused", [(0, 0), (0, 1), (0, 2), (0, 3), (0, 4), (1, 1),
-                                          (1, 3), (1, 5), (1, 6), (1, 7), (1, 8), (1, 10)])
+                                          (1, 3), (1, 5), (1, 6), (1, 7), (1, 8), (1, 10),
+                                          (2, 1), (2, 2), (2, 5), (2, 8), (2, 9), (2, 10)])
 @pytest.mark.parametrize("dt", [np.int32, np.uint64, np.int64])
 def test_fused_bottom_levels_match_oracle(ipm, dev, orc, engine, fused, dt):
     """The last `fused` levels done by groups of CTAs (each group stages its pairs, then
@@ -261,8 +262,24 @@ def test_fused_bottom_levels_match_oracle(ipm, dev, orc, engine, fused, dt):
             want = orc.merge(a, b)
             assert first_diff(got, want) is None, (la, lb, dist, G, first_diff(got, want))
     finally:
-        ipm.ipm_set_fused_levels(8)
+        ipm.ipm_set_fused_levels(10)
+        ipm.ipm_set_fused_engine(2)
+
+
+def test_default_fused_plan_uses_tensor_memory(ipm):
+    """By default 4-byte keys without payload take the two-pairs kernel that parks a
+    merged pair in TMEM, fusing one level more than one pair per CTA; key-value and
+    8-byte keys take the one-pair group barrier."""
+    n = 1 << 28
+    e2, f2 = ipm.ipm_merge_fused_plan(n, n, "int32")
+    try:
         ipm.ipm_set_fused_engine(1)
+        e1, f1 = ipm.ipm_merge_fused_plan(n, n, "int32")
+    finally:
+        ipm.ipm_set_fused_engine(2)
+    assert (e1, e2) == (1, 2) and f2 == f1 + 1
+    assert ipm.ipm_merge_fused_plan(n, n, "int32", with_values=4)[0] == 1
+    assert ipm.ipm_merge_fused_plan(n, n, "uint64")[0] == 1
 
 
 @pytest.mark.parametrize("engine", [0, 1])
@@ -294,7 +311,7 @@ def test_exchange_engines_match_oracle(ipm, dev, orc, engine):
                 a, b = W.make_pair(dist, dt, la, lb, seed=la)
                 got = _merge_dev(ipm, dev, a, b)
                 assert first_diff(got, orc.merge(a, b)) is None, (dist, la, lb, fused)
-        ipm.ipm_set_fused_levels(8)
+        ipm.ipm_set_fused_levels(10)
         ka, kb = W.make_pair("zipf", np.uint32, 2_000_003, 1_700_001, seed=3)
         keys = to_dev(np.concatenate([ka, kb]), dev)
         vals = torch.arange(ka.size + kb.size, dtype=torch.int32, device=dev)
@@ -308,7 +325,7 @@ def test_exchange_engines_match_oracle(ipm, dev, orc, engine):
         assert np.array_equal(vals.cpu().numpy().view(np.uint32), wv)
     finally:
         ipm.ipm_set_exchange_engine(1)
-        ipm.ipm_set_fused_levels(8)
+        ipm.ipm_set_fused_levels(10)
 
 
 @pytest.mark.parametrize("engine", [0, 1])
