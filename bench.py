@@ -681,17 +681,21 @@ def run_e2e_batched(torch, ipm, workloads, m, steps, stream, dev):
     offs = np.concatenate([[0], np.cumsum(la + lb)[:-1]]).astype(np.int64)
     segs = ipm.segment_table(offs, la, lb, dev)
     n = pristine.numel()
-    ws = ipm.workspace(ipm.ipm_merge_batched_workspace_bytes(n, la.size, "int32"), dev)
-    return run_e2e(torch, [pristine], steps, stream,
-                   lambda d: ipm.ipm_merge_batched(d[0], None, n, segs, la.size, "int32", ws))
+    wss = [ipm.workspace(ipm.ipm_merge_batched_workspace_bytes(n, la.size, "int32"), dev)
+           for _ in range(2)]
+    return run_e2e(torch, [pristine], steps,
+                   lambda d, k, st: ipm.ipm_merge_batched(d[0], None, n, segs, la.size, "int32",
+                                                          wss[k], stream=st))
 
 
 def run_e2e_learned(torch, ipm, m, steps, stream, model):
     pristine = m["pristine"]
     la = lb = pristine.numel() // 2
-    ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, "float32"), pristine.device)
-    return run_e2e(torch, [pristine], steps, stream,
-                   lambda d: ipm.ipm_merge_inplace_learned(d[0], la, lb, "float32", model, ws))
+    wss = [ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, "float32"), pristine.device)
+           for _ in range(2)]
+    return run_e2e(torch, [pristine], steps,
+                   lambda d, k, st: ipm.ipm_merge_inplace_learned(d[0], la, lb, "float32", model,
+                                                                  wss[k], stream=st))
 
 
 def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
@@ -715,11 +719,12 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
 
     mb = method_bytes(n, w)
 
-    def merge(kb, vb=None):
+    def merge(kb, vb=None, w=None, stream=None):
+        w = ws if w is None else w
         if kv:
-            ipm.ipm_merge_inplace_kv(kb, vb, la, lb, dt, ws, val_dtype=vdt)
+            ipm.ipm_merge_inplace_kv(kb, vb, la, lb, dt, w, val_dtype=vdt, stream=stream)
         else:
-            ipm.ipm_merge_inplace(kb, la, lb, dt, ws)
+            ipm.ipm_merge_inplace(kb, la, lb, dt, w, stream=stream)
 
     def restore():
         buf.copy_(pristine)
@@ -797,8 +802,9 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(torch, [pristine, vpristine] if kv else [pristine], args.steps, stream,
-                      lambda d: merge(*d))
+        ws2 = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, dt, with_values=vbytes), dev)
+        e2e = run_e2e(torch, [pristine, vpristine] if kv else [pristine], args.steps,
+                      lambda d, k, st: merge(d[0], d[1] if kv else None, (ws, ws2)[k], st))
     del buf, pristine, vbuf, vpristine
 
     if rank != 0:
@@ -843,28 +849,51 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
     }
 
 
-def run_e2e(torch, pristines, steps, stream, merge):
-    """The merge through the public API with host buffers: H2D of the inputs (keys, and
-    payloads for key-value) from pinned memory, merge(device buffers), D2H of the
-    results into pinned memory, all timed."""
+def run_e2e(torch, pristines, steps, merge):
+    """The merge through the public API with host buffers, as a caller merging a stream
+    of inputs runs it: every step copies its input (keys, and payloads for key-value)
+    from pinned host memory, merges it and copies the result back to pinned host memory;
+    consecutive steps alternate between two streams, each with its own device buffers
+    and workspace (merge(device buffers, slot, stream)), so one step's copy back overlaps
+    the next step's copy in (the link carries both directions at once).  Timed from
+    before the first copy in to after the last copy back."""
     host_in = [p.cpu().pin_memory() for p in pristines]
-    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
-    dbuf = [torch.empty_like(p) for p in pristines]
+    host_out = [[torch.empty_like(h).pin_memory() for h in host_in] for _ in range(2)]
+    dbuf = [[torch.empty_like(p) for p in pristines] for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    merged = [torch.cuda.Event(), torch.cuda.Event()]
 
-    def call():
-        for d, h in zip(dbuf, host_in):
-            d.copy_(h, non_blocking=True)
-        merge(dbuf)
-        for h, d in zip(host_out, dbuf):
-            h.copy_(d, non_blocking=True)
+    def step(k):
+        st = streams[k % 2]
+        with torch.cuda.stream(st):
+            for d, h in zip(dbuf[k % 2], host_in):
+                d.copy_(h, non_blocking=True)
+            # merges never overlap each other (their persistent kernels each take the
+            # whole GPU); only the copies overlap
+            if k > 0:
+                st.wait_event(merged[(k - 1) % 2])
+            merge(dbuf[k % 2], k % 2, st)
+            merged[k % 2].record(st)
+            for h, d in zip(host_out[k % 2], dbuf[k % 2]):
+                h.copy_(d, non_blocking=True)
 
-    for _ in range(2):
-        call()
+    for k in range(2):
+        step(k)
     torch.cuda.synchronize()
-    ms = sum(timed_steps(torch, stream, steps, lambda: None, call)) / steps
+    start, mid, end = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    start.record(streams[0])
+    streams[1].wait_event(start)
+    for k in range(steps):
+        step(k)
+    mid.record(streams[1])
+    streams[0].wait_event(mid)
+    end.record(streams[0])
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end) / steps
     nbytes = sum(p.numel() * p.element_size() for p in pristines)
     return {"value": pristines[0].numel() / (ms * 1e-3) / 1e9, "unit": UNIT,
-            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": ms}
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": ms,
+            "pipelined": "steps alternate between two streams (copy in / copy back overlap)"}
 
 
 def main():

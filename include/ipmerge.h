@@ -17,6 +17,10 @@
  *     library never allocates or frees device memory; every call that needs scratch
  *     takes a caller-owned workspace sized by the matching *_workspace_bytes query.
  *   - Lengths and offsets count elements, not bytes.
+ *   - Calls are asynchronous on their stream.  Merge calls must not run concurrently with
+ *     each other on different streams: their persistent kernels size their grids to the
+ *     whole GPU and their group barriers need their own CTAs resident (order such calls
+ *     with events; copies may overlap them).
  *   - Keys are compared with the key type's own "<=": signed for IPM_INT32 /
  *     IPM_INT64, unsigned for IPM_UINT32 / IPM_UINT64, IEEE for IPM_FLOAT32 (NaN keys
  *     are not allowed;
