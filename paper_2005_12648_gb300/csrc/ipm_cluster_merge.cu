@@ -52,6 +52,14 @@ struct ClusterShape {
     static constexpr size_t kSmem = 128 + kKeyBytes + kValBytes;
 };
 
+// Half the plain merge's tile: 4-byte keys alone 512 x 33; up to 12 bytes per element
+// 256 x 33; 16 bytes (8-byte keys with an 8-byte payload) 128 x 33.
+template <typename K, bool KV, typename V = uint32_t>
+struct ClusterTileOf {
+    static constexpr int kElem = int(sizeof(K)) + (KV ? int(sizeof(V)) : 0);
+    static constexpr int T = kElem == 4 ? 512 : (kElem <= 12 ? 256 : 128), E = 33;
+};
+
 // Element phase of an address within its 16-byte line.
 template <typename T>
 __device__ __forceinline__ uint32_t phase_of(const T *p) {
@@ -407,7 +415,7 @@ __global__ void __launch_bounds__(THREADS, 2)
 }
 
 // ---------------------------------------------------------------------------------
-// The group barrier with two pairs per CTA (4-byte keys, no payload): the first pair is
+// The group barrier with two pairs per CTA (keys without payload): the first pair is
 // merged on chip and its output parked in tensor memory (TMEM, 256 columns of the
 // SM's 512 per CTA), then the second is staged and merged in shared memory, so a CTA
 // holds two merged pairs and a group of 2^F pairs needs 2^(F-1) resident CTAs: one
@@ -428,9 +436,13 @@ __global__ void __launch_bounds__(THREADS, 2)
     group2_merge_kernel(K *__restrict__ buf, uint64_t la, uint64_t lb,
                         const uint64_t *__restrict__ split, uint32_t G, uint32_t F,
                         uint32_t *__restrict__ gctr, StatusBlock *sb) {
-    static_assert(sizeof(K) == 4 && E == 33 && THREADS % 128 == 0, "4-byte keys, 33 per thread");
-    // a warp's 33 columns start at a multiple of 64 (the 32-column access aligned to 32)
-    static_assert((THREADS / 128) * 64 <= int(kGroup2Cols), "a thread's outputs fit its columns");
+    // a thread parks its E keys as W 32-bit words in W consecutive columns of its lane;
+    // the warps sharing a lane quarter take column blocks of CS (W rounded up to 64, so
+    // every 32-column access starts at a multiple of 32)
+    constexpr int W = E * int(sizeof(K)) / 4;
+    constexpr uint32_t CS = uint32_t((W + 63) / 64 * 64);
+    static_assert(E % 2 == 1 && THREADS % 128 == 0 && sizeof(K) % 4 == 0, "shape");
+    static_assert((THREADS / 128) * CS <= kGroup2Cols, "a thread's outputs fit its columns");
     using Shape = ClusterShape<K, false, THREADS, E>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);
@@ -465,10 +477,10 @@ __global__ void __launch_bounds__(THREADS, 2)
     tmem_fence_before_sync();
     __syncthreads();
     tmem_fence_after_sync();
-    // this thread's TMEM cells: its warp's lane quarter, columns 64 (warp / 4) + 0..32
+    // this thread's TMEM cells: its warp's lane quarter, columns CS (warp / 4) + 0..W-1
     // (recomputed from shared memory where used, so it is not live across the merge)
     auto tcol = [&]() {
-        return tmem_warp_addr(*((volatile uint32_t *)&s_taddr), (warp >> 2) * 64u);
+        return tmem_warp_addr(*((volatile uint32_t *)&s_taddr), (warp >> 2) * CS);
     };
     uint32_t parity = 0, cur = 0;
 
@@ -499,14 +511,14 @@ __global__ void __launch_bounds__(THREADS, 2)
             if (!abort_flag)
                 merge_path_regs<K, false, THREADS, E, true>(R + g0.offA, g0.a, g0.offB - g0.offA,
                                                             g0.b, ok, oi);
-            uint32_t w[32];
-#pragma unroll
-            for (int e = 0; e < 32; ++e) memcpy(&w[e], &ok[e], 4);
-            uint32_t w32;
-            memcpy(&w32, &ok[32], 4);
+            uint32_t w[W];
+            memcpy(w, ok, sizeof(w));
             const uint32_t ta = tcol();
-            tmem_st32(ta, w);
-            tmem_st1(ta + 32u, w32);
+#pragma unroll
+            for (int c = 0; c + 32 <= W; c += 32)
+                tmem_st32(ta + uint32_t(c), *reinterpret_cast<const uint32_t(*)[32]>(w + c));
+#pragma unroll
+            for (int c = W / 32 * 32; c < W; ++c) tmem_st1(ta + uint32_t(c), w[c]);
             tmem_wait_st();
         }
         __syncthreads();  // the staging buffer is read: free for the second pair
@@ -557,17 +569,21 @@ __global__ void __launch_bounds__(THREADS, 2)
         __syncthreads();  // the staging buffer is free again
         const uint32_t c0 = g0.a + g0.b;
         {
-            uint32_t w[32];
+            uint32_t w[W];
             const uint32_t ta = tcol();
-            tmem_ld32(ta, w);
-            const uint32_t w32 = tmem_ld1(ta + 32u);
+#pragma unroll
+            for (int c = 0; c + 32 <= W; c += 32)
+                tmem_ld32(ta + uint32_t(c), *reinterpret_cast<uint32_t(*)[32]>(w + c));
+#pragma unroll
+            for (int c = W / 32 * 32; c < W; ++c) w[c] = tmem_ld1(ta + uint32_t(c));
             tmem_wait_ld();
+            K ok[E];
+            memcpy(ok, w, sizeof(ok));
             const uint32_t dt = tid * uint32_t(E);
             K *out = R + g0.oo;
 #pragma unroll
-            for (int e = 0; e < 32; ++e)
-                if (dt + e < c0) memcpy(&out[dt + e], &w[e], 4);
-            if (dt + 32 < c0) memcpy(&out[dt + 32], &w32, 4);
+            for (int e = 0; e < E; ++e)
+                if (dt + e < c0) out[dt + e] = ok[e];
         }
         fence_proxy_async_smem();
         __syncthreads();
@@ -633,7 +649,8 @@ ipm_status group_merge_t(void *buf, void *vals, uint64_t la, uint64_t lb,
 // kernel that allocates TMEM, whatever it allocates; two such CTAs do run side by side.)
 template <typename K>
 int group2_grid() {
-    auto kern = group2_merge_kernel<K, 512, 33>;
+    constexpr int T = ClusterTileOf<K, false>::T;
+    auto kern = group2_merge_kernel<K, T, 33>;
     static int cached = -1;
     if (cached >= 0) return cached;
     cached = 0;
@@ -655,9 +672,9 @@ int group2_grid() {
         (void)cudaGetLastError();
         return cached;
     }
-    const long regs_cta = long(fa.numRegs) * 512;
+    const long regs_cta = long(fa.numRegs) * T;
     const long smem_cta = long(kGroup2Smem) + long(fa.sharedSizeBytes) + long(reserved);
-    long per_sm = threads_sm / 512;
+    long per_sm = threads_sm / T;
     if (regs_cta > 0 && regs_sm / regs_cta < per_sm) per_sm = regs_sm / regs_cta;
     if (smem_sm / smem_cta < per_sm) per_sm = smem_sm / smem_cta;
     cached = per_sm == 2 ? 2 * num_sms() : 0;
@@ -672,8 +689,9 @@ ipm_status group2_merge_t(void *buf, uint64_t la, uint64_t lb, const uint64_t *s
     if (F < 1 || grid < (1 << (F - 1))) return IPM_ERR_CUDA;
     const uint64_t claims = (1ull << G) >> 1;
     const unsigned g = unsigned(claims < uint64_t(grid) ? claims : uint64_t(grid));
-    group2_merge_kernel<K, 512, 33><<<g, 512, kGroup2Smem, stream>>>((K *)buf, la, lb, split, G,
-                                                                     F, gctr, sb);
+    constexpr int T = ClusterTileOf<K, false>::T;
+    group2_merge_kernel<K, T, 33><<<g, T, kGroup2Smem, stream>>>((K *)buf, la, lb, split, G, F,
+                                                               gctr, sb);
     return last_launch_status();
 }
 
@@ -743,13 +761,6 @@ ipm_status cluster_merge_t(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
 // Half the plain merge's tile (two CTAs per SM, so one CTA's merge overlaps the
 // other's staging): 4-byte keys 512 x 33, 8-byte keys and key-value 256 x 33.  The
 // caller splits one level deeper so that every pair fits.
-// Half the plain merge's tile: 4-byte keys alone 512 x 33; up to 12 bytes per element
-// 256 x 33; 16 bytes (8-byte keys with an 8-byte payload) 128 x 33.
-template <typename K, bool KV, typename V = uint32_t>
-struct ClusterTileOf {
-    static constexpr int kElem = int(sizeof(K)) + (KV ? int(sizeof(V)) : 0);
-    static constexpr int T = kElem == 4 ? 512 : (kElem <= 12 ? 256 : 128), E = 33;
-};
 
 template <typename K, int C>
 ipm_status cluster_dispatch(void *buf, uint32_t *vals, uint64_t la, uint64_t lb,
@@ -875,10 +886,15 @@ ipm_status launch_group_merge(void *buf, void *vals, uint32_t vb, uint64_t la, u
 }
 
 uint32_t usable_group2_levels(ipm_dtype key, uint32_t vb, uint32_t wanted) {
-    if (vb != 0 || dtype_bytes(key) != 4) return 0;
-    const int grid = key == IPM_FLOAT32 ? group2_grid<float>()
-                     : key == IPM_UINT32 ? group2_grid<uint32_t>()
-                                         : group2_grid<int32_t>();
+    if (vb != 0) return 0;
+    int grid = 0;
+    switch (key) {
+    case IPM_INT32: grid = group2_grid<int32_t>(); break;
+    case IPM_UINT32: grid = group2_grid<uint32_t>(); break;
+    case IPM_FLOAT32: grid = group2_grid<float>(); break;
+    case IPM_UINT64: grid = group2_grid<uint64_t>(); break;
+    case IPM_INT64: grid = group2_grid<int64_t>(); break;
+    }
     if (grid == 0 || wanted == 0) return 0;
     uint32_t f = wanted;
     while (f > 1 && (1 << (f - 1)) > grid) --f;  // a group's claims must fit the residents
@@ -893,6 +909,8 @@ ipm_status launch_group2_merge(void *buf, uint64_t la, uint64_t lb, ipm_dtype ke
     case IPM_INT32: return group2_merge_t<int32_t>(buf, la, lb, split, G, F, gctr, sb, stream);
     case IPM_UINT32: return group2_merge_t<uint32_t>(buf, la, lb, split, G, F, gctr, sb, stream);
     case IPM_FLOAT32: return group2_merge_t<float>(buf, la, lb, split, G, F, gctr, sb, stream);
+    case IPM_UINT64: return group2_merge_t<uint64_t>(buf, la, lb, split, G, F, gctr, sb, stream);
+    case IPM_INT64: return group2_merge_t<int64_t>(buf, la, lb, split, G, F, gctr, sb, stream);
     default: return IPM_ERR_UNSUPPORTED_DTYPE;
     }
 }

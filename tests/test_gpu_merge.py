@@ -267,9 +267,9 @@ def test_fused_bottom_levels_match_oracle(ipm, dev, orc, engine, fused, dt):
 
 
 def test_default_fused_plan_uses_tensor_memory(ipm):
-    """By default 4-byte keys without payload take the two-pairs kernel that parks a
-    merged pair in TMEM, fusing one level more than one pair per CTA; key-value and
-    8-byte keys take the one-pair group barrier."""
+    """By default keys without payload take the two-pairs kernel that parks a merged pair
+    in TMEM, fusing one level more than one pair per CTA; key-value merges take the
+    one-pair group barrier."""
     n = 1 << 28
     e2, f2 = ipm.ipm_merge_fused_plan(n, n, "int32")
     try:
@@ -279,7 +279,9 @@ def test_default_fused_plan_uses_tensor_memory(ipm):
         ipm.ipm_set_fused_engine(2)
     assert (e1, e2) == (1, 2) and f2 == f1 + 1
     assert ipm.ipm_merge_fused_plan(n, n, "int32", with_values=4)[0] == 1
-    assert ipm.ipm_merge_fused_plan(n, n, "uint64")[0] == 1
+    assert ipm.ipm_merge_fused_plan(n, n, "uint64", with_values=8)[0] == 1
+    for dt in ("uint64", "int64", "float32", "uint32"):
+        assert ipm.ipm_merge_fused_plan(n, n, dt) == (2, f2), dt
 
 
 @pytest.mark.parametrize("engine", [0, 1])
