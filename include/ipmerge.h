@@ -241,8 +241,8 @@ ipm_status ipm_read_exchange_bytes(const void *d_ws, ipm_stream_t stream, uint64
  * per group (cluster barrier; F <= 4), 1 = CTAs taken from a ticket in order and a
  * group barrier in global memory, 2 = the same with two pairs per CTA, the first
  * merged pair parked in tensor memory (TMEM) until the group barrier, which fuses one
- * level more (the default; it takes keys without payload, key-value merges use engine
- * 1).  ipm_merge_fused_plan reports what a merge will use.
+ * level more (the default, for every key type with or without payload).
+ * ipm_merge_fused_plan reports what a merge will use.
  */
 /*
  * The fused engine (0, 1, 2 as above; 0xFFFFFFFF when no level is fused) and the number

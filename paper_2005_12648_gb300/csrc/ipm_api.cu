@@ -160,8 +160,9 @@ uint32_t payload_bytes(int with_values) {
 
 // The fused engine and level count a merge with 2^G plain pairs uses: the selected
 // engine where it applies (the cluster kernels move 4-byte payloads, so 8-byte ones take
-// the group barrier; the two-pairs TMEM kernel takes 4-byte keys without payload, the
-// rest the group barrier), and the most levels it can fuse up to the setting.
+// the group barrier; the two-pairs TMEM kernel takes every key type and payload, the
+// group barrier only where it cannot keep two CTAs on an SM), and the most levels it can
+// fuse up to the setting.
 struct FusedChoice {
     uint32_t engine, levels;
 };
@@ -231,7 +232,7 @@ ipm_status merge_core(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t 
         return launch_cluster_merge(buf, static_cast<uint32_t *>(vals), la, lb, key, split, Gs,
                                     F, sb, stream);
     if (F > 0 && use_tmem)
-        return launch_group2_merge(buf, la, lb, key, split, Gs, F,
+        return launch_group2_merge(buf, vals, vb, la, lb, key, split, Gs, F,
                                    reinterpret_cast<uint32_t *>(w + L.group_off), sb, stream);
     if (F > 0)
         return launch_group_merge(buf, vals, vb, la, lb, key, split, Gs, F,

@@ -415,8 +415,8 @@ __global__ void __launch_bounds__(THREADS, 2)
 }
 
 // ---------------------------------------------------------------------------------
-// The group barrier with two pairs per CTA (keys without payload): the first pair is
-// merged on chip and its output parked in tensor memory (TMEM, 256 columns of the
+// The group barrier with two pairs per CTA (keys, with or without payload): the first
+// pair is merged on chip and its output parked in tensor memory (TMEM, 256 columns of the
 // SM's 512 per CTA), then the second is staged and merged in shared memory, so a CTA
 // holds two merged pairs and a group of 2^F pairs needs 2^(F-1) resident CTAs: one
 // more level is fused than with one pair per CTA.  After the group barrier the second
@@ -424,32 +424,45 @@ __global__ void __launch_bounds__(THREADS, 2)
 // its own lane and columns) and stored the same way.  Tickets cover pairs 2t and 2t+1
 // (one group: groups are aligned to 2^F >= 2 pairs); the ticket-order argument of the
 // one-pair kernel holds with 2^(F-1) claims per group.  Exactly two CTAs fit an SM
-// (shared memory is padded to kGroup2Smem), so the two allocations never wait.
+// (each CTA takes at least kGroup2Smem of shared memory), so the two allocations never
+// wait.
 // ---------------------------------------------------------------------------------
 constexpr uint32_t kGroup2Cols = 256;
 // more than a third of the SM's 228 KB (no third CTA fits), less than half with each
 // CTA's static and reserved bytes (two fit the carveout)
 constexpr size_t kGroup2Smem = 78u << 10;
 
-template <typename K, int THREADS, int E>
+// The dynamic shared memory of a two-pairs CTA: its staging buffer, at least kGroup2Smem.
+template <typename K, bool KV, typename V>
+constexpr size_t group2_smem() {
+    constexpr size_t need =
+        ClusterShape<K, KV, ClusterTileOf<K, KV, V>::T, ClusterTileOf<K, KV, V>::E, V>::kSmem;
+    return need > kGroup2Smem ? need : kGroup2Smem;
+}
+
+template <typename K, bool KV, typename V, int THREADS, int E>
 __global__ void __launch_bounds__(THREADS, 2)
-    group2_merge_kernel(K *__restrict__ buf, uint64_t la, uint64_t lb,
+    group2_merge_kernel(K *__restrict__ buf, V *__restrict__ vals, uint64_t la, uint64_t lb,
                         const uint64_t *__restrict__ split, uint32_t G, uint32_t F,
                         uint32_t *__restrict__ gctr, StatusBlock *sb) {
-    // a thread parks its E keys as W 32-bit words in W consecutive columns of its lane;
-    // the warps sharing a lane quarter take column blocks of CS (W rounded up to 64, so
-    // every 32-column access starts at a multiple of 32)
-    constexpr int W = E * int(sizeof(K)) / 4;
+    // a thread parks its E keys (and E payloads) as W 32-bit words in W consecutive
+    // columns of its lane; the warps sharing a lane quarter take column blocks of CS (W
+    // rounded up to 64, so every 32-column access starts at a multiple of 32)
+    constexpr int WK = E * int(sizeof(K)) / 4, WV = KV ? E * int(sizeof(V)) / 4 : 0;
+    constexpr int W = WK + WV;
     constexpr uint32_t CS = uint32_t((W + 63) / 64 * 64);
-    static_assert(E % 2 == 1 && THREADS % 128 == 0 && sizeof(K) % 4 == 0, "shape");
+    static_assert(E % 2 == 1 && THREADS % 128 == 0 && sizeof(K) % 4 == 0 && sizeof(V) % 4 == 0,
+                  "shape");
     static_assert((THREADS / 128) * CS <= kGroup2Cols, "a thread's outputs fit its columns");
-    using Shape = ClusterShape<K, false, THREADS, E>;
+    using Shape = ClusterShape<K, KV, THREADS, E, V>;
+    static_assert(Shape::kSmem <= group2_smem<K, KV, V>(), "launched with the staging buffer");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);
     K *R = reinterpret_cast<K *>(smem_raw + 128);
+    V *RV = reinterpret_cast<V *>(smem_raw + 128 + Shape::kKeyBytes);
     __shared__ int abort_flag;
     __shared__ uint32_t s_t[2], s_taddr;
-    __shared__ PairGeo<K> pgs[2][2];  // [current / next claim][first / second pair]
+    __shared__ PairGeo<K, V> pgs[2][2];  // [current / next claim][first / second pair]
     if (sb == nullptr || *((volatile unsigned int *)&sb->done)) return;
     const uint32_t tid = threadIdx.x, warp = tid >> 5;
     const uint64_t claims = (1ull << G) >> 1;
@@ -462,10 +475,10 @@ __global__ void __launch_bounds__(THREADS, 2)
         const uint32_t t = atomicAdd(&sb->counters[kGroupTicket], 1u);
         s_t[q] = t;
         if (uint64_t(t) < claims) {
-            pair_geometry<K, false, Shape::kTile, uint32_t>(pgs[q][0], buf, nullptr, la, lb,
-                                                            split, G, F, 2ull * t, sb);
-            pair_geometry<K, false, Shape::kTile, uint32_t>(pgs[q][1], buf, nullptr, la, lb,
-                                                            split, G, F, 2ull * t + 1, sb);
+            pair_geometry<K, KV, Shape::kTile, V>(pgs[q][0], buf, vals, la, lb, split, G, F,
+                                                  2ull * t, sb);
+            pair_geometry<K, KV, Shape::kTile, V>(pgs[q][1], buf, vals, la, lb, split, G, F,
+                                                  2ull * t + 1, sb);
         }
     };
     if (tid == 0) {
@@ -485,34 +498,65 @@ __global__ void __launch_bounds__(THREADS, 2)
     uint32_t parity = 0, cur = 0;
 
     // stage one pair's two slices (bodies by bulk copy, heads / tails by plain loads)
-    auto stage = [&](volatile PairGeo<K> &vg) {
+    auto stage = [&](volatile PairGeo<K, V> &vg) {
         const uint32_t a = vg.a, b = vg.b;
         if (a + b == 0) return;
-        if (tid == 0)
-            mbar_arrive_expect_tx(mbar, body_bytes(const_cast<K *>(vg.gA), a) +
-                                            body_bytes(const_cast<K *>(vg.gB), b));
+        if (tid == 0) {
+            uint32_t tx = body_bytes(const_cast<K *>(vg.gA), a) +
+                          body_bytes(const_cast<K *>(vg.gB), b);
+            if (KV)
+                tx += body_bytes(const_cast<V *>(vg.vA), a) + body_bytes(const_cast<V *>(vg.vB), b);
+            mbar_arrive_expect_tx(mbar, tx);
+        }
         stage_range<K, THREADS>(R + vg.offA, vg.gA, a, mbar);
         stage_range<K, THREADS>(R + vg.offB, vg.gB, b, mbar);
+        if (KV) {
+            stage_range<V, THREADS>(RV + vg.offAV, vg.vA, a, mbar);
+            stage_range<V, THREADS>(RV + vg.offBV, vg.vB, b, mbar);
+        }
         if (!mbar_wait_bounded(mbar, parity)) atomicOr(&abort_flag, 1);
         parity ^= 1u;
+    };
+    // store one pair's merged keys (and payloads) from the staging buffer
+    auto store = [&](volatile PairGeo<K, V> &vg) {
+        const uint32_t c = vg.a + vg.b;
+        if (c == 0) return;
+        store_range<K, THREADS>(const_cast<K *>(vg.gO), R + vg.oo, c);
+        if (KV) store_range<V, THREADS>(const_cast<V *>(vg.vO), RV + vg.ooV, c);
     };
 
     for (;;) {
         if (uint64_t(*((volatile uint32_t *)&s_t[cur])) >= claims) break;
-        volatile PairGeo<K> &g0 = pgs[cur][0];
-        volatile PairGeo<K> &g1 = pgs[cur][1];
+        volatile PairGeo<K, V> &g0 = pgs[cur][0];
+        volatile PairGeo<K, V> &g1 = pgs[cur][1];
 
         // ---- first pair: stage, merge into registers, park in TMEM
         stage(g0);
         __syncthreads();  // every thread's head / tail loads have landed too
         {
             K ok[E] = {};  // outputs past the pair's end are parked but never read back
-            uint32_t oi[1];
-            if (!abort_flag)
-                merge_path_regs<K, false, THREADS, E, true>(R + g0.offA, g0.a, g0.offB - g0.offA,
-                                                            g0.b, ok, oi);
+            V ov[KV ? E : 1] = {};
+            uint32_t oi[KV ? E : 1];
+            const uint32_t a0 = g0.a, c0 = g0.a + g0.b;
+            const K *sk = R + g0.offA;
+            if (!abort_flag) {
+                merge_path_regs<K, KV, THREADS, E, true>(sk, a0, g0.offB - g0.offA, g0.b, ok,
+                                                         oi);
+                const uint32_t dt = tid * uint32_t(E);
+                if (KV && dt < c0) {  // the merge gave staged indices: gather both
+                    const V *sv = RV + g0.offAV;
+                    const uint32_t bo = g0.offB - g0.offA, bov = g0.offBV - g0.offAV;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const uint32_t q = (dt + e < c0) ? oi[KV ? e : 0] : 0u;
+                        ok[e] = sk[q];
+                        ov[KV ? e : 0] = sv[q < a0 ? q : bov + (q - bo)];
+                    }
+                }
+            }
             uint32_t w[W];
-            memcpy(w, ok, sizeof(w));
+            memcpy(w, ok, sizeof(ok));
+            if (KV) memcpy(w + WK, ov, size_t(WV) * 4);
             const uint32_t ta = tcol();
 #pragma unroll
             for (int c = 0; c + 32 <= W; c += 32)
@@ -529,9 +573,9 @@ __global__ void __launch_bounds__(THREADS, 2)
         if (tid == 0)  // both pairs' slices have been read
             atomicAdd(gctr + (*((volatile uint32_t *)&s_t[cur]) >> (F - 1)), 1u);
         if (!abort_flag && g1.a + g1.b > 0)
-            merge_two<K, false, THREADS, E, true, uint32_t>(R + g1.offA, nullptr, g1.a,
-                                                            g1.offB - g1.offA, 0u, g1.b,
-                                                            R + g1.oo, nullptr);
+            merge_two<K, KV, THREADS, E, true, V>(R + g1.offA, RV + g1.offAV, g1.a,
+                                                  g1.offB - g1.offA, g1.offBV - g1.offAV, g1.b,
+                                                  R + g1.oo, RV + g1.ooV);
         fence_proxy_async_smem();
 
         // ---- group barrier: the group's region may be written once every member has
@@ -559,15 +603,13 @@ __global__ void __launch_bounds__(THREADS, 2)
         }
 
         // ---- store the second pair, then bring the first back from TMEM and store it
-        const uint32_t c1 = g1.a + g1.b;
-        if (c1 > 0) store_range<K, THREADS>(const_cast<K *>(g1.gO), R + g1.oo, c1);
+        store(g1);
         if (tid == 0) {
             bulk_commit();
             bulk_wait_read0();
         }
         fence_proxy_async_smem();
         __syncthreads();  // the staging buffer is free again
-        const uint32_t c0 = g0.a + g0.b;
         {
             uint32_t w[W];
             const uint32_t ta = tcol();
@@ -577,17 +619,26 @@ __global__ void __launch_bounds__(THREADS, 2)
 #pragma unroll
             for (int c = W / 32 * 32; c < W; ++c) w[c] = tmem_ld1(ta + uint32_t(c));
             tmem_wait_ld();
+            const uint32_t c0 = g0.a + g0.b;
+            const uint32_t dt = tid * uint32_t(E);
             K ok[E];
             memcpy(ok, w, sizeof(ok));
-            const uint32_t dt = tid * uint32_t(E);
             K *out = R + g0.oo;
 #pragma unroll
             for (int e = 0; e < E; ++e)
                 if (dt + e < c0) out[dt + e] = ok[e];
+            if (KV) {
+                V ov[KV ? E : 1];
+                memcpy(ov, w + WK, size_t(WV) * 4);
+                V *vout = RV + g0.ooV;
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (dt + e < c0) vout[dt + e] = ov[KV ? e : 0];
+            }
         }
         fence_proxy_async_smem();
         __syncthreads();
-        if (c0 > 0) store_range<K, THREADS>(const_cast<K *>(g0.gO), R + g0.oo, c0);
+        store(g0);
         if (tid == 0) {
             bulk_commit();
             claim(cur ^ 1u);  // the next claim, while the bulk store reads shared memory
@@ -647,17 +698,17 @@ ipm_status group_merge_t(void *buf, void *vals, uint64_t la, uint64_t lb,
 // holds half of the SM's TMEM), computed once from its registers, shared memory and
 // threads against the SM's limits.  (The occupancy query answers one CTA per SM for any
 // kernel that allocates TMEM, whatever it allocates; two such CTAs do run side by side.)
-template <typename K>
+template <typename K, bool KV, typename V>
 int group2_grid() {
-    constexpr int T = ClusterTileOf<K, false>::T;
-    auto kern = group2_merge_kernel<K, T, 33>;
+    constexpr int T = ClusterTileOf<K, KV, V>::T;
+    auto kern = group2_merge_kernel<K, KV, V, T, 33>;
     static int cached = -1;
     if (cached >= 0) return cached;
     cached = 0;
     int dev = 0, regs_sm = 0, smem_sm = 0, threads_sm = 0, reserved = 0;
     cudaFuncAttributes fa;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(kGroup2Smem)) != cudaSuccess ||
+                             int(group2_smem<K, KV, V>())) != cudaSuccess ||
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                              int(cudaSharedmemCarveoutMaxShared)) != cudaSuccess ||
         cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
@@ -673,7 +724,8 @@ int group2_grid() {
         return cached;
     }
     const long regs_cta = long(fa.numRegs) * T;
-    const long smem_cta = long(kGroup2Smem) + long(fa.sharedSizeBytes) + long(reserved);
+    const long smem_cta =
+        long(group2_smem<K, KV, V>()) + long(fa.sharedSizeBytes) + long(reserved);
     long per_sm = threads_sm / T;
     if (regs_cta > 0 && regs_sm / regs_cta < per_sm) per_sm = regs_sm / regs_cta;
     if (smem_sm / smem_cta < per_sm) per_sm = smem_sm / smem_cta;
@@ -681,18 +733,40 @@ int group2_grid() {
     return cached;
 }
 
-template <typename K>
-ipm_status group2_merge_t(void *buf, uint64_t la, uint64_t lb, const uint64_t *split,
-                          uint32_t G, uint32_t F, uint32_t *gctr, StatusBlock *sb,
-                          cudaStream_t stream) {
-    const int grid = group2_grid<K>();
+template <typename K, bool KV, typename V>
+ipm_status group2_merge_t(void *buf, void *vals, uint64_t la, uint64_t lb,
+                          const uint64_t *split, uint32_t G, uint32_t F, uint32_t *gctr,
+                          StatusBlock *sb, cudaStream_t stream) {
+    const int grid = group2_grid<K, KV, V>();
     if (F < 1 || grid < (1 << (F - 1))) return IPM_ERR_CUDA;
     const uint64_t claims = (1ull << G) >> 1;
     const unsigned g = unsigned(claims < uint64_t(grid) ? claims : uint64_t(grid));
-    constexpr int T = ClusterTileOf<K, false>::T;
-    group2_merge_kernel<K, T, 33><<<g, T, kGroup2Smem, stream>>>((K *)buf, la, lb, split, G, F,
-                                                               gctr, sb);
+    constexpr int T = ClusterTileOf<K, KV, V>::T;
+    static_assert(ClusterTileOf<K, KV, V>::E == 33, "the instantiated shape");
+    group2_merge_kernel<K, KV, V, T, 33><<<g, T, group2_smem<K, KV, V>(), stream>>>(
+        (K *)buf, (V *)vals, la, lb, split, G, F, gctr, sb);
     return last_launch_status();
+}
+
+template <typename K>
+int group2_grid_vb(uint32_t vb) {
+    return vb == 8   ? group2_grid<K, true, uint64_t>()
+           : vb != 0 ? group2_grid<K, true, uint32_t>()
+                     : group2_grid<K, false, uint32_t>();
+}
+
+template <typename K>
+ipm_status group2_dispatch(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t lb,
+                           const uint64_t *split, uint32_t G, uint32_t F, uint32_t *gctr,
+                           StatusBlock *sb, cudaStream_t stream) {
+    if (vb == 8)
+        return group2_merge_t<K, true, uint64_t>(buf, vals, la, lb, split, G, F, gctr, sb,
+                                                 stream);
+    if (vb != 0)
+        return group2_merge_t<K, true, uint32_t>(buf, vals, la, lb, split, G, F, gctr, sb,
+                                                 stream);
+    return group2_merge_t<K, false, uint32_t>(buf, nullptr, la, lb, split, G, F, gctr, sb,
+                                              stream);
 }
 
 // Resident clusters of the kernel on the current device (0 when clusters of C CTAs
@@ -886,14 +960,13 @@ ipm_status launch_group_merge(void *buf, void *vals, uint32_t vb, uint64_t la, u
 }
 
 uint32_t usable_group2_levels(ipm_dtype key, uint32_t vb, uint32_t wanted) {
-    if (vb != 0) return 0;
     int grid = 0;
     switch (key) {
-    case IPM_INT32: grid = group2_grid<int32_t>(); break;
-    case IPM_UINT32: grid = group2_grid<uint32_t>(); break;
-    case IPM_FLOAT32: grid = group2_grid<float>(); break;
-    case IPM_UINT64: grid = group2_grid<uint64_t>(); break;
-    case IPM_INT64: grid = group2_grid<int64_t>(); break;
+    case IPM_INT32: grid = group2_grid_vb<int32_t>(vb); break;
+    case IPM_UINT32: grid = group2_grid_vb<uint32_t>(vb); break;
+    case IPM_FLOAT32: grid = group2_grid_vb<float>(vb); break;
+    case IPM_UINT64: grid = group2_grid_vb<uint64_t>(vb); break;
+    case IPM_INT64: grid = group2_grid_vb<int64_t>(vb); break;
     }
     if (grid == 0 || wanted == 0) return 0;
     uint32_t f = wanted;
@@ -901,18 +974,23 @@ uint32_t usable_group2_levels(ipm_dtype key, uint32_t vb, uint32_t wanted) {
     return f;
 }
 
-ipm_status launch_group2_merge(void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
-                               const uint64_t *split, uint32_t G, uint32_t F, uint32_t *gctr,
-                               StatusBlock *sb, cudaStream_t stream) {
+ipm_status launch_group2_merge(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t lb,
+                               ipm_dtype key, const uint64_t *split, uint32_t G, uint32_t F,
+                               uint32_t *gctr, StatusBlock *sb, cudaStream_t stream) {
     IPM_CUDA_TRY(cudaMemsetAsync(gctr, 0, sizeof(uint32_t) * size_t((1ull << G) >> F), stream));
     switch (key) {
-    case IPM_INT32: return group2_merge_t<int32_t>(buf, la, lb, split, G, F, gctr, sb, stream);
-    case IPM_UINT32: return group2_merge_t<uint32_t>(buf, la, lb, split, G, F, gctr, sb, stream);
-    case IPM_FLOAT32: return group2_merge_t<float>(buf, la, lb, split, G, F, gctr, sb, stream);
-    case IPM_UINT64: return group2_merge_t<uint64_t>(buf, la, lb, split, G, F, gctr, sb, stream);
-    case IPM_INT64: return group2_merge_t<int64_t>(buf, la, lb, split, G, F, gctr, sb, stream);
-    default: return IPM_ERR_UNSUPPORTED_DTYPE;
+    case IPM_INT32:
+        return group2_dispatch<int32_t>(buf, vals, vb, la, lb, split, G, F, gctr, sb, stream);
+    case IPM_UINT32:
+        return group2_dispatch<uint32_t>(buf, vals, vb, la, lb, split, G, F, gctr, sb, stream);
+    case IPM_FLOAT32:
+        return group2_dispatch<float>(buf, vals, vb, la, lb, split, G, F, gctr, sb, stream);
+    case IPM_UINT64:
+        return group2_dispatch<uint64_t>(buf, vals, vb, la, lb, split, G, F, gctr, sb, stream);
+    case IPM_INT64:
+        return group2_dispatch<int64_t>(buf, vals, vb, la, lb, split, G, F, gctr, sb, stream);
     }
+    return IPM_ERR_UNSUPPORTED_DTYPE;
 }
 
 uint32_t usable_fused_levels(ipm_dtype key, bool with_values, uint32_t wanted) {

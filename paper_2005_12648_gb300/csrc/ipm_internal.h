@@ -75,10 +75,11 @@ ipm_status launch_group_merge(void *buf, void *vals, uint32_t vb, uint64_t la, u
 uint32_t usable_group_levels(ipm_dtype key, uint32_t vb, uint32_t wanted);
 
 // The group barrier with two pairs per CTA, the first merged pair parked in TMEM
-// (4-byte keys without payload): groups of 2^F pairs need 2^(F-1) resident CTAs.
-ipm_status launch_group2_merge(void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
-                               const uint64_t *split, uint32_t G, uint32_t F, uint32_t *gctr,
-                               StatusBlock *sb, cudaStream_t stream);
+// (every key type, with or without payload): groups of 2^F pairs need 2^(F-1) resident
+// CTAs.
+ipm_status launch_group2_merge(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t lb,
+                               ipm_dtype key, const uint64_t *split, uint32_t G, uint32_t F,
+                               uint32_t *gctr, StatusBlock *sb, cudaStream_t stream);
 // The largest F <= wanted the two-pairs kernel can run (0: not for this key / payload).
 uint32_t usable_group2_levels(ipm_dtype key, uint32_t vb, uint32_t wanted);
 

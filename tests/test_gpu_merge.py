@@ -197,7 +197,8 @@ def test_merge_inplace_kv8_matches_oracle(ipm, dev, orc, dt, dist):
         assert np.array_equal(vals.cpu().numpy().view(np.uint64), wv), (la, lb)
 
 
-@pytest.mark.parametrize("engine,fused", [(1, 0), (1, 2), (1, 5), (1, 8), (0, 4)])
+@pytest.mark.parametrize("engine,fused", [(1, 0), (1, 2), (1, 5), (1, 8), (0, 4), (2, 1),
+                                          (2, 9)])
 @pytest.mark.parametrize("dt", [np.uint32, np.int64])
 def test_kv8_fused_levels_match_oracle(ipm, dev, orc, engine, fused, dt):
     """8-byte payloads through every fused-level setting (the cluster engine hands
@@ -221,6 +222,48 @@ def test_kv8_fused_levels_match_oracle(ipm, dev, orc, engine, fused, dt):
     wk, wv = orc.merge_kvw(a, pay[:la], b, pay[la:])
     assert first_diff(from_dev(keys, dt), wk) is None
     assert np.array_equal(vals.cpu().numpy().view(np.uint64), wv)
+
+
+@pytest.mark.parametrize("fused", [1, 2, 5, 9])
+@pytest.mark.parametrize("dt,vb", [(np.uint32, 4), (np.float32, 8), (np.int64, 4),
+                                   (np.uint64, 8)])
+def test_kv_tensor_memory_engine_matches_oracle(ipm, dev, orc, fused, dt, vb):
+    """Key-value merges through the two-pairs kernel (the first pair's keys and payloads
+    parked in TMEM) for every key / payload width pair: fused depths from one level to
+    the default, pair counts below the group size, empty runs, ties and ragged sizes."""
+    import torch
+
+    cases = [(3_000_017, 2_900_011, "uniform", 0), (123_457, 98_765, "dup16", 6),
+             (1_000_000, 1, "uniform", 4), (50_000, 70_001, "zipf", 3),
+             (333_333, 333_333, "revdisjoint", 5)]
+    ipm.ipm_set_fused_levels(fused)
+    try:
+        for la, lb, dist, G in cases:
+            if dist == "zipf" and dt == np.float32:
+                dist = "dup16"
+            a, b = W.make_pair(dist, dt, la, lb, seed=la + 3 * lb + fused)
+            n = la + lb
+            idx = np.arange(n, dtype=np.uint64)
+            if vb == 8:
+                pay = (idx << np.uint64(32)) | ((idx * np.uint64(2654435761)) &
+                                               np.uint64(0xFFFFFFFF))
+                vals = torch.from_numpy(pay.view(np.int64).copy()).to(dev)
+            else:
+                pay = (idx * np.uint64(2654435761) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+                vals = torch.from_numpy(pay.view(np.int32).copy()).to(dev)
+            name = NAME[np.dtype(dt)]
+            G = max(G, ipm.ipm_merge_plan(la, lb, name, with_values=vb)[0])
+            assert ipm.ipm_merge_fused_plan(la, lb, name, with_values=vb)[0] == 2
+            keys = to_dev(np.concatenate([a, b]), dev)
+            ws = ipm.merge_inplace_kv(keys, vals, la, lb, name, log2_pairs=G)
+            torch.cuda.synchronize()
+            assert ipm.ipm_read_device_status(ws) == 0
+            wk, wv = orc.merge_kvw(a, pay[:la], b, pay[la:])
+            assert first_diff(from_dev(keys, dt), wk) is None, (la, lb, dist, G)
+            got_v = vals.cpu().numpy().view(np.uint64 if vb == 8 else np.uint32)
+            assert np.array_equal(got_v, wv), (la, lb, dist, G)
+    finally:
+        ipm.ipm_set_fused_levels(10)
 
 
 def test_async_on_a_side_stream(ipm, dev, orc):
@@ -267,9 +310,9 @@ def test_fused_bottom_levels_match_oracle(ipm, dev, orc, engine, fused, dt):
 
 
 def test_default_fused_plan_uses_tensor_memory(ipm):
-    """By default keys without payload take the two-pairs kernel that parks a merged pair
-    in TMEM, fusing one level more than one pair per CTA; key-value merges take the
-    one-pair group barrier."""
+    """By default every key type, with or without a 4- or 8-byte payload, takes the
+    two-pairs kernel that parks a merged pair in TMEM, fusing one level more than one
+    pair per CTA."""
     n = 1 << 28
     e2, f2 = ipm.ipm_merge_fused_plan(n, n, "int32")
     try:
@@ -278,10 +321,11 @@ def test_default_fused_plan_uses_tensor_memory(ipm):
     finally:
         ipm.ipm_set_fused_engine(2)
     assert (e1, e2) == (1, 2) and f2 == f1 + 1
-    assert ipm.ipm_merge_fused_plan(n, n, "int32", with_values=4)[0] == 1
-    assert ipm.ipm_merge_fused_plan(n, n, "uint64", with_values=8)[0] == 1
     for dt in ("uint64", "int64", "float32", "uint32"):
         assert ipm.ipm_merge_fused_plan(n, n, dt) == (2, f2), dt
+    for dt in ("int32", "uint64"):
+        for vb in (4, 8):
+            assert ipm.ipm_merge_fused_plan(n, n, dt, with_values=vb) == (2, f2), (dt, vb)
 
 
 @pytest.mark.parametrize("engine", [0, 1])
