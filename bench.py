@@ -571,6 +571,61 @@ def measure_division(torch, ipm, workloads, dev, stream, steps=10, warmup=3):
                              "ms": times}}
 
 
+def measure_permutation(torch, ipm, workloads, dev, stream, steps=5, warmup=3):
+    """The division stage by one permutation (sOptMov, Alg. 2) against the level-by-level
+    exchange (sRecPar, Alg. 3) on the headline buffer (uniform int32 2^28 + 2^28) with
+    the same exact split table: each alone, and each inside a whole merge (splits,
+    division, pair merge).  The two layouts are compared with each other."""
+    peak, _ = peaks()
+    la = lb = 1 << 28
+    n = la + lb
+    name = "int32"
+    pristine = workloads.make_buffer_torch(torch, "uniform", np.int32, la, lb, 0, dev)
+    buf = torch.empty_like(pristine)
+    G = ipm.ipm_merge_plan(la, lb, name)[0]
+    split = torch.empty((1 << G) + 1, dtype=torch.int64, device=dev)
+    ipm.ipm_merge_splits(pristine, la, lb, name, 1 << G, split)
+    ws_perm = ipm.workspace(ipm.ipm_rearrange_permute_workspace_bytes(la, lb, name), dev)
+    ws_lvl = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, name, False, G), dev)
+    calls = {
+        "permute": lambda: ipm.ipm_rearrange_permute(buf, None, la, lb, name, split, G,
+                                                     ws_perm),
+        "levels": lambda: ipm.ipm_merge_rearrange(buf, None, la, lb, name, split, G, ws_lvl),
+        "merge_via_permute": lambda: (ipm.ipm_merge_splits(buf, la, lb, name, 1 << G, split),
+                                      ipm.ipm_rearrange_permute(buf, None, la, lb, name, split,
+                                                                G, ws_perm),
+                                      ipm.ipm_merge_pairs(buf, None, la, lb, name, split, G)),
+        "merge_default": lambda: ipm.ipm_merge_inplace(buf, la, lb, name, ws_lvl),
+    }
+
+    def prep():
+        buf.copy_(pristine)
+
+    res, kept = {}, {}
+    for key, call in calls.items():
+        for _ in range(warmup):
+            prep()
+            call()
+        torch.cuda.synchronize()
+        kept[key] = buf.clone() if key in ("permute", "levels") else None
+        if key.startswith("merge"):
+            kept[key] = bool(torch.all(buf[1:] >= buf[:-1]).item())
+        ms = float(np.median(timed_steps(torch, stream, steps, prep, call)))
+        res[key] = {"ms": ms}
+        if key in ("permute", "levels"):
+            gbs = 2.0 * n * 4 / (ms * 1e-3) / 1e9
+            res[key].update({"gbs_one_pass": gbs, "frac_one_pass": gbs / peak})
+        else:
+            res[key]["gkeys_s"] = n / (ms * 1e-3) / 1e9
+    same = bool(torch.equal(kept["permute"], kept["levels"]))
+    del kept["permute"], kept["levels"], buf, pristine, ws_perm, ws_lvl
+    return {"workload": "uniform int32 2^28 + 2^28, exact splits, P = 2^%d" % G,
+            "bytes_one_pass": 2 * n * 4, "peak_gbs": peak, "ms": res,
+            "layouts_identical": same, "merges_sorted": [kept["merge_via_permute"],
+                                                         kept["merge_default"]],
+            "permute_over_levels_time": res["permute"]["ms"] / res["levels"]["ms"]}
+
+
 def _public(d):
     return {k: v for k, v in d.items() if k not in ("buffer", "pristine", "model_tensor")}
 
@@ -609,6 +664,8 @@ def run_ours(args, rank, world):
         forms["rotate"] = measure_rotations(torch, ipm, dev, stream)
         torch.cuda.empty_cache()
         forms["division"] = measure_division(torch, ipm, workloads, dev, stream)
+        torch.cuda.empty_cache()
+        forms["permutation"] = measure_permutation(torch, ipm, workloads, dev, stream)
         torch.cuda.empty_cache()
         line["forms"] = forms
     print(json.dumps(line), flush=True)

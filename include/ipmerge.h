@@ -175,6 +175,36 @@ ipm_status ipm_merge_rearrange(void *d_buf, void *d_vals, uint64_t len_a, uint64
                                ipm_stream_t stream);
 
 /*
+ * Step 2 by one permutation (sOptMov, Alg. 2, Sec. 3.2): the same layout as
+ * ipm_merge_rearrange (pair k at d_buf[d_k, d_{k+1}) as A[i_k, i_{k+1}) followed by
+ * B[j_k, j_{k+1}), d_k = floor(k*n/2^log2_pairs), j_k = d_k - i_k), reached by moving
+ * every element once along the cycles of that permutation instead of level by level.
+ * d_split_a (device, 2^log2_pairs + 1 uint64, read only) is any table with i_0 = 0,
+ * i_P = len_a and, for every k, i_k <= i_{k+1}, i_{k+1} - i_k <= d_{k+1} - d_k,
+ * i_k <= d_k and d_{k+1} - i_{k+1} <= len_b (ipm_merge_splits makes one).  The paper's
+ * in-value marker of moved elements is replaced by a bitmap of n bits in the workspace,
+ * so keys of every type keep their full range.  with_values is the payload width as in
+ * ipm_merge_plan (0: d_vals must be NULL; 1 or 4: uint32; 8: uint64), moved with the
+ * keys.  The workspace (ipm_rearrange_permute_workspace_bytes for the same sizes, type
+ * and payload; 256-byte aligned) holds the bitmap and the elements saved per round,
+ * about n/8 + (n/31) * (key + payload + 8) bytes.  The call blocks the host thread: it
+ * runs rounds on `stream` and reads the uncovered count back after each (at most 32
+ * rounds).  Errors: IPM_ERR_INVALID_ARG (NULL pointers, d_vals not matching
+ * with_values, log2_pairs > 22, len_a or len_b > 2^40, or a table that is not of the
+ * form above: detected on the device before any element moves), IPM_ERR_ALIGNMENT
+ * (d_buf / d_vals not aligned to their element size, d_split_a not 8-byte aligned,
+ * d_ws not 256-byte aligned), IPM_ERR_WORKSPACE, IPM_ERR_UNSUPPORTED_DTYPE,
+ * IPM_ERR_CUDA, IPM_ERR_DEVICE (an internal consistency check failed).
+ */
+ipm_status ipm_rearrange_permute_workspace_bytes(uint64_t len_a, uint64_t len_b,
+                                                 ipm_dtype key_dtype, int with_values,
+                                                 size_t *bytes);
+ipm_status ipm_rearrange_permute(void *d_buf, void *d_vals, uint64_t len_a, uint64_t len_b,
+                                 ipm_dtype key_dtype, int with_values,
+                                 const uint64_t *d_split_a, uint32_t log2_pairs, void *d_ws,
+                                 size_t ws_bytes, ipm_stream_t stream);
+
+/*
  * Step 3 alone: merge every pair of an arranged buffer (the layout step 2 produces)
  * in place, one CTA per pair through shared memory.  d_split_a is the P+1 split table
  * (P = 2^log2_pairs); every pair must fit the tile capacity.  d_vals as above.

@@ -69,6 +69,8 @@ _SIGS = {
     "ipm_merge_splits": (_i, [_vp, _u64, _u64, _i, _u64, _vp, _vp]),
     "ipm_merge_rearrange": (_i, [_vp, _vp, _u64, _u64, _i, _vp, _u32, _vp, _sz, _vp]),
     "ipm_merge_pairs": (_i, [_vp, _vp, _u64, _u64, _i, _vp, _u32, _vp]),
+    "ipm_rearrange_permute_workspace_bytes": (_i, [_u64, _u64, _i, _i, ctypes.POINTER(_sz)]),
+    "ipm_rearrange_permute": (_i, [_vp, _vp, _u64, _u64, _i, _i, _vp, _u32, _vp, _sz, _vp]),
     "ipm_rotate_workspace_bytes": (_i, [_u64, _u64, _u32, ctypes.POINTER(_sz)]),
     "ipm_read_exchange_bytes": (_i, [_vp, _vp, ctypes.POINTER(_u64)]),
     "ipm_rotate": (_i, [_vp, _u64, _u64, _u32, _vp, _sz, _vp]),
@@ -245,6 +247,30 @@ def ipm_merge_rearrange(buf, vals, len_a: int, len_b: int, key_dtype, split_a,
     _check(load().ipm_merge_rearrange(_ptr(buf), _ptr(vals), len_a, len_b, _dt(key_dtype),
                                       _ptr(split_a), log2_pairs, _ptr(ws), wsb,
                                       _stream(stream)), "ipm_merge_rearrange")
+
+
+def ipm_rearrange_permute_workspace_bytes(len_a: int, len_b: int, key_dtype,
+                                          with_values=False) -> int:
+    out = _sz(0)
+    _check(load().ipm_rearrange_permute_workspace_bytes(len_a, len_b, _dt(key_dtype),
+                                                        _payload(with_values),
+                                                        ctypes.byref(out)),
+           "ipm_rearrange_permute_workspace_bytes")
+    return int(out.value)
+
+
+def ipm_rearrange_permute(buf, vals, len_a: int, len_b: int, key_dtype, split_a,
+                          log2_pairs: int, ws, ws_bytes: int | None = None, with_values=None,
+                          stream=None) -> None:
+    """The division stage as one permutation (sOptMov); with_values defaults to the
+    payload tensor's element size (None: keys only)."""
+    if with_values is None:
+        with_values = 0 if vals is None else vals.element_size()
+    wsb = _nbytes(ws) if ws_bytes is None else ws_bytes
+    _check(load().ipm_rearrange_permute(_ptr(buf), _ptr(vals), len_a, len_b, _dt(key_dtype),
+                                        _payload(with_values), _ptr(split_a), log2_pairs,
+                                        _ptr(ws), wsb, _stream(stream)),
+           "ipm_rearrange_permute")
 
 
 def ipm_merge_pairs(buf, vals, len_a: int, len_b: int, key_dtype, split_a,

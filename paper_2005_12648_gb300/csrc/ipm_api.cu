@@ -358,6 +358,40 @@ ipm_status ipm_merge_rearrange(void *d_buf, void *d_vals, uint64_t len_a, uint64
     return IPM_OK;
 }
 
+ipm_status ipm_rearrange_permute_workspace_bytes(uint64_t len_a, uint64_t len_b,
+                                                 ipm_dtype key_dtype, int with_values,
+                                                 size_t *bytes) {
+    if (bytes == nullptr) return IPM_ERR_INVALID_ARG;
+    if (!valid_key(key_dtype)) return IPM_ERR_UNSUPPORTED_DTYPE;
+    const uint32_t vb = payload_bytes(with_values);
+    if (vb != 0 && vb != 4 && vb != 8) return IPM_ERR_UNSUPPORTED_DTYPE;
+    if (len_a > (uint64_t(1) << 40) || len_b > (uint64_t(1) << 40)) return IPM_ERR_INVALID_ARG;
+    *bytes = permute_workspace_bytes(len_a + len_b, uint32_t(dtype_bytes(key_dtype)), vb);
+    return IPM_OK;
+}
+
+ipm_status ipm_rearrange_permute(void *d_buf, void *d_vals, uint64_t len_a, uint64_t len_b,
+                                 ipm_dtype key_dtype, int with_values,
+                                 const uint64_t *d_split_a, uint32_t log2_pairs, void *d_ws,
+                                 size_t ws_bytes, ipm_stream_t stream) {
+    size_t need = 0;
+    IPM_TRY(ipm_rearrange_permute_workspace_bytes(len_a, len_b, key_dtype, with_values, &need));
+    const uint32_t vb = payload_bytes(with_values);
+    const uint32_t kb = uint32_t(dtype_bytes(key_dtype));
+    const uint64_t n = len_a + len_b;
+    if (log2_pairs > kMaxLog2Pairs || n > (~uint64_t(0) >> log2_pairs))
+        return IPM_ERR_INVALID_ARG;
+    if (d_buf == nullptr || d_split_a == nullptr || (vb != 0) != (d_vals != nullptr))
+        return IPM_ERR_INVALID_ARG;
+    if (d_ws == nullptr || ws_bytes < need) return IPM_ERR_WORKSPACE;
+    if (!aligned(d_buf, kb) || (vb && !aligned(d_vals, vb)) || !aligned(d_split_a, 8) ||
+        !aligned(d_ws, 256))
+        return IPM_ERR_ALIGNMENT;
+    if (n == 0) return IPM_OK;
+    return launch_permute(d_buf, d_vals, kb, vb, len_a, len_b, d_split_a, log2_pairs, d_ws,
+                          (cudaStream_t)stream);
+}
+
 ipm_status ipm_merge_pairs(void *d_buf, void *d_vals, uint64_t len_a, uint64_t len_b,
                            ipm_dtype key_dtype, const uint64_t *d_split_a,
                            uint32_t log2_pairs, ipm_stream_t stream) {

@@ -95,6 +95,13 @@ struct CsPlan {
     uint64_t lx, n, g, L, S, W;
     bool whole;
 };
+// The division stage by one permutation (sOptMov): workspace bytes for n elements of kb
+// key bytes and vb payload bytes, and the rounds themselves (host-synchronous).
+size_t permute_workspace_bytes(uint64_t n, uint32_t kb, uint32_t vb);
+ipm_status launch_permute(void *buf, void *vals, uint32_t kb, uint32_t vb, uint64_t la,
+                          uint64_t lb, const uint64_t *split, uint32_t G, void *ws,
+                          cudaStream_t st);
+
 CsPlan cs_plan(uint64_t lx, uint64_t ly);
 ipm_status launch_cs_rotate(void *ptr, uint32_t elem_bytes, const CsPlan &pl, void *save,
                             cudaStream_t stream);

@@ -52,6 +52,16 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_host_queries(lib):
     L, m = lib
+    # the permutation's workspace: status and counters, an n-bit map, and per round the
+    # saved keys (and payloads) of every 31st block of 32 positions plus their 8-byte
+    # positions
+    n = 3_000_017 + 2_900_011
+    cap = 32 * -(-(-(-n // 32)) // 31)
+    up = lambda x: -(-x // 256) * 256  # noqa: E731
+    for vb in (0, 4, 8):
+        want = 512 + up(-(-n // 32) * 4) + up(cap * 4) + up(cap * vb) + up(cap * 8)
+        assert m.ipm_rearrange_permute_workspace_bytes(3_000_017, 2_900_011, "int32",
+                                                       vb) == want
     assert m.ipm_version() >= 100
     assert m.ipm_status_string(0) == "IPM_OK"
     assert m.ipm_status_string(6) == "IPM_ERR_TIMEOUT"
@@ -110,6 +120,27 @@ def test_argument_errors_return_before_any_cuda_call(lib):
     assert L.ipm_division_splits(null, 4, 4, 0, 3, 0, 0x2000, 0x3000, null) == 1
     assert L.ipm_division_splits(0x1004, 4, 4, 2, 3, 0, 0x2000, 0x3000, null) == 3
     assert L.ipm_division_splits(0x1000, 4, 4, 0, 3, 0, 0x2004, 0x3000, null) == 3
+    # permutation: payload width, NULL table, payload pointer without a width, pairs
+    # beyond 2^22, a run beyond 2^40, small workspace, alignment
+    sz = ctypes.c_size_t()
+    assert L.ipm_rearrange_permute_workspace_bytes(100, 100, 0, 3, ctypes.byref(sz)) == 2
+    assert L.ipm_rearrange_permute_workspace_bytes(100, 100, 9, 0, ctypes.byref(sz)) == 2
+    assert L.ipm_rearrange_permute(0x1000, null, 4, 4, 0, 0, null, 2, 0x2000, 1 << 20,
+                                   null) == 1
+    assert L.ipm_rearrange_permute(0x1000, 0x3000, 4, 4, 0, 0, 0x4000, 2, 0x2000, 1 << 20,
+                                   null) == 1
+    assert L.ipm_rearrange_permute(0x1000, null, 4, 4, 0, 0, 0x4000, 23, 0x2000, 1 << 20,
+                                   null) == 1
+    assert L.ipm_rearrange_permute(0x1000, null, (1 << 40) + 1, 4, 0, 0, 0x4000, 2,
+                                   0x2000, 1 << 62, null) == 1
+    assert L.ipm_rearrange_permute(0x1000, null, 1000, 1000, 0, 0, 0x4000, 2, 0x2000, 16,
+                                   null) == 4
+    assert L.ipm_rearrange_permute(0x1002, null, 4, 4, 0, 0, 0x4000, 2, 0x2000, 1 << 20,
+                                   null) == 3
+    assert L.ipm_rearrange_permute(0x1000, null, 4, 4, 0, 0, 0x4004, 2, 0x2000, 1 << 20,
+                                   null) == 3
+    assert L.ipm_rearrange_permute(0x1000, null, 0, 0, 0, 0, 0x4000, 2, 0x2000, 1 << 20,
+                                   null) == 0
     # empty inputs are a no-op that succeeds without touching the device
     assert L.ipm_merge_inplace(null, 0, 0, 0, 0, null, 0, null) == 0
     with pytest.raises(m.IpmError):
