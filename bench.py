@@ -80,6 +80,12 @@ WORKLOADS = {
                            "(300 Adam steps); ipm_merge_inplace_learned"),
 }
 FORM = {"c4-int32-batched": "batched", "c5-float32-learned": "learned"}
+
+# DRAM bytes (read + write) per launch of exchange_level_ws_kernel on a workload, from
+# one single-pass ncu capture of that workload (dram__bytes_read.sum +
+# dram__bytes_write.sum, mean of 6 launches).  Valid for the kernel as captured; any
+# change to it voids the figure.
+EXCHANGE_TRAFFIC = {"c2-int32-uniform": 2104257323}
 # key-value workloads: the payload type per workload (payload = original buffer index)
 KV_WORKLOADS = {"c3-uint32-kv-zipf": "uint32", "f1-uint64-kv64-uniform": "uint64"}
 NP_DT = {"int32": np.int32, "uint32": np.uint32, "uint64": np.uint64, "float32": np.float32,
@@ -889,7 +895,7 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
                      "kernel": "exchange_level_ws_kernel (one launch per exchange level)",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} hbm_gbs",
-                     "traffic": None,
+                     "traffic": EXCHANGE_TRAFFIC.get(args.workload),
                      "bytes_per_launch": exch_bytes_per_launch,
                      "launch_ms": exch_launch_ms},
         "path": {"method_bytes": mb["total"], "min_bytes": mb["min"],

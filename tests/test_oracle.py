@@ -120,6 +120,32 @@ def test_arrange_is_pairs_back_to_back(orc):
         assert np.array_equal(seg, np.concatenate([a[i0:i1], b[j0:j1]]))
 
 
+def test_arrange_of_any_valid_table_is_a_permutation_into_pairs(orc):
+    """The layout of an arbitrary table (not a merge's), for keys and 8-byte payloads:
+    pair k holds A[i_k, i_{k+1}) then B[j_k, j_{k+1}), and the result is a permutation
+    of A|B (every index appears once)."""
+    rng = np.random.default_rng(4)
+    for la, lb, P in [(1000, 777, 16), (5, 300, 8), (300, 5, 8), (64, 64, 32), (3, 2, 8)]:
+        n = la + lb
+        d = orc.diagonals(n, P)
+        i = [0] * (P + 1)
+        i[P] = la
+        for k in range(1, P):
+            dk, dp = int(d[k]), int(d[k - 1])
+            lo = max(i[k - 1], dk - lb, la - (n - dk))
+            hi = min(la, dk, i[k - 1] + (dk - dp))
+            i[k] = int(rng.integers(lo, hi + 1)) if hi > lo else lo
+        i = np.array(i, dtype=np.uint64)
+        idx = np.arange(n, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15)
+        arr = orc.arrange(idx[:la], idx[la:], d, i)
+        assert np.array_equal(np.sort(arr), np.sort(idx))
+        for k in range(P):
+            i0, i1 = int(i[k]), int(i[k + 1])
+            j0, j1 = int(d[k]) - i0, int(d[k + 1]) - i1
+            seg = arr[int(d[k]):int(d[k + 1])]
+            assert np.array_equal(seg, np.concatenate([idx[i0:i1], idx[la + j0:la + j1]]))
+
+
 def test_gallop_equals_bsearch_for_every_guess(orc):
     rng = random.Random(2)
     for _ in range(30):
