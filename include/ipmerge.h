@@ -8,7 +8,8 @@
  *                 on the diagonals d_k = floor(k*n/P), k = 0..P, n = len_a + len_b;
  *   2. rearrange  the sRecPar division stage (Alg. 3): level by level, the two middle
  *                 blocks of every pair are exchanged in place (the partition exchange of
- *                 Sec. 3.4), giving A_0 B_0 A_1 B_1 ... A_{P-1} B_{P-1};
+ *                 Sec. 3.4), giving A_0 B_0 A_1 B_1 ... A_{P-1} B_{P-1}; or the same
+ *                 layout by one permutation along its cycles (sOptMov, Alg. 2);
  *   3. merge      every pair (A_k, B_k) is merged stably in place (the per-thread merge
  *                 of Alg. 2/3, here one CTA per pair, staged in shared memory).
  *
@@ -17,10 +18,9 @@
  *     library never allocates or frees device memory; every call that needs scratch
  *     takes a caller-owned workspace sized by the matching *_workspace_bytes query.
  *   - Lengths and offsets count elements, not bytes.
- *   - Calls are asynchronous on their stream.  Merge calls must not run concurrently with
- *     each other on different streams: their persistent kernels size their grids to the
- *     whole GPU and their group barriers need their own CTAs resident (order such calls
- *     with events; copies may overlap them).
+ *   - Merge calls must not run concurrently with each other on different streams: their
+ *     persistent kernels size their grids to the whole GPU and their group barriers need
+ *     their own CTAs resident (order such calls with events; copies may overlap them).
  *   - Keys are compared with the key type's own "<=": signed for IPM_INT32 /
  *     IPM_INT64, unsigned for IPM_UINT32 / IPM_UINT64, IEEE for IPM_FLOAT32 (NaN keys
  *     are not allowed;
@@ -28,8 +28,10 @@
  *   - The merge is stable: equal keys keep their input order, every A element before
  *     every equal B element.  Keys (and payloads) are only moved, never computed, so
  *     the result is bit-exact.
- *   - Calls are asynchronous on `stream` (NULL = the legacy default stream).  Argument
- *     errors detectable on the host return immediately and launch nothing.  Errors
+ *   - Calls are asynchronous on `stream` (NULL = the legacy default stream), except
+ *     the ipm_read_* queries and ipm_rearrange_permute, which synchronise the stream,
+ *     and ipm_timing_read, which waits for the recorded events.
+ *     Argument errors detectable on the host return immediately and launch nothing.  Errors
  *     found on the device (a bounded wait that expired) are recorded in the status
  *     word at the start of the workspace, read with ipm_read_device_status.
  *   - Preconditions that are not checked: both runs are sorted under the comparison
