@@ -9,20 +9,23 @@
 namespace ipm {
 
 int num_sms() {
-    static int cached[64] = {0};
+    static std::atomic<int> cached[64];  // zero-initialised; a racing first call repeats it
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         (void)cudaGetLastError();
         return 1;
     }
-    if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+    if (dev >= 0 && dev < 64) {
+        const int c = cached[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
     int v = 0;
     if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         v <= 0) {
         (void)cudaGetLastError();
         v = 1;
     }
-    if (dev >= 0 && dev < 64) cached[dev] = v;
+    if (dev >= 0 && dev < 64) cached[dev].store(v, std::memory_order_relaxed);
     return v;
 }
 

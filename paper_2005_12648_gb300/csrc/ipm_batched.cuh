@@ -542,14 +542,15 @@ constexpr uint64_t tile_of() {
 
 // Resident CTAs per SM of a kernel, queried once per (kernel, device).
 template <typename F>
-ipm_status occupancy_of(F kern, int threads, size_t smem, int &cache) {
-    if (cache == 0) {
+ipm_status occupancy_of(F kern, int threads, size_t smem, std::atomic<int> &cache,
+                        int &occ) {
+    occ = cache.load(std::memory_order_relaxed);  // set once; a racing first call repeats it
+    if (occ == 0) {
         IPM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           int(smem)));
-        int occ = 0;
         IPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
         if (occ < 1) return IPM_ERR_CUDA;
-        cache = occ;
+        cache.store(occ, std::memory_order_relaxed);
     }
     return IPM_OK;
 }
@@ -565,16 +566,18 @@ ipm_status batched_launch_t(void *buf, uint32_t *vals, uint64_t buf_len, QueueAr
     if (nseg == 0) return IPM_OK;
     // levels: one CTA per multi-tile segment (the prep kernel lists them)
     auto lk = batched_levels_kernel<K, KV>;
-    static int occ_levels = 0;
-    IPM_TRY(occupancy_of(lk, kLevelsThreads, S::kSmem, occ_levels));
+    static std::atomic<int> occ_levels_cache{0};
+    int occ_levels = 0;
+    IPM_TRY(occupancy_of(lk, kLevelsThreads, S::kSmem, occ_levels_cache, occ_levels));
     uint64_t lgrid = uint64_t(occ_levels) * uint64_t(num_sms());
     if (lgrid > nseg) lgrid = nseg;
     lk<<<unsigned(lgrid), kLevelsThreads, S::kSmem, stream>>>((K *)buf, vals, qa, kTile, sb);
     IPM_TRY(last_launch_status());
     // merge: every segment
     auto mk = batched_merge_kernel<K, KV, BT::T, BT::E, BT::MINB>;
-    static int occ_merge = 0;
-    IPM_TRY(occupancy_of(mk, BT::T, Tile::kSmem, occ_merge));
+    static std::atomic<int> occ_merge_cache{0};
+    int occ_merge = 0;
+    IPM_TRY(occupancy_of(mk, BT::T, Tile::kSmem, occ_merge_cache, occ_merge));
     uint32_t per_sm = uint32_t(occ_merge);
     if (ctas_per_sm != 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     uint64_t grid = uint64_t(per_sm) * uint64_t(num_sms());

@@ -660,23 +660,23 @@ __global__ void __launch_bounds__(THREADS, 2)
 
 template <typename K, bool KV, int THREADS, int E, typename V>
 int group_grid() {
-    using Shape = ClusterShape<K, KV, THREADS, E, V>;
-    auto kern = group_merge_kernel<K, KV, THREADS, E, V>;
-    static int cached = -1;
-    if (cached >= 0) return cached;
-    cached = 0;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(Shape::kSmem)) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return cached;
-    }
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, Shape::kSmem) !=
-        cudaSuccess) {
-        (void)cudaGetLastError();
-        per_sm = 0;
-    }
-    cached = per_sm > 0 ? per_sm * num_sms() : 0;
+    // computed by the first call (static initialisation: other threads wait for it)
+    static const int cached = []() -> int {
+        using Shape = ClusterShape<K, KV, THREADS, E, V>;
+        auto kern = group_merge_kernel<K, KV, THREADS, E, V>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(Shape::kSmem)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return 0;
+        }
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS,
+                                                          Shape::kSmem) != cudaSuccess) {
+            (void)cudaGetLastError();
+            per_sm = 0;
+        }
+        return per_sm > 0 ? per_sm * num_sms() : 0;
+    }();
     return cached;
 }
 
@@ -700,36 +700,37 @@ ipm_status group_merge_t(void *buf, void *vals, uint64_t la, uint64_t lb,
 // kernel that allocates TMEM, whatever it allocates; two such CTAs do run side by side.)
 template <typename K, bool KV, typename V>
 int group2_grid() {
-    constexpr int T = ClusterTileOf<K, KV, V>::T;
-    auto kern = group2_merge_kernel<K, KV, V, T, 33>;
-    static int cached = -1;
-    if (cached >= 0) return cached;
-    cached = 0;
-    int dev = 0, regs_sm = 0, smem_sm = 0, threads_sm = 0, reserved = 0;
-    cudaFuncAttributes fa;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(group2_smem<K, KV, V>())) != cudaSuccess ||
-        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             int(cudaSharedmemCarveoutMaxShared)) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) !=
-            cudaSuccess ||
-        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
-            cudaSuccess ||
-        cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) !=
-            cudaSuccess ||
-        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
-            cudaSuccess) {
-        (void)cudaGetLastError();
-        return cached;
-    }
-    const long regs_cta = long(fa.numRegs) * T;
-    const long smem_cta =
-        long(group2_smem<K, KV, V>()) + long(fa.sharedSizeBytes) + long(reserved);
-    long per_sm = threads_sm / T;
-    if (regs_cta > 0 && regs_sm / regs_cta < per_sm) per_sm = regs_sm / regs_cta;
-    if (smem_sm / smem_cta < per_sm) per_sm = smem_sm / smem_cta;
-    cached = per_sm == 2 ? 2 * num_sms() : 0;
+    // computed by the first call (static initialisation: other threads wait for it)
+    static const int cached = []() -> int {
+        constexpr int T = ClusterTileOf<K, KV, V>::T;
+        auto kern = group2_merge_kernel<K, KV, V, T, 33>;
+        int dev = 0, regs_sm = 0, smem_sm = 0, threads_sm = 0, reserved = 0;
+        cudaFuncAttributes fa;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(group2_smem<K, KV, V>())) != cudaSuccess ||
+            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 int(cudaSharedmemCarveoutMaxShared)) != cudaSuccess ||
+            cudaFuncGetAttributes(&fa, kern) != cudaSuccess ||
+            cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) !=
+                cudaSuccess ||
+            cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+                cudaSuccess) {
+            (void)cudaGetLastError();
+            return 0;
+        }
+        const long regs_cta = long(fa.numRegs) * T;
+        const long smem_cta =
+            long(group2_smem<K, KV, V>()) + long(fa.sharedSizeBytes) + long(reserved);
+        long per_sm = threads_sm / T;
+        if (regs_cta > 0 && regs_sm / regs_cta < per_sm) per_sm = regs_sm / regs_cta;
+        if (smem_sm / smem_cta < per_sm) per_sm = smem_sm / smem_cta;
+        return per_sm == 2 ? 2 * num_sms() : 0;
+    }();
     return cached;
 }
 
@@ -773,35 +774,35 @@ ipm_status group2_dispatch(void *buf, void *vals, uint32_t vb, uint64_t la, uint
 // cannot be scheduled), queried once per instantiation.
 template <typename K, bool KV, int THREADS, int E, int C>
 int cluster_capacity() {
-    using Shape = ClusterShape<K, KV, THREADS, E>;
-    auto kern = cluster_merge_kernel<K, KV, THREADS, E, C>;
-    static int cached = -1;
-    if (cached >= 0) return cached;
-    cached = 0;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             int(Shape::kSmem)) != cudaSuccess ||
-        (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                                       1) != cudaSuccess)) {
-        (void)cudaGetLastError();
-        return cached;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = C;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(C * 64, 1, 1);
-    cfg.blockDim = dim3(THREADS, 1, 1);
-    cfg.dynamicSmemBytes = Shape::kSmem;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int mc = 0;
-    if (cudaOccupancyMaxActiveClusters(&mc, kern, &cfg) != cudaSuccess) {
-        (void)cudaGetLastError();
-        mc = 0;
-    }
-    cached = mc > 0 ? mc : 0;
+    // computed by the first call (static initialisation: other threads wait for it)
+    static const int cached = []() -> int {
+        using Shape = ClusterShape<K, KV, THREADS, E>;
+        auto kern = cluster_merge_kernel<K, KV, THREADS, E, C>;
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(Shape::kSmem)) != cudaSuccess ||
+            (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                           1) != cudaSuccess)) {
+            (void)cudaGetLastError();
+            return 0;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(C * 64, 1, 1);
+        cfg.blockDim = dim3(THREADS, 1, 1);
+        cfg.dynamicSmemBytes = Shape::kSmem;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int mc = 0;
+        if (cudaOccupancyMaxActiveClusters(&mc, kern, &cfg) != cudaSuccess) {
+            (void)cudaGetLastError();
+            mc = 0;
+        }
+        return mc > 0 ? mc : 0;
+    }();
     return cached;
 }
 

@@ -1172,7 +1172,8 @@ ipm_status exchange_level_t(void *buf, void *vals, uint64_t n, uint32_t l,
         kern = exchange_level_ws_kernel<E, KV, V>;
     else
         kern = exchange_level_kernel<E, KV>;
-    static int grid = 0;
+    static std::atomic<int> grid_cache{0};  // set once; a racing first call repeats it
+    int grid = grid_cache.load(std::memory_order_relaxed);
     if (grid == 0) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(C::kSmem)) != cudaSuccess) {
@@ -1187,6 +1188,7 @@ ipm_status exchange_level_t(void *buf, void *vals, uint64_t n, uint32_t l,
         }
         if (per_sm < 1) per_sm = 1;
         grid = per_sm * num_sms();
+        grid_cache.store(grid, std::memory_order_relaxed);
     }
     const uint64_t R = 1ull << l;
     const RotPlan *plans = reinterpret_cast<const RotPlan *>(pa.plans) + (R - 1);

@@ -58,15 +58,15 @@ ipm_status tile_merge_t(void *buf, void *vals, uint64_t la, uint64_t lb,
                         const uint64_t *split, uint32_t G, StatusBlock *sb,
                         cudaStream_t stream) {
     using Shape = TileShape<K, KV, THREADS, E, V>;
-    static bool configured = false;
+    static std::atomic<bool> configured{false};  // a racing first call repeats the set-up
     auto kern = tile_merge_kernel<K, KV, THREADS, E, V>;
-    if (!configured) {
+    if (!configured.load(std::memory_order_relaxed)) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(Shape::kSmem)) != cudaSuccess) {
             (void)cudaGetLastError();
             return IPM_ERR_CUDA;
         }
-        configured = true;
+        configured.store(true, std::memory_order_relaxed);
     }
     const uint64_t P = 1ull << G;
     const uint64_t grid = P < uint64_t(num_sms()) ? P : uint64_t(num_sms());
