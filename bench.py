@@ -287,6 +287,32 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------------ our arm
 
+def max_over_ranks(torch, value, world, device):
+    """The largest of every rank's value (the slowest rank's time); the value itself on
+    one rank."""
+    if world <= 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(keys_per_rank, world, ms_per_step):
+    """Whole-job GKeys/s of N replicas: every rank's keys over the slowest rank's time."""
+    return keys_per_rank * world / (ms_per_step * 1e-3) / 1e9
+
+
+def e2e_over_ranks(torch, e2e, world, device):
+    """The end-to-end figure of N replicas (every rank measured its own): every rank's
+    keys over the slowest rank's step time; one rank's figure unchanged."""
+    if e2e is None or world <= 1:
+        return e2e
+    out = dict(e2e)
+    out["ms_per_step"] = max_over_ranks(torch, e2e["ms_per_step"], world, device)
+    out["value"] = job_throughput(e2e["keys_per_step"], world, out["ms_per_step"])
+    return out
+
+
 def timed_steps(torch, stream, steps, prep, call):
     """CUDA-event time (ms) of `call` per step, with `prep` (the input restore) run
     before each step outside the timed interval."""
@@ -692,11 +718,13 @@ def run_form(args, rank, world, torch, ipm, workloads, dev, stream, form):
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
-    ms = m["ms_per_step"]
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, m["ms_per_step"], world, dev)
+    e2e = None
+    if not args.no_e2e and form == "learned":
+        e2e = run_e2e_learned(torch, ipm, m, args.steps, stream, m["model_tensor"])
+    elif not args.no_e2e:
+        e2e = run_e2e_batched(torch, ipm, workloads, m, args.steps, stream, dev)
+    e2e = e2e_over_ranks(torch, e2e, world, dev)
     if rank != 0:
         return None
     dist, dt, la, lb, desc = WORKLOADS[args.workload]
@@ -719,13 +747,9 @@ def run_form(args, rank, world, torch, ipm, workloads, dev, stream, form):
     if not args.no_cpu_baseline:
         v, sample, reps, _ = cpu_oracle_timing(WORKLOADS[args.workload], budget_s=10.0)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
-    e2e = None
-    if not args.no_e2e and form == "learned":
-        e2e = run_e2e_learned(torch, ipm, m, args.steps, stream, m["model_tensor"])
-    elif not args.no_e2e:
-        e2e = run_e2e_batched(torch, ipm, workloads, m, args.steps, stream, dev)
+
     return {
-        "metric": METRIC, "value": n * world / (ms * 1e-3) / 1e9, "unit": UNIT,
+        "metric": METRIC, "value": job_throughput(n, world, ms), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dt,
         "data": "synthetic",
@@ -828,13 +852,9 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
-    total_ms = sum(s.elapsed_time(e) for s, e in evs)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(torch, sum(s.elapsed_time(e) for s, e in evs), world, dev)
     ms_per_step = total_ms / args.steps
-    value = n * world / (ms_per_step * 1e-3) / 1e9
+    value = job_throughput(n, world, ms_per_step)
     if ipm.ipm_read_device_status(ws) != 0:
         raise RuntimeError("device status not OK after the timed steps")
 
@@ -868,6 +888,7 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
         ws2 = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, dt, with_values=vbytes), dev)
         e2e = run_e2e(torch, [pristine, vpristine] if kv else [pristine], args.steps,
                       lambda d, k, st: merge(d[0], d[1] if kv else None, (ws, ws2)[k], st))
+        e2e = e2e_over_ranks(torch, e2e, world, dev)
     del buf, pristine, vbuf, vpristine
 
     if rank != 0:
@@ -956,6 +977,7 @@ def run_e2e(torch, pristines, steps, merge):
     nbytes = sum(p.numel() * p.element_size() for p in pristines)
     return {"value": pristines[0].numel() / (ms * 1e-3) / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": ms,
+            "keys_per_step": pristines[0].numel(),
             "pipelined": "steps alternate between two streams (copy in / copy back overlap)"}
 
 
