@@ -15,6 +15,11 @@
  * type.  The learned split proposer (a 1 -> H -> 1 tanh MLP trained with Adam) has
  * no counterpart in the paper; its float64 forward, backward and Adam step below are
  * the textbook definitions.
+ *
+ * Parity unpinned: FindMedian's balance against the optimal split (the E1 comparison
+ * of Sec. 4) is given by the paper only as a plot, so orc_findmedian and orc_division
+ * with FindMedian pivots are pinned by FindMedian's corner cases and the validity of
+ * its splits, not by the paper's values.
  */
 #include <math.h>
 #include <stddef.h>
