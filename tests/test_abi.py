@@ -36,7 +36,9 @@ def test_header_declares_the_hot_path():
     names = declared_symbols()
     for required in ("ipm_merge_inplace", "ipm_merge_inplace_kv", "ipm_merge_splits",
                      "ipm_merge_rearrange", "ipm_merge_pairs", "ipm_rotate",
-                     "ipm_merge_workspace_bytes", "ipm_read_device_status"):
+                     "ipm_merge_workspace_bytes", "ipm_read_device_status",
+                     "ipm_merge_batched", "ipm_merge_inplace_learned", "ipm_rotate_cs",
+                     "ipm_division_splits", "ipm_rearrange_permute"):
         assert required in names
 
 
