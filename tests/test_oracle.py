@@ -14,7 +14,7 @@ import pytest
 
 import workloads
 
-DTYPES = [np.int32, np.uint32, np.uint64, np.float32]
+DTYPES = [np.int32, np.uint32, np.uint64, np.float32, np.int64]
 
 
 def library_stable_merge(a, b):
@@ -62,13 +62,36 @@ def test_merge_brute_force_all_interleavings(orc, alphabet):
 @pytest.mark.parametrize("dt", DTYPES)
 def test_merge_random_all_dtypes(orc, dt):
     rng = random.Random(5)
+    negatives = 0
     for _ in range(60):
         la, lb = rng.randint(0, 300), rng.randint(0, 300)
         for dist in ("uniform", "dup16"):
             a, b = workloads.make_pair(dist, dt, la, lb, seed=rng.randint(0, 10**6))
+            negatives += int((a < 0).sum() + (b < 0).sum())
             exp = library_stable_merge(a, b)
             got = orc.merge(a, b)
             assert got.tolist() == [t[0] for t in exp]
+    if dt == np.int64:
+        # the signed instantiation must see keys on both sides of zero: an unsigned
+        # comparison would order every negative key after the positive ones
+        assert negatives > 1000
+
+
+def test_merge_brute_force_int64_across_zero(orc):
+    """Every interleaving of keys that straddle zero and both ends of the int64 range:
+    the signed 64-bit instantiation must order them as Python's integers do."""
+    c = np.array([-2**63, -2**40, -7, -1, -1, 0, 3, 2**40, 2**63 - 1], dtype=np.int64)
+    for la in range(c.size + 1):
+        for a, b in interleavings(c, la):
+            exp = library_stable_merge(a, b)
+            assert orc.merge(a, b).tolist() == [t[0] for t in exp]
+            d = np.arange(c.size + 1, dtype=np.uint64)
+            want = np.cumsum([0] + [1 - t[1] for t in exp])
+            assert orc.splits_replay(a, b, d).tolist() == want.tolist()
+            va = np.arange(a.size, dtype=np.uint32)
+            vb = np.arange(a.size, a.size + b.size, dtype=np.uint32)
+            _, v = orc.merge_kv(a, va, b, vb)
+            assert v.tolist() == [t[2] + (a.size if t[1] else 0) for t in exp]
 
 
 def test_float_signed_zero_ties_keep_input_order(orc):
@@ -339,6 +362,38 @@ def test_adam_first_step_closed_form(orc):
     orc.adam_step(p, m, v, g, lr, 0.9, 0.999, eps, 1)
     # first step: mhat = g, vhat = g^2  ->  p - lr * g / (|g| + eps)
     assert np.allclose(p, p0 - lr * g / (np.abs(g) + eps), rtol=1e-12, atol=0)
+
+
+def test_adam_three_steps_worked_by_hand(orc):
+    """Steps 1-3 of Adam with beta1 = 1/2, beta2 = 3/4, lr = 1, eps = 0, worked out by
+    hand.  Bias corrections: 1 - beta1^t = 1/2, 3/4, 7/8 and 1 - beta2^t = 1/4, 7/16,
+    37/64.
+
+    Coordinate 0, gradients 2, -2, 2:
+      t=1  m = 1,    v = 1      mhat = 2,    vhat = 4  -> step  1
+      t=2  m = -1/2, v = 7/4    mhat = -2/3, vhat = 4  -> step -1/3
+      t=3  m = 3/4,  v = 37/16  mhat = 6/7,  vhat = 4  -> step  3/7
+    Coordinate 1, gradients 1, 3, 0:
+      t=1  m = 1/2,  v = 1/4    mhat = 1,    vhat = 1      -> step 1
+      t=2  m = 7/4,  v = 39/16  mhat = 7/3,  vhat = 39/7   -> step (7/3) / sqrt(39/7)
+      t=3  m = 7/8,  v = 117/64 mhat = 1,    vhat = 117/37 -> step 1 / sqrt(117/37)
+    A first moment that forgets its history (m = (1 - beta1) g), a second moment that
+    does, or a step count stuck at 1 changes every step after the first."""
+    p = np.array([10.0, 10.0])
+    m, v = np.zeros(2), np.zeros(2)
+    grads = [np.array([2.0, 1.0]), np.array([-2.0, 3.0]), np.array([2.0, 0.0])]
+    want = [np.array([9.0, 9.0]),
+            np.array([9.0 + 1.0 / 3.0, 9.0 - (7.0 / 3.0) / math.sqrt(39.0 / 7.0)]),
+            np.array([9.0 + 1.0 / 3.0 - 3.0 / 7.0,
+                      9.0 - (7.0 / 3.0) / math.sqrt(39.0 / 7.0) - 1.0 / math.sqrt(117.0 / 37.0)])]
+    want_m = [np.array([1.0, 0.5]), np.array([-0.5, 1.75]), np.array([0.75, 0.875])]
+    want_v = [np.array([1.0, 0.25]), np.array([1.75, 39.0 / 16.0]),
+              np.array([37.0 / 16.0, 117.0 / 64.0])]
+    for t in range(3):
+        orc.adam_step(p, m, v, grads[t], 1.0, 0.5, 0.75, 0.0, t + 1)
+        assert np.allclose(m, want_m[t], rtol=1e-15, atol=0)
+        assert np.allclose(v, want_v[t], rtol=1e-15, atol=0)
+        assert np.allclose(p, want[t], rtol=1e-14, atol=0)
 
 
 # ------------------------------------------------- division balance (Sec. 4, E1)
