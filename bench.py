@@ -184,6 +184,39 @@ def gpu_uuid(torch):
 
 # ------------------------------------------------------------------ accounting
 
+def host_cpu() -> dict:
+    """The host the CPU numbers ran on: its logical CPU count and model name."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:  # noqa: BLE001 - lscpu missing: fall back to /proc/cpuinfo
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu model")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+
+    return {"host_cpus": os.cpu_count(), "cpu_model": model or platform.machine(),
+            "arch": platform.machine()}
+
+
+def spread(times_ms) -> dict:
+    """Median and 10th / 90th percentiles of per-step times (ms)."""
+    q = np.percentile(np.asarray(times_ms, dtype=np.float64), [10, 50, 90])
+    return {"median": float(q[1]), "p10": float(q[0]), "p90": float(q[2]),
+            "n": len(times_ms)}
+
+
 def method_bytes(n: int, w: int) -> dict:
     """Algorithmic bytes of the pair merge (every key read and written once) and of an
     out-of-place merge; the exchange's bytes come from the library after a run."""
@@ -278,7 +311,7 @@ def run_reference(args, rank, world):
         "vs_baseline": None, "dtype": wl[1], "data": "synthetic",
         "config": {"workload": args.workload, "description": wl[4]},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, **host_cpu()},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": time.perf_counter() - t0,
     }
@@ -461,34 +494,47 @@ def measure_learned(torch, ipm, workloads, dev, stream, steps, warmup, P=1 << 16
     same = bool(torch.equal(out, ref))
 
     ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, "float32"), dev)
-    merges = {}
-    for name in ("plain", "learned"):
-        if name == "plain":
-            call = (lambda: ipm.ipm_merge_inplace(buf, la, lb, "float32", ws))
-        else:
-            call = (lambda: ipm.ipm_merge_inplace_learned(buf, la, lb, "float32", model, ws))
-        for _ in range(max(1, warmup)):
+    calls = {"plain": lambda: ipm.ipm_merge_inplace(buf, la, lb, "float32", ws),
+             "learned": lambda: ipm.ipm_merge_inplace_learned(buf, la, lb, "float32", model,
+                                                              ws)}
+    for _ in range(max(1, warmup)):
+        for call in calls.values():
             buf.copy_(pristine)
             call()
-        ipm.ipm_timing_read()
-        ipm.ipm_timing_enable(True)
-        times = timed_steps(torch, stream, steps, lambda: buf.copy_(pristine), call)
-        ipm.ipm_timing_enable(False)
-        ph = ipm.ipm_timing_read().as_dict()
-        if ipm.ipm_read_device_status(ws) != 0:
-            raise RuntimeError(f"learned form ({name}): device status not OK")
-        split_key = "learned_split" if name == "learned" else "split"
-        ms = statistics.median(times)
-        merges[name] = {"ms_per_step": ms, "value": n / (ms * 1e-3) / 1e9,
-                        "split_phase_ms": ph[split_key]["ms"] / steps,
-                        "launches_per_step": sum(v["launches"] for v in ph.values()) // steps}
+    # the two forms alternate step by step on the same buffer, so a drift of the clock
+    # or of the memory system affects both alike
+    times = {"plain": [], "learned": []}
+    split_ms = {"plain": 0.0, "learned": 0.0}
+    launches = {"plain": 0, "learned": 0}
+    for _ in range(steps):
+        for name, call in calls.items():
+            ipm.ipm_timing_read()
+            ipm.ipm_timing_enable(True)
+            times[name] += timed_steps(torch, stream, 1, lambda: buf.copy_(pristine), call)
+            ipm.ipm_timing_enable(False)
+            ph = ipm.ipm_timing_read().as_dict()
+            split_ms[name] += ph["learned_split" if name == "learned" else "split"]["ms"]
+            launches[name] += sum(v["launches"] for v in ph.values())
+            if ipm.ipm_read_device_status(ws) != 0:
+                raise RuntimeError(f"learned form ({name}): device status not OK")
+    merges = {}
+    for name in calls:
+        sp = spread(times[name])
+        merges[name] = {"ms_per_step": sp["median"], "value": n / (sp["median"] * 1e-3) / 1e9,
+                        "step_ms": sp, "split_phase_ms": split_ms[name] / steps,
+                        "launches_per_step": launches[name] // steps}
+    pl, le = merges["plain"]["step_ms"], merges["learned"]["step_ms"]
+    gain = {"median_ratio": pl["median"] / le["median"],
+            "ranges_overlap": not (le["p90"] < pl["p10"] or pl["p90"] < le["p10"]),
+            "split_phase_saved_ms": merges["plain"]["split_phase_ms"] -
+            merges["learned"]["split_phase_ms"]}
     ok_sorted = bool((buf[1:] >= buf[:-1]).all().item())
     return {
         "workload": "c5-float32-learned", "keys": n, "P": P,
         "model": {"hidden": 32, "params": 97, "dtype": "fp32", "train_samples": nsamples,
                   "train_steps": train_steps, "train_ms": train_ms, "train_loss": loss},
         "split": split, "split_speedup": split["plain"]["ms"] / split["learned"]["ms"],
-        "splits_identical": same, "merge": merges,
+        "splits_identical": same, "merge": merges, "end_to_end_gain": gain,
         "value": merges["learned"]["value"], "ms_per_step": merges["learned"]["ms_per_step"],
         "unit": UNIT, "sorted_check": ok_sorted, "buffer": buf, "pristine": pristine,
         "model_tensor": model,
@@ -691,7 +737,7 @@ def run_ours(args, rank, world):
             torch.cuda.empty_cache()
         if form != "learned":
             forms["learned"] = _public(measure_learned(torch, ipm, workloads, dev, stream,
-                                                       steps=5, warmup=1))
+                                                       steps=50, warmup=2))
             torch.cuda.empty_cache()
         forms["rotate"] = measure_rotations(torch, ipm, dev, stream)
         torch.cuda.empty_cache()
@@ -746,7 +792,8 @@ def run_form(args, rank, world, torch, ipm, workloads, dev, stream, form):
     cpu = None
     if not args.no_cpu_baseline:
         v, sample, reps, _ = cpu_oracle_timing(WORKLOADS[args.workload], budget_s=10.0)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               **host_cpu()}
 
     return {
         "metric": METRIC, "value": job_throughput(n, world, ms), "unit": UNIT,
@@ -852,7 +899,8 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
-    total_ms = max_over_ranks(torch, sum(s.elapsed_time(e) for s, e in evs), world, dev)
+    step_times = [s.elapsed_time(e) for s, e in evs]
+    total_ms = max_over_ranks(torch, sum(step_times), world, dev)
     ms_per_step = total_ms / args.steps
     value = job_throughput(n, world, ms_per_step)
     if ipm.ipm_read_device_status(ws) != 0:
@@ -896,11 +944,13 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
     cpu = None
     if not args.no_cpu_baseline:
         v, sample, reps, _ = cpu_oracle_timing(WORKLOADS[args.workload], budget_s=10.0)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               **host_cpu()}
     step_s = ms_per_step * 1e-3
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "step_ms": spread(step_times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": f"{dt} key + {vdt} payload" if kv else dt,
         "data": "synthetic",

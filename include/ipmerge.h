@@ -59,7 +59,9 @@ typedef enum {
     IPM_ERR_WORKSPACE = 4,         /* workspace NULL or smaller than required */
     IPM_ERR_CUDA = 5,              /* a CUDA runtime call or launch failed */
     IPM_ERR_TIMEOUT = 6,           /* a bounded device-side wait expired */
-    IPM_ERR_DEVICE = 7             /* the device found an inconsistent state */
+    IPM_ERR_DEVICE = 7             /* the device found an inconsistent state; or (no-alloc
+                                      merge) the buffer or stream is not on the current
+                                      device */
 } ipm_status;
 
 typedef enum {
@@ -298,6 +300,23 @@ ipm_status ipm_set_fused_engine(uint32_t engine);
 ipm_status ipm_set_exchange_engine(uint32_t engine);
 
 /*
+ * Limit, in nanoseconds of GPU wall time, of the waits in which a CTA of a merge call
+ * waits for another CTA's progress: the "reads done" flags and step joins of the
+ * exchange levels (Sec. 3.4 executed by many CTAs) and the group barrier of the fused
+ * bottom levels.  Process-wide, read when a merge call (ipm_merge_inplace, _kv,
+ * _learned, _noalloc) is issued; 0 restores the default of 2 s; at most 2 s, else
+ * IPM_ERR_INVALID_ARG.  When such a wait runs out, the kernel records IPM_ERR_TIMEOUT in
+ * the call's status word (ipm_read_device_status) and leaves without finishing its
+ * work, the call's later kernels skip theirs, and the buffer's contents are
+ * unspecified; the device stays usable.  Waits for a CTA's own bulk copies
+ * always keep the 2 s limit, so no copy into a CTA's shared memory is in flight when it
+ * leaves.  A short limit exists to test this path; normal use keeps the default.
+ * ipm_get_wait_limit_ns reports the limit in effect.
+ */
+ipm_status ipm_set_wait_limit_ns(uint64_t ns);
+ipm_status ipm_get_wait_limit_ns(uint64_t *ns);
+
+/*
  * Batched segmented merge: many independent in-place merges in one call.
  * Segment t of the table is the problem of Sec. 1 on its own slice of the buffer:
  * A = d_buf[offset, offset + len_a) and B = d_buf[offset + len_a, offset + len_a +
@@ -367,6 +386,60 @@ ipm_status ipm_merge_batched(void *d_buf, void *d_vals, uint64_t buf_len,
                              const ipm_segment *d_segs, uint32_t nseg, ipm_dtype key_dtype,
                              ipm_dtype val_dtype, const ipm_batched_options *opt,
                              void *d_ws, size_t ws_bytes, ipm_stream_t stream);
+
+/*
+ * Autotuner of ipm_merge_batched.  The paper has no counterpart: every option set gives
+ * the same result, and the tuner picks the fastest for a given segment table.  It times
+ * each candidate (the three merge tiles, which also fix the pair count P = 2^G of every
+ * segment longer than one tile; full and reduced resident CTAs per SM; both queue
+ * orders; IPM_TUNE_MAX_CANDIDATES at most) and the defaults, each as the median of
+ * `reps` runs (1 <= reps <= 100) after one warm-up run, with CUDA events on `stream`.
+ * Every run first restores d_scratch (and d_scratch_vals) from d_buf (and d_vals), so
+ * the caller's input is only read; the scratch buffers hold buf_len elements each and
+ * end up merged.  d_ws holds ipm_merge_batched_tune_workspace_bytes(...) bytes.
+ *
+ * Cache: the choice is stored under a signature of the workload (key type, payload
+ * width, and floor(log2) of the segment count, of the total length, of the longest and
+ * of the median segment; ipm_batched_tune_signature computes it from a host copy of the
+ * table) in a text file: cache_path, or when cache_path is NULL the file named by the
+ * environment variable IPM_TUNE_CACHE, or no cache when neither is set (an empty string
+ * disables it too).  A signature found there is returned without timing anything
+ * (from_cache = 1; with h_segs given, without any CUDA call).  h_segs is an optional host
+ * copy of the table; when NULL the table is copied from d_segs.  The call synchronises
+ * `stream` and blocks the host thread while it times.  Errors: IPM_ERR_INVALID_ARG (NULL
+ * out, reps, a scratch pointer missing, or no option set that merges every segment),
+ * IPM_ERR_UNSUPPORTED_DTYPE (payloads other than IPM_UINT32), IPM_ERR_WORKSPACE, and the
+ * errors of ipm_merge_batched.
+ */
+#define IPM_TUNE_MAX_CANDIDATES 16
+typedef struct {
+    ipm_batched_options options;
+    float ms;       /* median time of the candidate */
+    uint32_t pad;
+} ipm_batched_tune_entry;
+
+typedef struct {
+    ipm_batched_options best;  /* the fastest option set (from the cache: the stored one) */
+    float best_ms;             /* its median time (from the cache: the stored time) */
+    float default_ms;          /* the defaults' median time; negative when not timed or
+                                  when the defaults refuse a segment of the table */
+    uint32_t candidates;       /* option sets timed (0 when the cache answered) */
+    uint32_t from_cache;       /* 1: read from the cache file, nothing timed */
+    uint64_t signature;        /* the workload's cache key */
+    ipm_batched_tune_entry table[IPM_TUNE_MAX_CANDIDATES];  /* every timed candidate */
+} ipm_batched_tune_result;
+
+ipm_status ipm_merge_batched_tune_workspace_bytes(uint64_t buf_len, uint32_t nseg,
+                                                  ipm_dtype key_dtype, int with_values,
+                                                  size_t *bytes);
+ipm_status ipm_batched_tune_signature(const ipm_segment *h_segs, uint32_t nseg,
+                                      ipm_dtype key_dtype, int with_values, uint64_t *out);
+ipm_status ipm_merge_batched_tune(const void *d_buf, const void *d_vals, uint64_t buf_len,
+                                  const ipm_segment *d_segs, const ipm_segment *h_segs,
+                                  uint32_t nseg, ipm_dtype key_dtype, ipm_dtype val_dtype,
+                                  void *d_scratch, void *d_scratch_vals, void *d_ws,
+                                  size_t ws_bytes, uint32_t reps, const char *cache_path,
+                                  ipm_batched_tune_result *out, ipm_stream_t stream);
 
 /*
  * Algorithmic bytes the pair merges of the last batched call that used this workspace
@@ -487,6 +560,17 @@ ipm_status ipm_merge_inplace_learned(void *d_buf, uint64_t len_a, uint64_t len_b
  */
 ipm_status ipm_merge_inplace_noalloc(void *d_buf, uint64_t len_a, uint64_t len_b,
                                      ipm_dtype key_dtype, ipm_stream_t stream);
+
+/*
+ * Device rule and status of ipm_merge_inplace_noalloc.  The array exists once per
+ * device, so the call needs d_buf to be memory of the CURRENT device and `stream` a
+ * stream of that device (NULL: the current device's legacy stream); otherwise it returns
+ * IPM_ERR_DEVICE and launches nothing (a host pointer gives the same answer).
+ * ipm_read_noalloc_status reads the device status word (IPM_OK, IPM_ERR_TIMEOUT or
+ * IPM_ERR_DEVICE) that the last no-alloc call on the current device left in the array;
+ * it synchronises `stream`.  Before the first no-alloc call on a device it reads IPM_OK.
+ */
+ipm_status ipm_read_noalloc_status(ipm_stream_t stream, ipm_status *out);
 
 /*
  * Optional per-phase timing (for benchmarks).  When enabled on a host thread, the

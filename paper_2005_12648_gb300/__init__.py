@@ -28,9 +28,12 @@ __all__ = [
     "ipm_read_device_status",
     "ipm_read_exchange_bytes",
     "ipm_timing_enable", "ipm_timing_read", "IpmTiming", "ipm_merge_inplace_noalloc",
+    "ipm_read_noalloc_status", "ipm_set_wait_limit_ns", "ipm_get_wait_limit_ns",
     "workspace", "merge_inplace", "merge_inplace_kv",
     "IpmBatchedOptions", "ipm_merge_batched_workspace_bytes", "ipm_merge_batched_max_segment",
     "ipm_merge_batched", "ipm_read_merge_bytes", "segment_table", "merge_batched",
+    "IpmBatchedTuneResult", "ipm_merge_batched_tune_workspace_bytes",
+    "ipm_batched_tune_signature", "ipm_merge_batched_tune",
     "IpmSplitModel", "IpmSplitTrainOptions", "IpmSplitStats", "SPLIT_MODEL_HIDDEN",
     "ipm_split_model_train_workspace_bytes", "ipm_split_model_train", "ipm_split_model_forward",
     "ipm_split_model_loss_grad", "ipm_merge_splits_learned", "ipm_merge_inplace_learned",
@@ -79,12 +82,19 @@ _SIGS = {
     "ipm_division_splits": (_i, [_vp, _u64, _u64, _i, _u32, _u32, _vp, _vp, _vp]),
     "ipm_read_device_status": (_i, [_vp, _vp, ctypes.POINTER(_i)]),
     "ipm_merge_inplace_noalloc": (_i, [_vp, _u64, _u64, _i, _vp]),
+    "ipm_read_noalloc_status": (_i, [_vp, ctypes.POINTER(_i)]),
+    "ipm_set_wait_limit_ns": (_i, [_u64]),
+    "ipm_get_wait_limit_ns": (_i, [ctypes.POINTER(_u64)]),
     "ipm_timing_enable": (_i, [_i]),
     "ipm_timing_read": (_i, [ctypes.c_void_p]),
     "ipm_merge_batched_workspace_bytes": (_i, [_u64, _u32, _i, _i, _vp, ctypes.POINTER(_sz)]),
     "ipm_merge_batched_max_segment": (_i, [_i, _i, _vp, ctypes.POINTER(_u64)]),
     "ipm_merge_batched": (_i, [_vp, _vp, _u64, _vp, _u32, _i, _i, _vp, _vp, _sz, _vp]),
     "ipm_read_merge_bytes": (_i, [_vp, _vp, ctypes.POINTER(_u64)]),
+    "ipm_merge_batched_tune_workspace_bytes": (_i, [_u64, _u32, _i, _i, ctypes.POINTER(_sz)]),
+    "ipm_batched_tune_signature": (_i, [_vp, _u32, _i, _i, ctypes.POINTER(_u64)]),
+    "ipm_merge_batched_tune": (_i, [_vp, _vp, _u64, _vp, _vp, _u32, _i, _i, _vp, _vp, _vp, _sz,
+                                    _u32, ctypes.c_char_p, _vp, _vp]),
     "ipm_split_model_train_workspace_bytes": (_i, [_u32, ctypes.POINTER(_sz)]),
     "ipm_split_model_train": (_i, [_vp, _u64, _u64, _i, _vp, _u32, _vp, _vp, _vp, _sz, _vp]),
     "ipm_split_model_forward": (_i, [_vp, _vp, _u32, _vp, _vp]),
@@ -354,6 +364,25 @@ def ipm_merge_inplace_noalloc(buf, len_a: int, len_b: int, key_dtype, stream=Non
                                             _stream(stream)), "ipm_merge_inplace_noalloc")
 
 
+def ipm_read_noalloc_status(stream=None) -> int:
+    """Device status the last no-alloc merge on the current device left (0 = IPM_OK)."""
+    out = _i(0)
+    _check(load().ipm_read_noalloc_status(_stream(stream), ctypes.byref(out)),
+           "ipm_read_noalloc_status")
+    return int(out.value)
+
+
+def ipm_set_wait_limit_ns(ns: int) -> None:
+    """Limit of the merge calls' waits on other CTAs (0 = the default, 2 s)."""
+    _check(load().ipm_set_wait_limit_ns(int(ns)), "ipm_set_wait_limit_ns")
+
+
+def ipm_get_wait_limit_ns() -> int:
+    out = _u64(0)
+    _check(load().ipm_get_wait_limit_ns(ctypes.byref(out)), "ipm_get_wait_limit_ns")
+    return int(out.value)
+
+
 def ipm_timing_enable(enable: bool = True) -> None:
     _check(load().ipm_timing_enable(int(bool(enable))), "ipm_timing_enable")
 
@@ -373,6 +402,29 @@ class IpmBatchedOptions(ctypes.Structure):
     def as_dict(self):
         return {"tile": int(self.tile), "ctas_per_sm": int(self.ctas_per_sm),
                 "order": int(self.order)}
+
+
+TUNE_MAX_CANDIDATES = 16
+
+
+class IpmBatchedTuneEntry(ctypes.Structure):
+    _fields_ = [("options", IpmBatchedOptions), ("ms", ctypes.c_float), ("pad", ctypes.c_uint32)]
+
+
+class IpmBatchedTuneResult(ctypes.Structure):
+    """Mirror of ipm_batched_tune_result."""
+    _fields_ = [("best", IpmBatchedOptions), ("best_ms", ctypes.c_float),
+                ("default_ms", ctypes.c_float), ("candidates", ctypes.c_uint32),
+                ("from_cache", ctypes.c_uint32), ("signature", ctypes.c_uint64),
+                ("table", IpmBatchedTuneEntry * TUNE_MAX_CANDIDATES)]
+
+    def as_dict(self):
+        k = min(int(self.candidates), TUNE_MAX_CANDIDATES)
+        return {"best": self.best.as_dict(), "best_ms": float(self.best_ms),
+                "default_ms": float(self.default_ms), "candidates": int(self.candidates),
+                "from_cache": bool(self.from_cache), "signature": f"{self.signature:016x}",
+                "table": [{**self.table[i].options.as_dict(), "ms": float(self.table[i].ms)}
+                          for i in range(k)]}
 
 
 def _opts(options) -> "IpmBatchedOptions | None":
@@ -549,6 +601,55 @@ def merge_inplace_kv(keys, vals, len_a: int, len_b: int, key_dtype, log2_pairs: 
     ipm_merge_inplace_kv(keys, vals, len_a, len_b, key_dtype, ws, val_dtype=val_dtype,
                          log2_pairs=log2_pairs, stream=stream)
     return ws
+
+
+def ipm_merge_batched_tune_workspace_bytes(buf_len: int, nseg: int, key_dtype,
+                                           with_values: bool = False) -> int:
+    out = _sz(0)
+    _check(load().ipm_merge_batched_tune_workspace_bytes(buf_len, nseg, _dt(key_dtype),
+                                                         int(bool(with_values)),
+                                                         ctypes.byref(out)),
+           "ipm_merge_batched_tune_workspace_bytes")
+    return int(out.value)
+
+
+def _host_segments(h_segs):
+    """A C-contiguous host uint64 [nseg, 3] copy of a segment table (or None)."""
+    if h_segs is None:
+        return None
+    import numpy as np
+    return np.ascontiguousarray(np.asarray(h_segs, dtype=np.int64).reshape(-1, 3)
+                                .view(np.uint64))
+
+
+def ipm_batched_tune_signature(h_segs, key_dtype, with_values: bool = False) -> str:
+    """The autotuner's cache key of a host segment table ([nseg, 3] offset, len_a, len_b)."""
+    hs = _host_segments(h_segs)
+    out = _u64(0)
+    _check(load().ipm_batched_tune_signature(hs.ctypes.data if hs.size else None, hs.shape[0],
+                                             _dt(key_dtype), int(bool(with_values)),
+                                             ctypes.byref(out)), "ipm_batched_tune_signature")
+    return f"{out.value:016x}"
+
+
+def ipm_merge_batched_tune(buf, vals, buf_len: int, segs, nseg: int, key_dtype, scratch,
+                           ws, scratch_vals=None, reps: int = 5, cache_path=None,
+                           h_segs=None, val_dtype="uint32", ws_bytes: int | None = None,
+                           stream=None) -> dict:
+    """Time the candidate option sets of ipm_merge_batched on `scratch` (restored from
+    buf before every run) and return the fastest (see ipm_merge_batched_tune in the
+    header); the dict holds the chosen options, both times and every candidate's."""
+    res = IpmBatchedTuneResult()
+    hs = _host_segments(h_segs)
+    wsb = (_nbytes(ws) if ws is not None else 0) if ws_bytes is None else ws_bytes
+    path = cache_path.encode() if isinstance(cache_path, str) else cache_path
+    _check(load().ipm_merge_batched_tune(
+        _ptr(buf), _ptr(vals), buf_len, _ptr(segs),
+        hs.ctypes.data if hs is not None and hs.size else None, nseg, _dt(key_dtype),
+        _dt(val_dtype), _ptr(scratch), _ptr(scratch_vals), _ptr(ws), wsb, reps, path,
+        ctypes.addressof(res), _stream(stream) if buf is not None else None),
+        "ipm_merge_batched_tune")
+    return res.as_dict()
 
 
 def segment_table(offsets, len_a, len_b, device=None):

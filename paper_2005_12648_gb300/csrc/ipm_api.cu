@@ -92,6 +92,8 @@ constexpr uint32_t kMaxLog2Pairs = 22;
 // and how the groups synchronise: 0 = thread-block clusters (F <= 4), 1 = group
 // barriers in global memory (ipm_set_fused_engine).
 uint32_t g_fused_levels = 10;  // as many as the engine can (8 or 9 on GB300)
+// Limit of the merge calls' waits on other CTAs (ipm_set_wait_limit_ns; 0 = 2 s).
+std::atomic<unsigned long long> g_wait_limit_ns{0};
 uint32_t g_fused_engine = 2;  // TMEM two-pairs kernel where it applies, else 1
 
 bool valid_key(ipm_dtype t) {
@@ -210,7 +212,8 @@ ipm_status merge_core(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t 
     {
         PhaseScope ps(model ? 6 : 0, 2, stream);
         // a0: early exit (A empty, B empty, or A[last] <= B[0]) -> later steps are no-ops
-        IPM_TRY(launch_early_exit(buf, la, lb, key, sb, stream));
+        IPM_TRY(launch_early_exit(buf, la, lb, key, sb,
+                                  g_wait_limit_ns.load(std::memory_order_relaxed), stream));
         // a1: exact stable splits on every diagonal (from the model's proposals when one
         // is given: the same splits)
         if (model != nullptr)
@@ -656,6 +659,19 @@ ipm_status ipm_set_fused_levels(uint32_t levels) {
 ipm_status ipm_get_fused_levels(uint32_t *levels) {
     if (levels == nullptr) return IPM_ERR_INVALID_ARG;
     *levels = g_fused_levels;
+    return IPM_OK;
+}
+
+ipm_status ipm_set_wait_limit_ns(uint64_t ns) {
+    if (ns > kWaitLimitNs) return IPM_ERR_INVALID_ARG;
+    g_wait_limit_ns.store(ns, std::memory_order_relaxed);
+    return IPM_OK;
+}
+
+ipm_status ipm_get_wait_limit_ns(uint64_t *ns) {
+    if (ns == nullptr) return IPM_ERR_INVALID_ARG;
+    const unsigned long long v = g_wait_limit_ns.load(std::memory_order_relaxed);
+    *ns = v ? v : kWaitLimitNs;
     return IPM_OK;
 }
 

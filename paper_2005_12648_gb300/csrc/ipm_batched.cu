@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(kPrepThreads)
         sb->done = 0u;
         sb->exchange_bytes = 0ull;
         sb->merge_bytes = 0ull;
+        sb->wait_limit_ns = 0ull;  // the batched kernels do not wait on other CTAs
         for (int q = 0; q < kNumCounters; ++q) sb->counters[q] = 0u;
         nmulti = 0;
     }

@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(THREADS, 2)
     __shared__ int abort_flag;
     __shared__ uint32_t s_t[2];
     __shared__ PairGeo<K, V> pgs[2];  // the current pair and the next one
-    if (sb == nullptr || *((volatile unsigned int *)&sb->done)) return;
+    if (sb == nullptr || call_finished(sb)) return;
     const uint32_t tid = threadIdx.x;
     const uint64_t P = 1ull << G;
     const uint32_t gsize = 1u << F;
@@ -376,19 +376,12 @@ __global__ void __launch_bounds__(THREADS, 2)
         // ---- group barrier: the group's region may be written once every member has
         // its slices on chip
         if (tid == 0 && !abort_flag) {
-            unsigned long long t0 = 0;
-            uint32_t it = 0;
-            while (ld_acquire_u32(ctr) < gsize) {
-                if ((++it & 63u) == 0) {
-                    const unsigned long long now = globaltimer_ns();
-                    if (t0 == 0)
-                        t0 = now;
-                    else if (now - t0 > kWaitLimitNs) {
-                        abort_flag = 1;
-                        break;
-                    }
+            DepTimer tm(wait_limit(sb));
+            while (ld_acquire_u32(ctr) < gsize)
+                if (tm.expired()) {
+                    abort_flag = 1;
+                    break;
                 }
-            }
         }
         __syncthreads();
         if (abort_flag) {
@@ -463,7 +456,7 @@ __global__ void __launch_bounds__(THREADS, 2)
     __shared__ int abort_flag;
     __shared__ uint32_t s_t[2], s_taddr;
     __shared__ PairGeo<K, V> pgs[2][2];  // [current / next claim][first / second pair]
-    if (sb == nullptr || *((volatile unsigned int *)&sb->done)) return;
+    if (sb == nullptr || call_finished(sb)) return;
     const uint32_t tid = threadIdx.x, warp = tid >> 5;
     const uint64_t claims = (1ull << G) >> 1;
     const uint32_t gsize = 1u << (F - 1);  // claims per group
@@ -582,19 +575,12 @@ __global__ void __launch_bounds__(THREADS, 2)
         // its slices on chip
         if (tid == 0 && !abort_flag) {
             const uint32_t *ctr = gctr + (*((volatile uint32_t *)&s_t[cur]) >> (F - 1));
-            unsigned long long t0 = 0;
-            uint32_t it = 0;
-            while (ld_acquire_u32(ctr) < gsize) {
-                if ((++it & 63u) == 0) {
-                    const unsigned long long now = globaltimer_ns();
-                    if (t0 == 0)
-                        t0 = now;
-                    else if (now - t0 > kWaitLimitNs) {
-                        abort_flag = 1;
-                        break;
-                    }
+            DepTimer tm(wait_limit(sb));
+            while (ld_acquire_u32(ctr) < gsize)
+                if (tm.expired()) {
+                    abort_flag = 1;
+                    break;
                 }
-            }
         }
         __syncthreads();
         if (abort_flag) {

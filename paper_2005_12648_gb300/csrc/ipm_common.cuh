@@ -22,16 +22,18 @@ __device__ __forceinline__ bool key_le(K x, K y) { return x <= y; }
 //   done            early-exit flag: nonzero when the runs are already in order
 //   exchange_bytes  algorithmic bytes of the exchange levels of the current call
 //   merge_bytes     algorithmic bytes of the pair merges (batched calls only)
+//   wait_limit_ns   limit of this call's waits on other CTAs (0: kWaitLimitNs)
 //   counters        per-call ticket counters of the persistent kernels
 // All of it is reset at the start of every call.
 // ---------------------------------------------------------------------------------
-constexpr int kNumCounters = 58;
+constexpr int kNumCounters = 56;
 
 struct StatusBlock {
     unsigned int status;
     unsigned int done;
     unsigned long long exchange_bytes;
     unsigned long long merge_bytes;
+    unsigned long long wait_limit_ns;
     unsigned int counters[kNumCounters];
 };
 
@@ -50,8 +52,44 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-// Upper bound for every device-side wait (mbarrier, flags): 2 s of wall time.
+// Upper bound for every device-side wait (mbarrier, flags): 2 s of wall time.  Waits
+// on another CTA's progress (flags, joins, group barriers) use the call's own limit
+// (wait_limit below), which defaults to this; waits for this CTA's own bulk copies
+// always use this one, so a CTA never leaves with a copy into its shared memory in
+// flight.
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+// The limit of this call's waits on other CTAs.
+__device__ __forceinline__ unsigned long long wait_limit(const StatusBlock *sb) {
+    if (sb == nullptr) return kWaitLimitNs;
+    const unsigned long long v = *((volatile const unsigned long long *)&sb->wait_limit_ns);
+    return v ? v : kWaitLimitNs;
+}
+
+// True when the call this kernel belongs to needs no more work: the runs were already
+// in order (early exit) or an earlier kernel of the call recorded an error.
+__device__ __forceinline__ bool call_finished(const StatusBlock *sb) {
+    if (sb == nullptr) return false;
+    const volatile StatusBlock *v = sb;
+    return v->done != 0u || v->status != 0u;
+}
+
+// Clock of a wait on another CTA: call expired() after every poll that found the
+// condition unmet.  The clock starts at the first failed poll and is read again every
+// 8th one; expired() turns true once more than `lim` ns have passed.
+struct DepTimer {
+    unsigned long long t0, lim;
+    uint32_t it;
+    __device__ __forceinline__ explicit DepTimer(unsigned long long l) : t0(0), lim(l), it(0) {}
+    __device__ __forceinline__ bool expired() {
+        ++it;
+        if (it == 1) {
+            t0 = globaltimer_ns();
+            return false;
+        }
+        return (it & 7u) == 0 && globaltimer_ns() - t0 > lim;
+    }
+};
 
 // ---------------------------------------------------------------------------------
 // Small host helpers.

@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(kPlanThreads)
     xplan_levels_kernel(const uint64_t *__restrict__ split, uint64_t n, uint32_t G,
                         XPlanArea pa, XParams prm, uint32_t hcap, uint32_t elem,
                         StatusBlock *sb) {
-    if (sb != nullptr && *((volatile const unsigned int *)&sb->done)) return;
+    if (call_finished(sb)) return;
     const uint32_t l = blockIdx.x;
     prm.max_holders = level_holders(l, hcap);
     const uint64_t R = 1ull << l;
@@ -161,19 +161,11 @@ __device__ __forceinline__ uint32_t ld_flag(const uint32_t *p) {
     return v;
 }
 
-// Thread 0: wait until *ctr >= target.  False on timeout.
-__device__ bool wait_count(const uint32_t *ctr, uint32_t target) {
-    unsigned long long t0 = 0;
-    uint32_t it = 0;
-    while (ld_acquire(ctr) < target) {
-        if ((++it & 63u) == 0) {
-            const unsigned long long now = globaltimer_ns();
-            if (t0 == 0)
-                t0 = now;
-            else if (now - t0 > kWaitLimitNs)
-                return false;
-        }
-    }
+// Thread 0: wait until *ctr >= target.  False after `lim` ns.
+__device__ bool wait_count(const uint32_t *ctr, uint32_t target, unsigned long long lim) {
+    DepTimer tm(lim);
+    while (ld_acquire(ctr) < target)
+        if (tm.expired()) return false;
     return true;
 }
 
@@ -240,22 +232,15 @@ struct Shared {
 __device__ bool wait_flag_range_poll(const uint32_t *flags, uint32_t lo, uint32_t hi,
                                      uint32_t tag, bool nxt_loaded, bool nxt_flag,
                                      uint64_t *nbar, uint32_t nparity, uint32_t *my_flag,
-                                     bool &published) {
-    unsigned long long t0 = 0;
+                                     bool &published, unsigned long long lim) {
+    DepTimer tm(lim);
     for (uint32_t q = lo; q <= hi && lo <= hi; ++q) {
-        uint32_t it = 0;
         while (ld_flag(flags + q) < tag) {
             if (nxt_loaded && nxt_flag && !published && mbar_try_wait(nbar, nparity)) {
                 st_flag(my_flag, tag);
                 published = true;
             }
-            if ((++it & 63u) == 0) {
-                const unsigned long long now = globaltimer_ns();
-                if (t0 == 0)
-                    t0 = now;
-                else if (now - t0 > kWaitLimitNs)
-                    return false;
-            }
+            if (tm.expired()) return false;
         }
     }
     return true;
@@ -584,7 +569,8 @@ __global__ void __launch_bounds__(512, 1)
     extern __shared__ __align__(128) unsigned char xsmem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(xsmem + 2 * C::kStageSize);
     __shared__ Shared sh;
-    if (sb != nullptr && *((volatile unsigned int *)&sb->done)) return;
+    if (call_finished(sb)) return;
+    const unsigned long long lim = wait_limit(sb);
     XParams prm = C::params();
     prm.max_holders = holders;
     const uint32_t tid = threadIdx.x;
@@ -620,7 +606,7 @@ __global__ void __launch_bounds__(512, 1)
         // ---- the current item's earlier LS steps must be complete before it loads
         if (!cur_loaded) {
             if (cur.before > 0) {
-                if (tid == 0 && !wait_count(join + cur.r, cur.before)) {
+                if (tid == 0 && !wait_count(join + cur.r, cur.before, lim)) {
                     set_status(sb, IPM_ERR_TIMEOUT);
                     sh.abort = 1;
                 }
@@ -670,11 +656,11 @@ __global__ void __launch_bounds__(512, 1)
             const uint32_t np = cs ? parity0 : parity1;
             bool ok = wait_flag_range_poll(flags, cur.dp.lo0, cur.dp.hi0, tag, nxt_loaded,
                                            nxt.flag, &bar[cs ^ 1], np, flags + nxt_t,
-                                           nxt_flag_done);
+                                           nxt_flag_done, lim);
             if (ok)
                 ok = wait_flag_range_poll(flags, cur.dp.lo1, cur.dp.hi1, tag, nxt_loaded,
                                           nxt.flag, &bar[cs ^ 1], np, flags + nxt_t,
-                                          nxt_flag_done);
+                                          nxt_flag_done, lim);
             if (!ok) {
                 set_status(sb, IPM_ERR_TIMEOUT);
                 sh.abort = 1;
@@ -907,7 +893,8 @@ struct WsShared {
 // False on timeout.
 __device__ bool ws_wait_deps(const uint32_t *flags, uint32_t lo, uint32_t hi, uint32_t tag,
                              uint64_t *nbar, uint32_t nparity, const WsShared *sh,
-                             uint32_t ns, uint32_t *wflags, bool &next_pub) {
+                             uint32_t ns, uint32_t *wflags, bool &next_pub,
+                             unsigned long long lim) {
     auto poll_next = [&]() {
         if (!next_pub && mbar_try_wait(nbar, nparity)) {
             const volatile WsShared *v = sh;
@@ -916,18 +903,11 @@ __device__ bool ws_wait_deps(const uint32_t *flags, uint32_t lo, uint32_t hi, ui
         }
     };
     poll_next();
-    unsigned long long t0 = 0;
+    DepTimer tm(lim);
     for (uint32_t q = lo; q <= hi && lo <= hi; ++q) {
-        uint32_t it = 0;
         while (ld_flag(flags + q) < tag) {
             poll_next();
-            if ((++it & 63u) == 0) {
-                const unsigned long long now = globaltimer_ns();
-                if (t0 == 0)
-                    t0 = now;
-                else if (now - t0 > kWaitLimitNs)
-                    return false;
-            }
+            if (tm.expired()) return false;
         }
     }
     return true;
@@ -945,7 +925,8 @@ __global__ void __launch_bounds__(512, 1)
     uint64_t *full = reinterpret_cast<uint64_t *>(xsmem + 2 * C::kStageSize);
     uint64_t *empty = full + 2;
     __shared__ WsShared sh;
-    if (sb != nullptr && *((volatile unsigned int *)&sb->done)) return;
+    if (call_finished(sb)) return;
+    const unsigned long long lim = wait_limit(sb);
     const uint32_t tid = threadIdx.x;
     const uint32_t total = pf[nrot];
     if (tid == 0) {
@@ -989,6 +970,11 @@ __global__ void __launch_bounds__(512, 1)
                     unsigned long long t0 = 0;
                     for (uint32_t i = 0;; ++i) {
                         if (mbar_try_wait(&empty[q], drained[q] & 1u)) break;
+                        // the consumers left (an error): nothing will be released
+                        if (*((volatile int *)&sh.abort)) {
+                            ok = false;
+                            break;
+                        }
                         try_publish();
                         if ((i & 255u) == 0) {
                             const unsigned long long now = globaltimer_ns();
@@ -1053,7 +1039,7 @@ __global__ void __launch_bounds__(512, 1)
             bool ok = !it.single || drain(st ^ 1u);
             if (ok && it.before > 0) {
                 bool w = true;
-                if (lane == 0) w = wait_count(join + it.r, it.before);
+                if (lane == 0) w = wait_count(join + it.r, it.before, lim);
                 ok = __shfl_sync(0xffffffffu, w, 0) != 0;
             }
             if (!ok) {
@@ -1104,7 +1090,8 @@ __global__ void __launch_bounds__(512, 1)
     for (;;) {
         if (lead) {
             int stop = 0;
-            if (!mbar_wait_bounded(&full[st], fullph[st])) {
+            // (the producer may leave on an error without marking the stage's end)
+            if (!mbar_wait_or_abort(&full[st], fullph[st], &sh.abort)) {
                 set_status(sb, IPM_ERR_TIMEOUT);
                 sh.abort = 1;
                 stop = 1;
@@ -1125,10 +1112,10 @@ __global__ void __launch_bounds__(512, 1)
             const uint32_t ns = st ^ 1u;
             bool next_pub = false;
             bool w = ws_wait_deps(flags, it.dp.lo0, it.dp.hi0, tag, &full[ns], fullph[ns], &sh,
-                                  ns, flags, next_pub);
+                                  ns, flags, next_pub, lim);
             if (w)
                 w = ws_wait_deps(flags, it.dp.lo1, it.dp.hi1, tag, &full[ns], fullph[ns], &sh,
-                                 ns, flags, next_pub);
+                                 ns, flags, next_pub, lim);
             cur_pub = next_pub;
             int stop = 0;
             if (!w) {

@@ -27,10 +27,11 @@ uint64_t tile_capacity(ipm_dtype key, uint32_t vb);
 
 // ---- launchers (all asynchronous on `stream`; return IPM_ERR_CUDA on launch failure)
 
-// Resets the status block and sets its early-exit flag when A is empty, B is empty
-// or A[last] <= B[0].
+// Resets the status block, stores the call's limit for waits on other CTAs (0: the
+// default) and sets the early-exit flag when A is empty, B is empty or A[last] <= B[0].
 ipm_status launch_early_exit(const void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
-                             StatusBlock *sb, cudaStream_t stream);
+                             StatusBlock *sb, unsigned long long wait_limit_ns,
+                             cudaStream_t stream);
 
 // Exact stable splits on d_k = floor(k*n/P), k = 0..P.  sb may be NULL.
 ipm_status launch_splits(const void *buf, uint64_t la, uint64_t lb, ipm_dtype key,

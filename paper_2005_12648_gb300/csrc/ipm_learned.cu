@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256)
         if (threadIdx.x < uint32_t(kNP)) prm[threadIdx.x] = model_params(model)[threadIdx.x];
         __syncthreads();
     }
-    if (sb != nullptr && *((volatile const unsigned int *)&sb->done)) return;
+    if (call_finished(sb)) return;
     const uint64_t k = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const unsigned lane = threadIdx.x & 31u;
     if (k > P) return;  // whole warp exits together

@@ -9,7 +9,8 @@ namespace ipm {
 namespace {
 
 template <typename K>
-__global__ void early_exit_kernel(const K *buf, uint64_t la, uint64_t lb, StatusBlock *sb) {
+__global__ void early_exit_kernel(const K *buf, uint64_t la, uint64_t lb, StatusBlock *sb,
+                                  unsigned long long wait_limit_ns) {
     if (threadIdx.x == 0) {
         unsigned int done = (la == 0 || lb == 0) ? 1u : 0u;
         if (!done) done = key_le(buf[la - 1], buf[la]) ? 1u : 0u;
@@ -17,6 +18,7 @@ __global__ void early_exit_kernel(const K *buf, uint64_t la, uint64_t lb, Status
         sb->done = done;
         sb->exchange_bytes = 0ull;
         sb->merge_bytes = 0ull;
+        sb->wait_limit_ns = wait_limit_ns;
         for (int q = 0; q < kNumCounters; ++q) sb->counters[q] = 0u;
     }
 }
@@ -26,7 +28,7 @@ __global__ void __launch_bounds__(256) split_kernel(const K *__restrict__ A, uin
                                                     const K *__restrict__ B, uint64_t lb,
                                                     uint64_t P, uint64_t *__restrict__ out,
                                                     const StatusBlock *sb) {
-    if (sb != nullptr && *((volatile const unsigned int *)&sb->done)) return;
+    if (call_finished(sb)) return;
     const uint64_t k = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const unsigned lane = threadIdx.x & 31u;
     if (k > P) return;  // whole warp exits together
@@ -50,22 +52,28 @@ ipm_status splits_t(const void *buf, uint64_t la, uint64_t lb, uint64_t P, uint6
 }  // namespace
 
 ipm_status launch_early_exit(const void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
-                             StatusBlock *sb, cudaStream_t stream) {
+                             StatusBlock *sb, unsigned long long wait_limit_ns,
+                             cudaStream_t stream) {
     switch (key) {
     case IPM_INT32:
-        early_exit_kernel<int32_t><<<1, 32, 0, stream>>>((const int32_t *)buf, la, lb, sb);
+        early_exit_kernel<int32_t><<<1, 32, 0, stream>>>((const int32_t *)buf, la, lb, sb,
+                                                         wait_limit_ns);
         break;
     case IPM_UINT32:
-        early_exit_kernel<uint32_t><<<1, 32, 0, stream>>>((const uint32_t *)buf, la, lb, sb);
+        early_exit_kernel<uint32_t><<<1, 32, 0, stream>>>((const uint32_t *)buf, la, lb, sb,
+                                                         wait_limit_ns);
         break;
     case IPM_UINT64:
-        early_exit_kernel<uint64_t><<<1, 32, 0, stream>>>((const uint64_t *)buf, la, lb, sb);
+        early_exit_kernel<uint64_t><<<1, 32, 0, stream>>>((const uint64_t *)buf, la, lb, sb,
+                                                         wait_limit_ns);
         break;
     case IPM_INT64:
-        early_exit_kernel<int64_t><<<1, 32, 0, stream>>>((const int64_t *)buf, la, lb, sb);
+        early_exit_kernel<int64_t><<<1, 32, 0, stream>>>((const int64_t *)buf, la, lb, sb,
+                                                         wait_limit_ns);
         break;
     case IPM_FLOAT32:
-        early_exit_kernel<float><<<1, 32, 0, stream>>>((const float *)buf, la, lb, sb);
+        early_exit_kernel<float><<<1, 32, 0, stream>>>((const float *)buf, la, lb, sb,
+                                                         wait_limit_ns);
         break;
     default:
         return IPM_ERR_UNSUPPORTED_DTYPE;

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     __shared__ int abort_flag;
     K *skeys = reinterpret_cast<K *>(smem_raw + 128);
     V *svals = reinterpret_cast<V *>(smem_raw + 128 + Shape::kKeyBytes);
-    if (sb != nullptr && *((volatile unsigned int *)&sb->done)) return;
+    if (call_finished(sb)) return;
 
     const uint32_t tid = threadIdx.x;
     const uint64_t n = la + lb;

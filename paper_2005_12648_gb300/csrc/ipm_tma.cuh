@@ -67,6 +67,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     }
 }
 
+// Wait for the mbarrier phase with the given parity, giving up early when *abort turns
+// nonzero (another role of the CTA left).  False on abort or after kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity,
+                                                   const int *abort) {
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*((const volatile int *)abort)) return false;
+        if ((it & 255u) == 0) {
+            const unsigned long long now = globaltimer_ns();
+            if (t0 == 0)
+                t0 = now;
+            else if (now - t0 > kWaitLimitNs)
+                return false;
+        }
+    }
+}
+
 // Global -> shared bulk copy; completion counted in bytes on the mbarrier.
 // Both addresses 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_load(void *smem_dst, const void *gsrc, uint32_t bytes,

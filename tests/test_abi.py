@@ -85,6 +85,35 @@ def test_host_queries(lib):
         assert m.ipm_rotate_cs_workspace_bytes(lx, ly, 8) <= 256 + 8 * (1 << 19)
 
 
+def test_noalloc_limit_fits_its_fixed_scratch(lib):
+    """The no-alloc merge serves up to 2^15 pairs from an 8 MiB array: at the largest
+    size it accepts (2^15 full tiles) the plan has exactly 2^15 pairs and the workspace
+    the merge needs fits the array, for 4- and 8-byte keys; one key more needs 2^16."""
+    L, m = lib
+    for dt in ("int32", "uint64"):
+        _, tile = m.ipm_merge_plan(1, 1, dt)
+        n = (1 << 15) * tile
+        G, _ = m.ipm_merge_plan(n // 2, n - n // 2, dt)
+        assert G == 15
+        assert m.ipm_merge_workspace_bytes(n // 2, n - n // 2, dt) <= 8 << 20
+        G1, _ = m.ipm_merge_plan(n // 2, n - n // 2 + 1, dt)
+        assert G1 == 16
+        # refused on the host, before any device call: a fake address is never touched
+        assert L.ipm_merge_inplace_noalloc(0x1000, n // 2, n - n // 2 + 1,
+                                           m.DTYPES[dt], None) == 1
+
+
+def test_wait_limit_setting(lib):
+    L, m = lib
+    assert m.ipm_get_wait_limit_ns() == 2_000_000_000
+    m.ipm_set_wait_limit_ns(5_000)
+    assert m.ipm_get_wait_limit_ns() == 5_000
+    m.ipm_set_wait_limit_ns(0)  # back to the default
+    assert m.ipm_get_wait_limit_ns() == 2_000_000_000
+    assert L.ipm_set_wait_limit_ns(2_000_000_001) == 1
+    assert m.ipm_get_wait_limit_ns() == 2_000_000_000
+
+
 def test_argument_errors_return_before_any_cuda_call(lib):
     L, m = lib
     null = None

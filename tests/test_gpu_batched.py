@@ -207,3 +207,43 @@ def test_batched_fullsize_20000_segments(ipm, dev, orc, opt):
         o, x, y = int(offs[s]), int(la[s]), int(lb[s])
         want = orc.merge(host[o:o + x], host[o + x:o + x + y])
         assert first_diff(got[o:o + x + y], want) is None, s
+
+
+@pytest.mark.parametrize("kv", [False, True])
+def test_autotuned_options_match_oracle(ipm, dev, orc, kv, tmp_path):
+    """The autotuner times every candidate option set on a scratch copy (the input is
+    only read), picks one, caches it; a merge with the pick equals the oracle segment
+    by segment, and a second tuning call is answered from the cache."""
+    import torch
+
+    la, lb, _ = W.batched_lengths(nseg=600, total_cap=1 << 23, seed=4)
+    buf, offs = W.batched_buffer(la, lb, seed=4)
+    segs = list(zip(offs.tolist(), la.tolist(), lb.tolist()))
+    vals = np.arange(buf.size, dtype=np.uint32) if kv else None
+    d = to_dev(buf, dev)
+    dv = None if vals is None else torch.from_numpy(vals.view(np.int32).copy()).to(dev)
+    scratch = torch.empty_like(d)
+    svals = None if dv is None else torch.empty_like(dv)
+    st = ipm.segment_table(offs.astype(np.int64), la, lb, dev)
+    ws = ipm.workspace(ipm.ipm_merge_batched_tune_workspace_bytes(buf.size, len(segs), "int32",
+                                                                  kv), dev)
+    cache = str(tmp_path / "tune.txt")
+    res = ipm.ipm_merge_batched_tune(d, dv, buf.size, st, len(segs), "int32", scratch, ws,
+                                     scratch_vals=svals, reps=3, cache_path=cache)
+    assert not res["from_cache"] and res["candidates"] >= 8
+    assert res["best_ms"] > 0 and res["default_ms"] > 0
+    assert res["best_ms"] <= min(e["ms"] for e in res["table"]) + 1e-6
+    torch.cuda.synchronize()
+    assert torch.equal(d, to_dev(buf, dev))  # the input was only read
+    want, wv = _expected(orc, buf, segs, vals)
+    # the scratch copy holds the last candidate's merge: already the right answer
+    assert np.array_equal(from_dev(scratch, np.int32), want)
+    got, gv, status, _ = _run(ipm, dev, buf, segs, np.int32, vals, options=res["best"])
+    assert status == 0
+    assert first_diff(got, want) is None
+    if kv:
+        assert np.array_equal(gv, wv)
+    again = ipm.ipm_merge_batched_tune(d, dv, buf.size, st, len(segs), "int32", scratch, ws,
+                                       scratch_vals=svals, reps=3, cache_path=cache)
+    assert again["from_cache"] and again["best"] == res["best"]
+    assert again["signature"] == res["signature"]
