@@ -361,11 +361,12 @@ def timed_steps(torch, stream, steps, prep, call):
 
 
 def measure_batched(torch, ipm, workloads, dev, stream, steps, warmup, options=None,
-                    loop_segments=500):
+                    loop_segments=None, tune=True):
     """The batched form: 20,000 int32 segments (2^28 keys) merged by one
-    ipm_merge_batched call per step; also replayed as a captured CUDA graph, and
-    compared with a loop of ipm_merge_inplace calls over the first loop_segments
-    segments."""
+    ipm_merge_batched call per step; also replayed as a captured CUDA graph, compared
+    with a loop of ipm_merge_inplace calls over the segments (all of them unless
+    loop_segments is given), and, when tune is set, timed again with the option set
+    the library's autotuner picks for this table."""
     la, lb, emax = workloads.batched_lengths()
     pristine, offs = workloads.batched_buffer_torch(torch, la, lb, 0, dev)
     n = pristine.numel()
@@ -416,8 +417,37 @@ def measure_batched(torch, ipm, workloads, dev, stream, steps, warmup, options=N
                          for o, x, y in zip(offs[:64].tolist(), la[:64].tolist(),
                                             lb[:64].tolist())))
 
+    # the autotuner's pick for this table (timed on `buf` as scratch, no cache file),
+    # then timed like the defaults
+    autotuned = None
+    if tune:
+        tws = ipm.workspace(ipm.ipm_merge_batched_tune_workspace_bytes(n, la.size, "int32"), dev)
+        t0 = time.perf_counter()
+        res = ipm.ipm_merge_batched_tune(pristine, None, n, segs, la.size, "int32", buf, tws,
+                                         reps=5, cache_path="")
+        tune_s = time.perf_counter() - t0
+        best = res["best"]
+        twsb = ipm.workspace(ipm.ipm_merge_batched_workspace_bytes(n, la.size, "int32", False,
+                                                                   best), dev)
+
+        def tcall():
+            ipm.ipm_merge_batched(buf, None, n, segs, la.size, "int32", twsb, options=best)
+
+        for _ in range(max(1, warmup)):
+            prep()
+            tcall()
+        ttimes = timed_steps(torch, stream, steps, prep, tcall)
+        if ipm.ipm_read_device_status(twsb) != 0:
+            raise RuntimeError("batched (autotuned options): device status not OK")
+        tms = statistics.median(ttimes)
+        autotuned = {"options": best, "ms_per_step": tms, "value": n / (tms * 1e-3) / 1e9,
+                     "step_ms": spread(ttimes), "default_ms_per_step": ms,
+                     "gain_over_default": ms / tms, "tuning_s": tune_s,
+                     "search": {k: res[k] for k in ("candidates", "best_ms", "default_ms",
+                                                    "table", "signature")}}
+
     # baseline: one ipm_merge_inplace call per segment, on the first segments
-    K = min(loop_segments, la.size)
+    K = la.size if loop_segments is None else min(loop_segments, la.size)
     kkeys = int((la[:K] + lb[:K]).sum())
     wsp = ipm.workspace(ipm.ipm_merge_workspace_bytes(int(la[:K].max()), int(lb[:K].max()),
                                                       "int32"), dev)
@@ -426,7 +456,7 @@ def measure_batched(torch, ipm, workloads, dev, stream, steps, warmup, options=N
         for o, x, y in zip(offs[:K].tolist(), la[:K].tolist(), lb[:K].tolist()):
             ipm.ipm_merge_inplace(buf[o:], x, y, "int32", wsp)
 
-    loop_ms = statistics.median(timed_steps(torch, stream, 3, prep, loop))
+    loop_ms = statistics.median(timed_steps(torch, stream, 2, prep, loop))
     peak, _ = peaks()
     min_b = 2 * n * 4
     return {
@@ -434,6 +464,7 @@ def measure_batched(torch, ipm, workloads, dev, stream, steps, warmup, options=N
         "e_max": round(float(emax), 4), "max_segment": int((la + lb).max()),
         "options": options or {"tile": 0, "order": 0, "ctas_per_sm": 0},
         "ms_per_step": ms, "value": n / (ms * 1e-3) / 1e9, "unit": UNIT,
+        "step_ms": spread(times), "autotuned": autotuned,
         "graph_ms_per_step": statistics.median(gtimes),
         "graph_value": n / (statistics.median(gtimes) * 1e-3) / 1e9,
         "launches_per_step": ph["launches"] // max(1, steps),

@@ -335,14 +335,18 @@ typedef struct {
  *                3 = quarter tile (four CTAs per SM);
  *   ctas_per_sm  0 = as many as fit, else at most this many resident CTAs per SM;
  *   order        0 = work queue in segment-size order, largest first; 1 = table order;
- *   reserved     must be 0.
+ *   form         0 = library default (1), 1 = three launches (queue preparation by one
+ *                CTA, then the exchange levels of every long segment, then the pair
+ *                merges), 2 = one launch (a memset node clears the call's counters, then
+ *                one persistent kernel prepares the queue with many CTAs and does each
+ *                segment whole: early exit, splits, exchange levels, pair merges).
  * Every option changes only the speed, never the result.
  */
 typedef struct {
     uint32_t tile;
     uint32_t ctas_per_sm;
     uint32_t order;
-    uint32_t reserved;
+    uint32_t form;
 } ipm_batched_options;
 
 /*
@@ -379,8 +383,9 @@ ipm_status ipm_merge_batched_max_segment(ipm_dtype key_dtype, int with_values,
  * work queues.  A segment that leaves the buffer or is longer than
  * ipm_merge_batched_max_segment is left untouched and the device status becomes
  * IPM_ERR_INVALID_ARG (ipm_read_device_status).  The call launches three kernels
- * (queue preparation, levels, merge), performs no host synchronisation and no
- * allocation, so it can be captured in a CUDA graph.
+ * (queue preparation, levels, merge), or in the one-launch form a memset node and one
+ * kernel; it performs no host synchronisation and no allocation, so it can be captured
+ * in a CUDA graph.
  */
 ipm_status ipm_merge_batched(void *d_buf, void *d_vals, uint64_t buf_len,
                              const ipm_segment *d_segs, uint32_t nseg, ipm_dtype key_dtype,
@@ -390,9 +395,10 @@ ipm_status ipm_merge_batched(void *d_buf, void *d_vals, uint64_t buf_len,
 /*
  * Autotuner of ipm_merge_batched.  The paper has no counterpart: every option set gives
  * the same result, and the tuner picks the fastest for a given segment table.  It times
- * each candidate (the three merge tiles, which also fix the pair count P = 2^G of every
- * segment longer than one tile; full and reduced resident CTAs per SM; both queue
- * orders; IPM_TUNE_MAX_CANDIDATES at most) and the defaults, each as the median of
+ * each candidate (both launch forms; the three merge tiles, which also fix the pair
+ * count P = 2^G of every segment longer than one tile; full and reduced resident CTAs
+ * per SM; both queue orders; IPM_TUNE_MAX_CANDIDATES at most) and the defaults, each as
+ * the median of
  * `reps` runs (1 <= reps <= 100) after one warm-up run, with CUDA events on `stream`.
  * Every run first restores d_scratch (and d_scratch_vals) from d_buf (and d_vals), so
  * the caller's input is only read; the scratch buffers hold buf_len elements each and
@@ -411,7 +417,7 @@ ipm_status ipm_merge_batched(void *d_buf, void *d_vals, uint64_t buf_len,
  * IPM_ERR_UNSUPPORTED_DTYPE (payloads other than IPM_UINT32), IPM_ERR_WORKSPACE, and the
  * errors of ipm_merge_batched.
  */
-#define IPM_TUNE_MAX_CANDIDATES 16
+#define IPM_TUNE_MAX_CANDIDATES 32
 typedef struct {
     ipm_batched_options options;
     float ms;       /* median time of the candidate */

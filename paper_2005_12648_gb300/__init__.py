@@ -395,16 +395,17 @@ def ipm_timing_read(into: "IpmTiming | None" = None) -> IpmTiming:
 
 class IpmBatchedOptions(ctypes.Structure):
     """Mirror of ipm_batched_options (tile 0 = default, 1 wide, 2 narrow, 3 quarter;
-    order 0 = largest segment first, 1 = table order; ctas_per_sm 0 = as many as fit)."""
+    order 0 = largest segment first, 1 = table order; ctas_per_sm 0 = as many as fit;
+    form 0 = default, 1 = three launches, 2 = one launch)."""
     _fields_ = [("tile", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("order", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("order", ctypes.c_uint32), ("form", ctypes.c_uint32)]
 
     def as_dict(self):
         return {"tile": int(self.tile), "ctas_per_sm": int(self.ctas_per_sm),
-                "order": int(self.order)}
+                "order": int(self.order), "form": int(self.form)}
 
 
-TUNE_MAX_CANDIDATES = 16
+TUNE_MAX_CANDIDATES = 32
 
 
 class IpmBatchedTuneEntry(ctypes.Structure):
@@ -431,7 +432,7 @@ def _opts(options) -> "IpmBatchedOptions | None":
     if options is None or isinstance(options, IpmBatchedOptions):
         return options
     return IpmBatchedOptions(int(options.get("tile", 0)), int(options.get("ctas_per_sm", 0)),
-                             int(options.get("order", 0)), 0)
+                             int(options.get("order", 0)), int(options.get("form", 0)))
 
 
 def ipm_merge_batched_workspace_bytes(buf_len: int, nseg: int, key_dtype,

@@ -126,15 +126,19 @@ ipm_status check_merge_args(uint64_t la, uint64_t lb, ipm_dtype key, uint32_t vb
 }
 
 // Kernel variant of a batched options struct (NULL = defaults): 0 wide, 1 narrow,
-// 2 quarter tile.
+// 2 quarter tile; and whether the one-launch form runs.
 constexpr uint32_t kDefaultBatchedVariant = 1;
+constexpr uint32_t kDefaultBatchedOneLaunch = 0;
 
-ipm_status batched_variant(const ipm_batched_options *opt, uint32_t *variant) {
+ipm_status batched_variant(const ipm_batched_options *opt, uint32_t *variant,
+                           uint32_t *one_launch = nullptr) {
     *variant = kDefaultBatchedVariant;
+    if (one_launch) *one_launch = kDefaultBatchedOneLaunch;
     if (opt == nullptr) return IPM_OK;
-    if (opt->tile > 3 || opt->order > 1 || opt->reserved != 0 || opt->ctas_per_sm > 64)
+    if (opt->tile > 3 || opt->order > 1 || opt->form > 2 || opt->ctas_per_sm > 64)
         return IPM_ERR_INVALID_ARG;
     *variant = opt->tile == 0 ? kDefaultBatchedVariant : opt->tile - 1;
+    if (one_launch && opt->form != 0) *one_launch = opt->form == 2 ? 1u : 0u;
     return IPM_OK;
 }
 
@@ -530,8 +534,8 @@ ipm_status ipm_merge_batched(void *d_buf, void *d_vals, uint64_t buf_len,
                              const ipm_segment *d_segs, uint32_t nseg, ipm_dtype key_dtype,
                              ipm_dtype val_dtype, const ipm_batched_options *opt,
                              void *d_ws, size_t ws_bytes, ipm_stream_t stream) {
-    uint32_t variant = 0;
-    IPM_TRY(batched_variant(opt, &variant));
+    uint32_t variant = 0, one_launch = 0;
+    IPM_TRY(batched_variant(opt, &variant, &one_launch));
     if (!valid_key(key_dtype)) return IPM_ERR_UNSUPPORTED_DTYPE;
     const bool kv = d_vals != nullptr;
     if (kv && val_dtype != IPM_UINT32) return IPM_ERR_UNSUPPORTED_DTYPE;
@@ -548,9 +552,9 @@ ipm_status ipm_merge_batched(void *d_buf, void *d_vals, uint64_t buf_len,
     cudaStream_t st = (cudaStream_t)stream;
     const uint32_t by_size = (opt == nullptr || opt->order == 0) ? 1u : 0u;
     const uint32_t per_sm = opt ? opt->ctas_per_sm : 0u;
-    PhaseScope ps(4, 3, st);
+    PhaseScope ps(4, nseg == 0 ? 0u : one_launch ? 1u : 3u, st);
     return launch_batched(d_buf, static_cast<uint32_t *>(d_vals), buf_len, key_dtype, d_segs,
-                          nseg, d_ws, L, by_size, variant, per_sm, st);
+                          nseg, d_ws, L, by_size, variant, per_sm, one_launch, st);
 }
 
 ipm_status ipm_split_model_train_workspace_bytes(uint32_t nsamples, size_t *bytes) {

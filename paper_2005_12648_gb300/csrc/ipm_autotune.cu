@@ -9,9 +9,9 @@
 // the workload (key type, payload width and coarse size statistics of the segment
 // table), so a later call with a similar table reads it instead of timing again.
 //
-// Cache file format: one line per signature, "ipmtune1 <signature hex> <tile>
-// <ctas_per_sm> <order> <ms>"; unknown or malformed lines are ignored, and a new choice
-// is appended.
+// Cache file format: one line per signature, "ipmtune2 <signature hex> <tile>
+// <ctas_per_sm> <order> <form> <ms>"; unknown or malformed lines are ignored, and a new
+// choice is appended.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -69,14 +69,15 @@ bool cache_lookup(const char *path, uint64_t sig, ipm_batched_options *opt, floa
     bool found = false;
     while (std::fgets(line, sizeof(line), f)) {
         unsigned long long s = 0;
-        unsigned t = 0, c = 0, o = 0;
+        unsigned t = 0, c = 0, o = 0, fm = 0;
         float m = 0.f;
-        if (std::sscanf(line, "ipmtune1 %llx %u %u %u %f", &s, &t, &c, &o, &m) != 5) continue;
-        if (s != sig || t > 3 || c > 64 || o > 1) continue;
+        if (std::sscanf(line, "ipmtune2 %llx %u %u %u %u %f", &s, &t, &c, &o, &fm, &m) != 6)
+            continue;
+        if (s != sig || t > 3 || c > 64 || o > 1 || fm > 2) continue;
         opt->tile = t;
         opt->ctas_per_sm = c;
         opt->order = o;
-        opt->reserved = 0;
+        opt->form = fm;
         *ms = m;
         found = true;  // the last matching line wins
     }
@@ -88,8 +89,8 @@ void cache_append(const char *path, uint64_t sig, const ipm_batched_options &opt
     std::lock_guard<std::mutex> lock(g_tune_file_mutex);
     FILE *f = std::fopen(path, "a");
     if (f == nullptr) return;  // an unwritable cache only costs a later re-tune
-    std::fprintf(f, "ipmtune1 %016llx %u %u %u %.6f\n", (unsigned long long)sig, opt.tile,
-                 opt.ctas_per_sm, opt.order, double(ms));
+    std::fprintf(f, "ipmtune2 %016llx %u %u %u %u %.6f\n", (unsigned long long)sig, opt.tile,
+                 opt.ctas_per_sm, opt.order, opt.form, double(ms));
     std::fclose(f);
 }
 
@@ -99,22 +100,24 @@ const char *cache_path_of(const char *arg) {
     return (env != nullptr && env[0]) ? env : nullptr;
 }
 
-// The candidate option sets: every tile, each at its full occupancy and at fewer
-// resident CTAs per SM, each with both queue orders.
+// The candidate option sets: both launch forms, every tile, each at its full occupancy
+// and at fewer resident CTAs per SM, each with both queue orders.
 std::vector<ipm_batched_options> candidates() {
     std::vector<ipm_batched_options> v;
     const uint32_t per_sm[3][2] = {{0, 0}, {0, 1}, {0, 2}};  // wide, narrow, quarter
-    for (uint32_t t = 1; t <= 3; ++t)
-        for (uint32_t c = 0; c < 2; ++c) {
-            if (c == 1 && per_sm[t - 1][1] == 0) continue;
-            for (uint32_t o = 0; o <= 1; ++o) {
-                ipm_batched_options op{};
-                op.tile = t;
-                op.ctas_per_sm = per_sm[t - 1][c];
-                op.order = o;
-                v.push_back(op);
+    for (uint32_t fm = 1; fm <= 2; ++fm)
+        for (uint32_t t = 1; t <= 3; ++t)
+            for (uint32_t c = 0; c < 2; ++c) {
+                if (c == 1 && per_sm[t - 1][1] == 0) continue;
+                for (uint32_t o = 0; o <= 1; ++o) {
+                    ipm_batched_options op{};
+                    op.tile = t;
+                    op.ctas_per_sm = per_sm[t - 1][c];
+                    op.order = o;
+                    op.form = fm;
+                    v.push_back(op);
+                }
             }
-        }
     return v;
 }
 

@@ -5,29 +5,26 @@
 namespace ipm {
 
 ipm_status batched_launch_i32(void *, uint32_t *, uint64_t, batched::QueueArea, uint32_t,
-                              uint32_t, uint32_t, StatusBlock *, cudaStream_t);
+                              uint32_t, uint32_t, uint32_t, const ipm_segment *, uint32_t,
+                              StatusBlock *, cudaStream_t);
 ipm_status batched_launch_u32(void *, uint32_t *, uint64_t, batched::QueueArea, uint32_t,
-                              uint32_t, uint32_t, StatusBlock *, cudaStream_t);
+                              uint32_t, uint32_t, uint32_t, const ipm_segment *, uint32_t,
+                              StatusBlock *, cudaStream_t);
 ipm_status batched_launch_u64(void *, uint32_t *, uint64_t, batched::QueueArea, uint32_t,
-                              uint32_t, uint32_t, StatusBlock *, cudaStream_t);
+                              uint32_t, uint32_t, uint32_t, const ipm_segment *, uint32_t,
+                              StatusBlock *, cudaStream_t);
 ipm_status batched_launch_f32(void *, uint32_t *, uint64_t, batched::QueueArea, uint32_t,
-                              uint32_t, uint32_t, StatusBlock *, cudaStream_t);
+                              uint32_t, uint32_t, uint32_t, const ipm_segment *, uint32_t,
+                              StatusBlock *, cudaStream_t);
 ipm_status batched_launch_i64(void *, uint32_t *, uint64_t, batched::QueueArea, uint32_t,
-                              uint32_t, uint32_t, StatusBlock *, cudaStream_t);
+                              uint32_t, uint32_t, uint32_t, const ipm_segment *, uint32_t,
+                              StatusBlock *, cudaStream_t);
 
 namespace {
 
 using namespace batched;
 
 constexpr uint32_t kPrepThreads = 1024;
-constexpr uint32_t kOrderBuckets = 256;  // 4 per octave of the segment length
-
-// Bucket of a segment of n >= 1 elements: 4 * floor(log2 n) + the next two bits.
-__device__ __forceinline__ uint32_t size_bucket(uint64_t n) {
-    const uint32_t lg = 63u - uint32_t(__clzll(n));
-    const uint32_t frac = lg >= 2 ? uint32_t(n >> (lg - 2)) & 3u : uint32_t(n << (2 - lg)) & 3u;
-    return (lg << 2) | frac;
-}
 
 constexpr uint32_t kPrepBatch = 8;  // descriptors in flight per thread
 constexpr uint32_t kPrepWarps = kPrepThreads / 32;
@@ -201,12 +198,14 @@ uint64_t batched_max_segment(ipm_dtype key, bool with_values, uint32_t variant) 
     return uint64_t(kMaxPairs) * batched_tile(key, with_values, variant);
 }
 
-// Workspace layout: status block | queue | multi | soff | split pool.  The pool holds
-// every multi-tile segment's P + 1 splits; P < 2 n / tile, so for segments that do not
-// overlap 2 (buf_len / tile + 1) + nseg entries suffice.
+// Workspace layout: status block | bucket counts and cursors (one-launch form) | queue |
+// multi | soff | split pool.  The pool holds every multi-tile segment's P + 1 splits;
+// P < 2 n / tile, so for segments that do not overlap 2 (buf_len / tile + 1) + nseg
+// entries suffice.
 BatchedLayout batched_layout(uint64_t buf_len, uint32_t nseg, uint64_t tile) {
     BatchedLayout L;
-    L.queue_off = kStatusBytes;
+    L.hist_off = kStatusBytes;
+    L.queue_off = L.hist_off + 2 * sizeof(uint32_t) * kOrderBuckets;
     L.multi_off = L.queue_off + align_up(sizeof(ipm_segment) * size_t(nseg), 256);
     L.soff_off = L.multi_off + align_up(sizeof(uint32_t) * size_t(nseg), 256);
     L.pool_off = L.soff_off + align_up(sizeof(uint32_t) * size_t(nseg), 256);
@@ -218,7 +217,7 @@ BatchedLayout batched_layout(uint64_t buf_len, uint32_t nseg, uint64_t tile) {
 ipm_status launch_batched(void *buf, uint32_t *vals, uint64_t buf_len, ipm_dtype key,
                           const ipm_segment *segs, uint32_t nseg, void *ws,
                           const BatchedLayout &L, uint32_t by_size, uint32_t variant,
-                          uint32_t ctas_per_sm, cudaStream_t stream) {
+                          uint32_t ctas_per_sm, uint32_t one_launch, cudaStream_t stream) {
     char *w = static_cast<char *>(ws);
     StatusBlock *sb = reinterpret_cast<StatusBlock *>(w);
     QueueArea qa;
@@ -227,27 +226,35 @@ ipm_status launch_batched(void *buf, uint32_t *vals, uint64_t buf_len, ipm_dtype
     qa.soff = reinterpret_cast<uint32_t *>(w + L.soff_off);
     qa.pool = reinterpret_cast<uint64_t *>(w + L.pool_off);
     qa.pool_cap = L.pool_cap;
+    qa.hist = reinterpret_cast<uint32_t *>(w + L.hist_off);
+    qa.cursor = qa.hist + kOrderBuckets;
     const uint64_t tile = batched_tile(key, vals != nullptr, variant);
-    batched_prep_kernel<<<1, kPrepThreads, 0, stream>>>(
-        segs, nseg, by_size, buf_len, tile, batched_max_segment(key, vals != nullptr, variant),
-        qa, sb);
-    IPM_TRY(last_launch_status());
+    if (one_launch) {
+        // the status block, its counters and the bucket counts start at zero; every other
+        // area is written before it is read
+        IPM_CUDA_TRY(cudaMemsetAsync(w, 0, L.queue_off, stream));
+    } else {
+        batched_prep_kernel<<<1, kPrepThreads, 0, stream>>>(
+            segs, nseg, by_size, buf_len, tile,
+            batched_max_segment(key, vals != nullptr, variant), qa, sb);
+        IPM_TRY(last_launch_status());
+    }
     switch (key) {
     case IPM_INT32:
-        return batched_launch_i32(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm, sb,
-                                  stream);
+        return batched_launch_i32(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm,
+                                  one_launch, segs, by_size, sb, stream);
     case IPM_UINT32:
-        return batched_launch_u32(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm, sb,
-                                  stream);
+        return batched_launch_u32(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm,
+                                  one_launch, segs, by_size, sb, stream);
     case IPM_UINT64:
-        return batched_launch_u64(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm, sb,
-                                  stream);
+        return batched_launch_u64(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm,
+                                  one_launch, segs, by_size, sb, stream);
     case IPM_FLOAT32:
-        return batched_launch_f32(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm, sb,
-                                  stream);
+        return batched_launch_f32(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm,
+                                  one_launch, segs, by_size, sb, stream);
     case IPM_INT64:
-        return batched_launch_i64(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm, sb,
-                                  stream);
+        return batched_launch_i64(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm,
+                                  one_launch, segs, by_size, sb, stream);
     }
     return IPM_ERR_UNSUPPORTED_DTYPE;
 }

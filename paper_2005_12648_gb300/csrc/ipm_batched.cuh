@@ -18,6 +18,14 @@
 //           and takes its early-exit test on the staged copy.
 // Keeping the exchange code out of the merge kernel keeps the merge loop free of
 // register spills.
+//
+// The same work also runs as ONE persistent launch (batched_fused_kernel, the "one
+// launch" form of the options): after a memset node clears the status block and the
+// queue counters, CTAs take tickets in order -- the first tickets build the size
+// histogram of the table chunk by chunk, the next ones scatter the descriptors into
+// size order (each waits, bounded, for every histogram chunk), and every later ticket is
+// one segment, done whole by its CTA (early exit, splits, exchange levels, pair merges).
+// Every wait is on an earlier ticket, held by a running CTA, so none can deadlock.
 #pragma once
 
 #include "ipm_exchange.cuh"
@@ -68,7 +76,18 @@ struct QueueArea {
     uint32_t *soff;      // [nseg] per queue position: split-table offset in the pool
     uint64_t *pool;      // [cap] split tables
     uint64_t pool_cap;
+    uint32_t *hist;      // [kOrderBuckets] one-launch form: segments per length bucket
+    uint32_t *cursor;    // [kOrderBuckets] one-launch form: queue slots taken per bucket
 };
+
+constexpr uint32_t kOrderBuckets = 256;  // 4 per octave of the segment length
+
+// Bucket of a segment of n >= 1 elements: 4 * floor(log2 n) + the next two bits.
+__device__ __forceinline__ uint32_t size_bucket(uint64_t n) {
+    const uint32_t lg = 63u - uint32_t(__clzll(n));
+    const uint32_t frac = lg >= 2 ? uint32_t(n >> (lg - 2)) & 3u : uint32_t(n << (2 - lg)) & 3u;
+    return (lg << 2) | frac;
+}
 
 // Asynchronous global -> shared copies (cp.async), for the queue entry of the next
 // segment while the current one is processed.
@@ -513,6 +532,242 @@ __global__ void __launch_bounds__(THREADS, MINB)
     }
 }
 
+// ---------------------------------------------------------------------------------
+// One-launch form: the queue preparation, the levels and the pair merges in one
+// persistent kernel (see the top of this file).
+// ---------------------------------------------------------------------------------
+constexpr uint32_t kFusedTicket = 4;    // status-block counters of the one-launch form
+constexpr uint32_t kHistDone = 5;       // histogram tickets finished
+constexpr uint32_t kScatterDone = 6;    // scatter tickets finished
+constexpr uint32_t kFusedChunk = 4096;  // descriptors per preparation ticket
+constexpr uint32_t kNoTicket = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t ld_acquire_gpu_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Thread 0: wait until *ctr >= target; false after the call's wait limit.
+__device__ __forceinline__ bool wait_at_least(const uint32_t *ctr, uint32_t target,
+                                              unsigned long long lim) {
+    DepTimer tm(lim);
+    while (ld_acquire_gpu_u32(ctr) < target)
+        if (tm.expired()) return false;
+    return true;
+}
+
+template <typename K, bool KV, int THREADS, int E>
+constexpr size_t fused_smem() {
+    constexpr size_t merge = TileShape<K, KV, THREADS, E>::kSmem;
+    constexpr size_t levels = 128 + Arena<K, KV>::kSmem;
+    return merge > levels ? merge : levels;
+}
+
+template <typename K, bool KV, int THREADS, int E, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
+    batched_fused_kernel(K *__restrict__ buf, uint32_t *__restrict__ vals, uint64_t buf_len,
+                         const ipm_segment *__restrict__ segs, uint32_t nseg, uint32_t by_size,
+                         QueueArea qa, uint64_t max_seg, StatusBlock *sb) {
+    using Tile = TileShape<K, KV, THREADS, E>;
+    using S = Arena<K, KV>;
+    constexpr uint64_t kTile = uint64_t(Tile::kTile);
+    constexpr uint32_t kElem = uint32_t(sizeof(K)) + (KV ? 4u : 0u);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw);
+    // the pair merges stage through [128, 128 + tile); the exchange levels use the same
+    // bytes as their arena (never at the same time)
+    K *skeys = reinterpret_cast<K *>(smem_raw + 128);
+    uint32_t *svals = reinterpret_cast<uint32_t *>(smem_raw + 128 + Tile::kKeyBytes);
+    __shared__ uint64_t ssplit[kMaxPairs + 1];
+    __shared__ uint32_t s_cnt[kOrderBuckets], s_base[kOrderBuckets];
+    __shared__ uint32_t s_t;
+    __shared__ int abort_flag, s_ready;
+    __shared__ ipm_segment s_sg;
+    const uint32_t tid = threadIdx.x;
+    const unsigned long long lim = wait_limit(sb);
+    const uint32_t C = by_size ? (nseg + kFusedChunk - 1) / kFusedChunk : 0u;
+    if (tid == 0) {
+        mbar_init(mbar, 1);
+        mbar_fence_init();
+        abort_flag = 0;
+        s_ready = by_size ? 0 : 1;
+    }
+    uint32_t parity = 0;
+    uint64_t moved = 0, xbytes = 0;  // thread 0: algorithmic bytes of merges / exchanges
+
+    for (;;) {
+        __syncthreads();  // the previous ticket's shared state is no longer read
+        if (tid == 0)
+            s_t = abort_flag ? kNoTicket : atomicAdd(&sb->counters[kFusedTicket], 1u);
+        __syncthreads();
+        const uint32_t t = s_t;
+        if (t == kNoTicket) break;
+        if (t < 2 * C) {
+            // ---- preparation: histogram tickets (t < C), then scatter tickets
+            const uint32_t chunk = t < C ? t : t - C;
+            const uint32_t i0 = chunk * kFusedChunk;
+            const uint32_t i1 = nseg - i0 < kFusedChunk ? nseg : i0 + kFusedChunk;
+            for (uint32_t q = tid; q < kOrderBuckets; q += THREADS) s_cnt[q] = 0u;
+            if (t >= C && tid == 0 && !wait_at_least(&sb->counters[kHistDone], C, lim)) {
+                set_status(sb, IPM_ERR_TIMEOUT);
+                abort_flag = 1;
+            }
+            __syncthreads();
+            if (abort_flag) continue;
+            for (uint32_t i = i0 + tid; i < i1; i += THREADS) {
+                const uint64_t n = segs[i].len_a + segs[i].len_b;
+                atomicAdd(&s_cnt[n ? size_bucket(n) : 0u], 1u);
+            }
+            __syncthreads();
+            if (t < C) {
+                for (uint32_t q = tid; q < kOrderBuckets; q += THREADS)
+                    if (s_cnt[q]) atomicAdd(&qa.hist[q], s_cnt[q]);
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) atomicAdd(&sb->counters[kHistDone], 1u);
+                continue;
+            }
+            // bucket starts: exclusive scan of the totals from the largest bucket down
+            if (tid < 32) {
+                uint32_t carry = 0;
+                for (int base = int(kOrderBuckets) - 32; base >= 0; base -= 32) {
+                    const uint32_t q = uint32_t(base) + 31u - tid;  // descending in the chunk
+                    const uint32_t v = __ldcg(&qa.hist[q]);
+                    uint32_t x = v;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                        if (int(tid) >= o) x += y;
+                    }
+                    s_base[q] = carry + x - v;
+                    carry += __shfl_sync(0xffffffffu, x, 31);
+                }
+            }
+            __syncthreads();
+            // this chunk's slots in every bucket
+            for (uint32_t q = tid; q < kOrderBuckets; q += THREADS)
+                if (s_cnt[q]) s_base[q] += atomicAdd(&qa.cursor[q], s_cnt[q]);
+            __syncthreads();
+            for (uint32_t i = i0 + tid; i < i1; i += THREADS) {
+                const ipm_segment sg = segs[i];
+                const uint64_t n = sg.len_a + sg.len_b;
+                qa.queue[atomicAdd(&s_base[n ? size_bucket(n) : 0u], 1u)] = sg;
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) atomicAdd(&sb->counters[kScatterDone], 1u);
+            continue;
+        }
+
+        // ---- one segment, in queue order
+        const uint32_t q = t - 2 * C;
+        if (q >= nseg) break;
+        if (tid == 0) {
+            if (!s_ready) {
+                if (wait_at_least(&sb->counters[kScatterDone], C, lim)) {
+                    s_ready = 1;
+                } else {
+                    set_status(sb, IPM_ERR_TIMEOUT);
+                    abort_flag = 1;
+                }
+            }
+            if (!abort_flag) {
+                ipm_segment sg;
+                if (by_size) {  // written by other CTAs of this launch: read through L2
+                    sg.offset = __ldcg(reinterpret_cast<const unsigned long long *>(&qa.queue[q].offset));
+                    sg.len_a = __ldcg(reinterpret_cast<const unsigned long long *>(&qa.queue[q].len_a));
+                    sg.len_b = __ldcg(reinterpret_cast<const unsigned long long *>(&qa.queue[q].len_b));
+                } else {
+                    sg = segs[q];
+                }
+                s_sg = sg;
+            }
+        }
+        __syncthreads();
+        if (abort_flag) continue;
+        const ipm_segment sg = s_sg;
+        const uint32_t cls = seg_class(sg, buf_len, kTile, max_seg);
+        if (cls == kSegInvalid) {
+            if (tid == 0) set_status(sb, IPM_ERR_INVALID_ARG);  // left untouched
+            continue;
+        }
+        if (cls == kSegTrivial) continue;
+        K *g = buf + sg.offset;
+        uint32_t *gv = KV ? vals + sg.offset : nullptr;
+        const uint64_t la = sg.len_a, n = sg.len_a + sg.len_b;
+        if (cls == kSegSingle) {
+            const int r = merge_pair_smem<K, KV, THREADS, E>(g, gv, uint32_t(la), uint32_t(n),
+                                                             skeys, svals, mbar, parity,
+                                                             abort_flag, sb);
+            if (tid == 0)
+                moved += r == kPairMerged ? 2ull * n * kElem : r == kPairInOrder ? n * kElem : 0;
+            continue;
+        }
+        // a multi-tile segment: a0 (already in order: nothing moves), a1, a2, a3
+        if (key_le(g[la - 1], g[la])) continue;
+        const uint32_t G = seg_levels(n, kTile);
+        const uint32_t P = 1u << G;
+        SegmentCtx<K, KV, THREADS> cx;
+        cx.ak = reinterpret_cast<K *>(smem_raw + 128);
+        cx.av = reinterpret_cast<uint32_t *>(smem_raw + 128 + S::kKeyBytes);
+        cx.g = g;
+        cx.gv = gv;
+        for (uint32_t k = tid >> 5; k <= P; k += THREADS / 32) {
+            const uint64_t d = (uint64_t(k) * n) >> G;
+            const uint64_t i = warp_split<false>(g, la, g + la, n - la, d);
+            if ((tid & 31u) == 0) ssplit[k] = i;
+        }
+        __syncthreads();
+        for (uint32_t l = 0; l < G; ++l) {
+            for (uint32_t r = 0; r < (1u << l); ++r) {
+                const uint32_t k_lo = r << (G - l);
+                const uint32_t k_mid = k_lo + (1u << (G - l - 1));
+                const uint32_t k_hi = k_lo + (1u << (G - l));
+                const uint64_t d_lo = (uint64_t(k_lo) * n) >> G;
+                const uint64_t d_mid = (uint64_t(k_mid) * n) >> G;
+                const uint64_t i_lo = ssplit[k_lo], i_mid = ssplit[k_mid], i_hi = ssplit[k_hi];
+                const uint64_t xs = d_lo + (i_mid - i_lo);
+                const uint64_t xa = i_hi - i_mid;
+                const uint64_t xb = (d_mid - i_mid) - (d_lo - i_lo);
+                if (tid == 0) {
+                    uint64_t it = 0, by = 0;
+                    x_count(S::params(), xs, xa, xb, kElem, it, by);
+                    xbytes += by;
+                }
+                cta_exchange<K, KV, THREADS>(cx, xs, xa, xb);
+            }
+        }
+        // the exchanges' global writes precede the bulk copies that read them back, and
+        // their shared-memory accesses precede the bulk copies into the same bytes
+        __threadfence();
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        fence_proxy_async_smem();
+        __syncthreads();
+        for (uint32_t k = 0; k < P; ++k) {
+            const uint64_t d0 = (uint64_t(k) * n) >> G, d1 = (uint64_t(k + 1) * n) >> G;
+            const uint32_t c = uint32_t(d1 - d0);
+            if (c == 0) continue;
+            if (ssplit[k + 1] < ssplit[k] || ssplit[k + 1] - ssplit[k] > c) {  // inconsistent
+                if (tid == 0) set_status(sb, IPM_ERR_DEVICE);
+                continue;
+            }
+            const uint32_t a = uint32_t(ssplit[k + 1] - ssplit[k]);
+            const int r = merge_pair_smem<K, KV, THREADS, E>(g + d0, KV ? gv + d0 : nullptr, a, c,
+                                                             skeys, svals, mbar, parity,
+                                                             abort_flag, sb);
+            if (r == kPairAbort) break;  // abort_flag is set: the next claim stops the CTA
+            if (tid == 0)
+                moved += r == kPairMerged ? 2ull * c * kElem : r == kPairInOrder ? 1ull * c * kElem : 0;
+        }
+    }
+    if (tid == 0) {
+        if (moved) atomicAdd(&sb->merge_bytes, moved);
+        if (xbytes) atomicAdd(&sb->exchange_bytes, xbytes);
+        bulk_wait_all0();
+    }
+}
+
 // Merge tile variants: 0 wide = the plain path's tile (one CTA per SM), 1 narrow = half
 // of it (two CTAs per SM), 2 quarter = a quarter (four CTAs per SM): the smaller the
 // tile, the more CTAs overlap one another's staging latency, and the more exchange
@@ -557,13 +812,30 @@ ipm_status occupancy_of(F kern, int threads, size_t smem, std::atomic<int> &cach
 
 template <typename K, bool KV, int VARIANT>
 ipm_status batched_launch_t(void *buf, uint32_t *vals, uint64_t buf_len, QueueArea qa,
-                            uint32_t nseg, uint32_t ctas_per_sm, StatusBlock *sb,
+                            uint32_t nseg, uint32_t ctas_per_sm, uint32_t one_launch,
+                            const ipm_segment *segs, uint32_t by_size, StatusBlock *sb,
                             cudaStream_t stream) {
     using BT = BatchTile<K, KV, VARIANT>;
     using Tile = TileShape<K, KV, BT::T, BT::E>;
     using S = Arena<K, KV>;
     constexpr uint64_t kTile = tile_of<K, KV, VARIANT>();
     if (nseg == 0) return IPM_OK;
+    if (one_launch) {
+        auto fk = batched_fused_kernel<K, KV, BT::T, BT::E, BT::MINB>;
+        constexpr size_t smem = fused_smem<K, KV, BT::T, BT::E>();
+        static std::atomic<int> occ_fused_cache{0};
+        int occ = 0;
+        IPM_TRY(occupancy_of(fk, BT::T, smem, occ_fused_cache, occ));
+        uint32_t per_sm = uint32_t(occ);
+        if (ctas_per_sm != 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+        const uint64_t tickets =
+            uint64_t(nseg) + 2ull * (by_size ? (nseg + kFusedChunk - 1) / kFusedChunk : 0u);
+        uint64_t grid = uint64_t(per_sm) * uint64_t(num_sms());
+        if (grid > tickets) grid = tickets;
+        fk<<<unsigned(grid), BT::T, smem, stream>>>((K *)buf, vals, buf_len, segs, nseg, by_size,
+                                                    qa, uint64_t(kMaxPairs) * kTile, sb);
+        return last_launch_status();
+    }
     // levels: one CTA per multi-tile segment (the prep kernel lists them)
     auto lk = batched_levels_kernel<K, KV>;
     static std::atomic<int> occ_levels_cache{0};
@@ -590,25 +862,26 @@ ipm_status batched_launch_t(void *buf, uint32_t *vals, uint64_t buf_len, QueueAr
 template <typename K>
 ipm_status batched_dispatch(void *buf, uint32_t *vals, uint64_t buf_len, QueueArea qa,
                             uint32_t nseg, uint32_t variant, uint32_t ctas_per_sm,
+                            uint32_t one_launch, const ipm_segment *segs, uint32_t by_size,
                             StatusBlock *sb, cudaStream_t stream) {
     if (vals != nullptr) {
         if (variant == 2)
-            return batched_launch_t<K, true, 2>(buf, vals, buf_len, qa, nseg, ctas_per_sm, sb,
-                                                stream);
+            return batched_launch_t<K, true, 2>(buf, vals, buf_len, qa, nseg, ctas_per_sm,
+                                                one_launch, segs, by_size, sb, stream);
         if (variant == 1)
-            return batched_launch_t<K, true, 1>(buf, vals, buf_len, qa, nseg, ctas_per_sm, sb,
-                                                stream);
-        return batched_launch_t<K, true, 0>(buf, vals, buf_len, qa, nseg, ctas_per_sm, sb,
-                                            stream);
+            return batched_launch_t<K, true, 1>(buf, vals, buf_len, qa, nseg, ctas_per_sm,
+                                                one_launch, segs, by_size, sb, stream);
+        return batched_launch_t<K, true, 0>(buf, vals, buf_len, qa, nseg, ctas_per_sm,
+                                            one_launch, segs, by_size, sb, stream);
     }
     if (variant == 2)
-        return batched_launch_t<K, false, 2>(buf, nullptr, buf_len, qa, nseg, ctas_per_sm, sb,
-                                             stream);
+        return batched_launch_t<K, false, 2>(buf, nullptr, buf_len, qa, nseg, ctas_per_sm,
+                                             one_launch, segs, by_size, sb, stream);
     if (variant == 1)
-        return batched_launch_t<K, false, 1>(buf, nullptr, buf_len, qa, nseg, ctas_per_sm, sb,
-                                             stream);
-    return batched_launch_t<K, false, 0>(buf, nullptr, buf_len, qa, nseg, ctas_per_sm, sb,
-                                         stream);
+        return batched_launch_t<K, false, 1>(buf, nullptr, buf_len, qa, nseg, ctas_per_sm,
+                                             one_launch, segs, by_size, sb, stream);
+    return batched_launch_t<K, false, 0>(buf, nullptr, buf_len, qa, nseg, ctas_per_sm,
+                                         one_launch, segs, by_size, sb, stream);
 }
 
 // Merge tile (elements) of a variant.

@@ -6,9 +6,11 @@ namespace ipm {
 
 ipm_status batched_launch_f32(void *buf, uint32_t *vals, uint64_t buf_len,
                                batched::QueueArea qa, uint32_t nseg, uint32_t variant,
-                               uint32_t ctas_per_sm, StatusBlock *sb, cudaStream_t stream) {
+                               uint32_t ctas_per_sm, uint32_t one_launch,
+                               const ipm_segment *segs, uint32_t by_size, StatusBlock *sb,
+                               cudaStream_t stream) {
     return batched::batched_dispatch<float>(buf, vals, buf_len, qa, nseg, variant, ctas_per_sm,
-                                          sb, stream);
+                                          one_launch, segs, by_size, sb, stream);
 }
 
 }  // namespace ipm

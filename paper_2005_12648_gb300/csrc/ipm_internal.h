@@ -115,16 +115,18 @@ ipm_status launch_tile_merge(void *buf, void *vals, uint32_t vb, uint64_t la, ui
 // Batched segmented merge (ipm_batched.cu): workspace layout, queue preparation and
 // the levels + merge kernels.  variant 0 = wide, 1 = narrow, 2 = quarter merge tile.
 struct BatchedLayout {
-    size_t queue_off, multi_off, soff_off, pool_off, total;
+    size_t hist_off, queue_off, multi_off, soff_off, pool_off, total;
     uint64_t pool_cap;
 };
 uint64_t batched_tile(ipm_dtype key, bool with_values, uint32_t variant);
 uint64_t batched_max_segment(ipm_dtype key, bool with_values, uint32_t variant);
 BatchedLayout batched_layout(uint64_t buf_len, uint32_t nseg, uint64_t tile);
+// one_launch: the one-launch form (a memset node, then one persistent kernel), else
+// three launches (queue preparation, levels, merges).
 ipm_status launch_batched(void *buf, uint32_t *vals, uint64_t buf_len, ipm_dtype key,
                           const ipm_segment *segs, uint32_t nseg, void *ws,
                           const BatchedLayout &L, uint32_t by_size, uint32_t variant,
-                          uint32_t ctas_per_sm, cudaStream_t stream);
+                          uint32_t ctas_per_sm, uint32_t one_launch, cudaStream_t stream);
 
 // Learned split proposer (ipm_learned.cu).
 ipm_status launch_learned_splits(const void *buf, uint64_t la, uint64_t lb, ipm_dtype key,

@@ -51,9 +51,10 @@ def test_cache_hit_answers_without_timing(m, tmp_path):
     sig = m.ipm_batched_tune_signature(t, "int32")
     path = tmp_path / "tune.txt"
     path.write_text("garbage line\n"
-                    f"ipmtune1 {sig} 1 0 0 9.0\n"
-                    "ipmtune1 0123456789abcdef 2 1 1 1.0\n"
-                    f"ipmtune1 {sig} 3 2 1 0.5\n")  # the last matching line wins
+                    f"ipmtune2 {sig} 1 0 0 1 9.0\n"
+                    "ipmtune2 0123456789abcdef 2 1 1 2 1.0\n"
+                    f"ipmtune1 {sig} 2 0 0 0.1\n"  # an older format: ignored
+                    f"ipmtune2 {sig} 3 2 1 2 0.5\n")  # the last matching line wins
     hs = np.ascontiguousarray(t.view(np.uint64))
     res = m.IpmBatchedTuneResult()
     fake = 0x1000  # never dereferenced on a cache hit
@@ -63,7 +64,7 @@ def test_cache_hit_answers_without_timing(m, tmp_path):
     assert rc == 0
     d = res.as_dict()
     assert d["from_cache"] and d["candidates"] == 0 and d["signature"] == sig
-    assert d["best"] == {"tile": 3, "ctas_per_sm": 2, "order": 1}
+    assert d["best"] == {"tile": 3, "ctas_per_sm": 2, "order": 1, "form": 2}
     assert d["best_ms"] == pytest.approx(0.5)
 
 

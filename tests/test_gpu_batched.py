@@ -10,7 +10,10 @@ pytestmark = pytest.mark.gpu
 
 DTYPES = [np.int32, np.uint32, np.uint64, np.float32, np.int64]
 OPTIONS = [None, {"tile": 1}, {"tile": 3}, {"order": 1},
-           {"tile": 2, "ctas_per_sm": 1, "order": 1}]
+           {"tile": 2, "ctas_per_sm": 1, "order": 1},
+           # the one-launch form (memset node + one persistent kernel)
+           {"form": 2}, {"form": 2, "tile": 1}, {"form": 2, "tile": 3, "order": 1},
+           {"form": 2, "tile": 2, "ctas_per_sm": 1}]
 
 
 def _table(dt, tile, seed, kv=False):
@@ -86,7 +89,7 @@ def test_batched_keys_match_oracle(ipm, dev, orc, dt, opt):
 
 
 @pytest.mark.parametrize("dt", [np.uint32, np.uint64, np.float32, np.int64])
-@pytest.mark.parametrize("opt", [0, 1, 2])
+@pytest.mark.parametrize("opt", [0, 1, 2, 5, 7])
 def test_batched_kv_stable(ipm, dev, orc, dt, opt):
     tile = ipm.ipm_merge_plan(1, 1, NAME[np.dtype(dt)], True)[1]
     buf, segs = _table(dt, tile, seed=11 + opt)
@@ -121,7 +124,8 @@ def test_batched_sizes_around_the_tile(ipm, dev, orc, opt):
     assert first_diff(got, want) is None
 
 
-def test_batched_bad_segments_are_skipped(ipm, dev, orc):
+@pytest.mark.parametrize("form", [1, 2])
+def test_batched_bad_segments_are_skipped(ipm, dev, orc, form):
     """A segment that leaves the buffer or exceeds the per-segment limit is left
     untouched and flagged; the valid segments are still merged."""
     dt = np.int32
@@ -132,14 +136,15 @@ def test_batched_bad_segments_are_skipped(ipm, dev, orc):
     n = buf.size
     segs = [(0, 1000, 999), (1999, big_a.size, big_b.size), (n - 10, 8, 8),
             (2**62, 1, 1), (0, 2**62, 2**62)]
-    got, _, status, _ = _run(ipm, dev, buf, segs, dt, options={"tile": 2})
+    got, _, status, _ = _run(ipm, dev, buf, segs, dt, options={"tile": 2, "form": form})
     assert status == 1  # IPM_ERR_INVALID_ARG
     want = buf.copy()
     want[:1999] = orc.merge(a, b)
     assert first_diff(got, want) is None
 
 
-def test_batched_merge_bytes(ipm, dev, orc):
+@pytest.mark.parametrize("form", [1, 2])
+def test_batched_merge_bytes(ipm, dev, orc, form):
     """Single-tile segments: a merged segment moves 2n elements, one whose runs are
     already in order is read once (n) and not written, one with an empty run is not
     touched."""
@@ -147,7 +152,7 @@ def test_batched_merge_bytes(ipm, dev, orc):
     tile = ipm.ipm_merge_plan(1, 1, "int32")[1]
     buf, segs = _table(dt, tile, seed=21)
     segs = [s for s in segs if s[1] + s[2] <= tile]
-    _, _, status, ws = _run(ipm, dev, buf, segs, dt)
+    _, _, status, ws = _run(ipm, dev, buf, segs, dt, options={"form": form})
     assert status == 0
     want = 0
     for off, la, lb in segs:
@@ -156,10 +161,12 @@ def test_batched_merge_bytes(ipm, dev, orc):
     assert ipm.ipm_read_merge_bytes(ws) == want
 
 
-def test_batched_graph_capture(ipm, dev, orc):
+@pytest.mark.parametrize("form", [1, 2])
+def test_batched_graph_capture(ipm, dev, orc, form):
     """The call captures into a CUDA graph; replays merge the restored input again."""
     import torch
 
+    opts = {"form": form}
     dt = np.int32
     tile = ipm.ipm_merge_plan(1, 1, "int32")[1]
     buf, segs = _table(dt, tile, seed=31)
@@ -172,12 +179,14 @@ def test_batched_graph_capture(ipm, dev, orc):
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):  # warm-up outside capture (first-call attribute setup)
-        ipm.ipm_merge_batched(d, None, buf.size, st, len(segs), "int32", ws, stream=s)
+        ipm.ipm_merge_batched(d, None, buf.size, st, len(segs), "int32", ws, options=opts,
+                              stream=s)
     torch.cuda.current_stream().wait_stream(s)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
-        ipm.ipm_merge_batched(d, None, buf.size, st, len(segs), "int32", ws, stream=s)
+        ipm.ipm_merge_batched(d, None, buf.size, st, len(segs), "int32", ws, options=opts,
+                              stream=s)
     for _ in range(2):
         d.copy_(pristine)
         torch.cuda.synchronize()
@@ -188,7 +197,7 @@ def test_batched_graph_capture(ipm, dev, orc):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("opt", [0, 1, 2])
+@pytest.mark.parametrize("opt", [0, 1, 2, 5])
 def test_batched_fullsize_20000_segments(ipm, dev, orc, opt):
     """20,000 uniform int32 segments, log-uniform side lengths, total <= 2^28."""
     import torch
@@ -230,7 +239,8 @@ def test_autotuned_options_match_oracle(ipm, dev, orc, kv, tmp_path):
     cache = str(tmp_path / "tune.txt")
     res = ipm.ipm_merge_batched_tune(d, dv, buf.size, st, len(segs), "int32", scratch, ws,
                                      scratch_vals=svals, reps=3, cache_path=cache)
-    assert not res["from_cache"] and res["candidates"] >= 8
+    assert not res["from_cache"] and res["candidates"] >= 16
+    assert {e["form"] for e in res["table"]} == {1, 2}
     assert res["best_ms"] > 0 and res["default_ms"] > 0
     assert res["best_ms"] <= min(e["ms"] for e in res["table"]) + 1e-6
     torch.cuda.synchronize()
