@@ -22,6 +22,15 @@
 // chain of LS steps.  Consecutive phases of one exchange
 // (LS steps) are ordered by a per-exchange completion counter.  Every wait is bounded
 // in time; on expiry the kernel records IPM_ERR_TIMEOUT and all CTAs leave.
+//
+// Ticket order within a level is phase-major: section k holds phase k of every exchange
+// (exchange by exchange), and the last section holds every exchange's remaining phases
+// (exchange-major).  An exchange whose blocks leave long chains of LS steps (heavy key
+// repeats) thus has step k of every exchange in flight together instead of one step of
+// one exchange at a time; an exchange that is done in one phase (the common case) lies
+// in section 0 as before.  Every wait is still on earlier tickets: a phase waits for the
+// earlier phases of its exchange (earlier sections, or earlier in the last one) and for
+// items of its own phase.
 #include "ipm_exchange.cuh"
 #include "ipm_internal.h"
 #include "ipm_tma.cuh"
@@ -44,6 +53,27 @@ __host__ __device__ inline uint32_t level_holders(uint32_t l, uint32_t hcap) {
 struct RotPlan {
     uint64_t s, a, b;
 };
+
+// Items of each section of one exchange (phase k in section k < kSections - 1, every
+// later phase in the last section) and its algorithmic bytes.
+__host__ __device__ inline void x_sections(const XParams &P, uint64_t s, uint64_t a, uint64_t b,
+                                           uint32_t elem, uint32_t (&c)[kSections],
+                                           uint64_t &bytes) {
+    for (uint32_t k = 0; k < kSections; ++k) c[k] = 0;
+    bytes = 0;
+    XPhase ph;
+    uint32_t p = 0;
+    while (x_phase(P, s, a, b, ph)) {
+        const uint32_t k = p < kSections - 1 ? p : kSections - 1;
+        for (uint32_t q = 0; q < kSections; ++q)
+            if (q == k) c[q] += ph.items();
+        const uint64_t mn = ph.a < ph.b ? ph.a : ph.b;
+        bytes += (ph.kind == XK_SWAP ? 4 * mn : 2 * (ph.a + ph.b)) * elem;
+        if (ph.final_phase) break;
+        x_after_step(ph, s, a, b);
+        ++p;
+    }
+}
 
 __device__ uint32_t block_exclusive_scan_u32(uint32_t v, uint32_t *total) {
     __shared__ uint32_t warp_sums[32];
@@ -86,41 +116,63 @@ __device__ __forceinline__ RotPlan level_rotation(const uint64_t *split, uint64_
     return q;
 }
 
-// One block per level: the exchanges of level l, their item prefix and (added into
-// the status block) their algorithmic bytes.
+// One block per level: the exchanges of level l, the item prefix of every section over
+// the exchanges, the section starts and (added into the status block) the algorithmic
+// bytes.
 __global__ void __launch_bounds__(kPlanThreads)
     xplan_levels_kernel(const uint64_t *__restrict__ split, uint64_t n, uint32_t G,
                         XPlanArea pa, XParams prm, uint32_t hcap, uint32_t elem,
                         StatusBlock *sb) {
+    __shared__ uint32_t s_tot[kSections];
     if (call_finished(sb)) return;
     const uint32_t l = blockIdx.x;
     prm.max_holders = level_holders(l, hcap);
     const uint64_t R = 1ull << l;
     RotPlan *plans = reinterpret_cast<RotPlan *>(pa.plans) + (R - 1);
-    uint32_t *pf = pa.item_pf + (R - 1) + l;
+    uint32_t *pk = pa.item_pf + level_prefix_offset(l);
+    uint32_t *sec = pa.sec_start + level_section_offset(l);
     const uint64_t per = (R + kPlanThreads - 1) / kPlanThreads;
     const uint64_t r0 = per * threadIdx.x;
     const uint64_t r1 = r0 + per < R ? r0 + per : R;
-    uint32_t items = 0;
+    uint32_t items[kSections] = {};
     unsigned long long bytes = 0;
     for (uint64_t r = r0; r < r1; ++r) {
         RotPlan q = level_rotation(split, n, G, l, r);
-        uint64_t it = 0, by = 0;
-        x_count(prm, q.s, q.a, q.b, elem, it, by);
-        items += uint32_t(it);
+        uint32_t c[kSections];
+        uint64_t by = 0;
+        x_sections(prm, q.s, q.a, q.b, elem, c, by);
+#pragma unroll
+        for (uint32_t k = 0; k < kSections; ++k) items[k] += c[k];
         bytes += by;
     }
-    uint32_t total;
-    uint32_t e = block_exclusive_scan_u32(items, &total);
+    uint32_t e[kSections];
+#pragma unroll
+    for (uint32_t k = 0; k < kSections; ++k) {
+        uint32_t tot;
+        e[k] = block_exclusive_scan_u32(items[k], &tot);
+        if (threadIdx.x == 0) s_tot[k] = tot;
+    }
     for (uint64_t r = r0; r < r1; ++r) {
         RotPlan q = level_rotation(split, n, G, l, r);
-        uint64_t it = 0, by = 0;
-        x_count(prm, q.s, q.a, q.b, elem, it, by);
+        uint32_t c[kSections];
+        uint64_t by = 0;
+        x_sections(prm, q.s, q.a, q.b, elem, c, by);
         plans[r] = q;
-        pf[r] = e;
-        e += uint32_t(it);
+#pragma unroll
+        for (uint32_t k = 0; k < kSections; ++k) {
+            pk[k * (R + 1) + r] = e[k];
+            e[k] += c[k];
+        }
     }
-    if (threadIdx.x == 0) pf[R] = total;
+    if (threadIdx.x == 0) {
+        uint32_t start = 0;
+        for (uint32_t k = 0; k < kSections; ++k) {
+            pk[k * (R + 1) + R] = s_tot[k];
+            sec[k] = start;
+            start += s_tot[k];
+        }
+        sec[kSections] = start;
+    }
     if (sb != nullptr && bytes) atomicAdd(&sb->exchange_bytes, bytes);
 }
 
@@ -129,11 +181,18 @@ __global__ void xplan_single_kernel(uint64_t lx, uint64_t ly, XPlanArea pa, XPar
     prm.max_holders = level_holders(0, hcap);
     if (threadIdx.x == 0) {
         RotPlan q{0, lx, ly};
-        uint64_t it = 0, by = 0;
-        x_count(prm, 0, lx, ly, 4, it, by);
+        uint32_t c[kSections];
+        uint64_t by = 0;
+        x_sections(prm, 0, lx, ly, 4, c, by);
         reinterpret_cast<RotPlan *>(pa.plans)[0] = q;
-        pa.item_pf[0] = 0;
-        pa.item_pf[1] = uint32_t(it);
+        uint32_t start = 0;
+        for (uint32_t k = 0; k < kSections; ++k) {
+            pa.item_pf[2 * k] = 0;
+            pa.item_pf[2 * k + 1] = c[k];
+            pa.sec_start[k] = start;
+            start += c[k];
+        }
+        pa.sec_start[kSections] = start;
     }
 }
 
@@ -334,23 +393,74 @@ __device__ __forceinline__ void decode_phase_item(const XParams &prm, const XPha
     }
 }
 
+// Item j (counted within section k) of exchange r: replay the exchange's phases to the
+// one holding it (phase k when k < kSections - 1; in the last section, its phases from
+// there on back to back).  t is the ticket; the phase's items have consecutive tickets,
+// so its item 0 (the base of its flag indices) is t minus the item's index in the phase.
+__device__ __forceinline__ bool decode_in_exchange(const XParams &prm, uint32_t t, uint32_t r,
+                                                   uint32_t j, uint32_t k, const RotPlan &q,
+                                                   uint64_t n, Item &it) {
+    XPhase ph;
+    uint64_t s = q.s, a = q.a, b = q.b;
+    uint32_t before = 0, p = 0;
+    bool found = false;
+    while (x_phase(prm, s, a, b, ph)) {
+        const uint32_t ps = p < kSections - 1 ? p : kSections - 1;
+        if (ps == k) {
+            if (j < ph.items()) {
+                found = true;
+                break;
+            }
+            if (k < kSections - 1) break;  // the section holds this one phase only
+            j -= ph.items();
+        }
+        before += ph.items();
+        if (ph.final_phase) break;
+        x_after_step(ph, s, a, b);
+        ++p;
+    }
+    const uint64_t m = ph.a + ph.b;
+    if (!found || ph.s > n || m > n - ph.s) return false;
+    decode_phase_item(prm, ph, t, r, before + j, before, t - j, it);
+    return true;
+}
+
+// The section of ticket t (the last k with sec[k] <= t), from the previous one: a CTA's
+// tickets only grow.  A new section restarts the exchange hint.
+__device__ __forceinline__ uint32_t ticket_section(const uint32_t *sec, uint32_t t,
+                                                   uint32_t &sec_hint, uint32_t &rot_hint) {
+    uint32_t k = sec_hint;
+    while (k + 1 < kSections && sec[k + 1] <= t) ++k;
+    if (k != sec_hint) {
+        sec_hint = k;
+        rot_hint = 0;
+    }
+    return k;
+}
+
 // Decode ticket t of a level plan into an item.  Every thread computes the same item.
+// pk: the level's per-section exchange prefixes (kSections x (nrot + 1)); sec: its
+// section starts.
 __device__ __forceinline__ bool decode_item(const XParams &prm, uint32_t t, uint32_t &rot_hint,
-                                            const uint32_t *pf, const RotPlan *plans,
+                                            uint32_t &sec_hint, const uint32_t *pk,
+                                            const uint32_t *sec, const RotPlan *plans,
                                             uint32_t nrot, uint64_t n, Item &it) {
-    // the exchange holding t is the last one with pf[r] <= t.  A CTA's tickets only
+    const uint32_t k = ticket_section(sec, t, sec_hint, rot_hint);
+    const uint32_t ts = t - sec[k];
+    const uint32_t *pf = pk + size_t(k) * (nrot + 1);
+    // the exchange holding ts is the last one with pf[r] <= ts.  A CTA's tickets only
     // grow: the block probes the 512 exchanges after the previous one in one coalesced
     // round (pf is non-decreasing, so the hits form a prefix); longer jumps bisect.
-    if (pf[rot_hint + 1] <= t) {
+    if (pf[rot_hint + 1] <= ts) {
         const uint32_t cand = rot_hint + 1 + threadIdx.x;
-        const int cnt = __syncthreads_count(cand <= nrot && pf[cand] <= t);
+        const int cnt = __syncthreads_count(cand <= nrot && pf[cand] <= ts);
         if (cnt < int(blockDim.x)) {
             rot_hint += uint32_t(cnt);
         } else {
             uint32_t lo = rot_hint + blockDim.x, hi = nrot;
             while (hi - lo > 1) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (pf[mid] <= t)
+                if (pf[mid] <= ts)
                     lo = mid;
                 else
                     hi = mid;
@@ -359,25 +469,7 @@ __device__ __forceinline__ bool decode_item(const XParams &prm, uint32_t t, uint
         }
     }
     const uint32_t r = rot_hint;
-    const uint32_t j = t - pf[r];
-    const RotPlan q = plans[r];
-    XPhase ph;
-    uint64_t s = q.s, a = q.a, b = q.b;
-    uint32_t before = 0;
-    bool found = false;
-    while (x_phase(prm, s, a, b, ph)) {
-        if (j < before + ph.items()) {
-            found = true;
-            break;
-        }
-        before += ph.items();
-        if (ph.final_phase) break;
-        x_after_step(ph, s, a, b);
-    }
-    const uint64_t m = ph.a + ph.b;
-    if (!found || ph.s > n || m > n - ph.s) return false;
-    decode_phase_item(prm, ph, t, r, j, before, pf[r] + before, it);
-    return true;
+    return decode_in_exchange(prm, t, r, ts - pf[r], k, plans[r], n, it);
 }
 
 // Shared-memory layout of a stage: two key slots, then two value slots.  A SINGLE
@@ -561,8 +653,9 @@ __device__ __forceinline__ void stage_store(const Item &it, K *buf, uint32_t *va
 template <typename K, bool KV>
 __global__ void __launch_bounds__(512, 1)
     exchange_level_kernel(K *__restrict__ buf, uint32_t *__restrict__ vals, uint64_t n,
-                          const RotPlan *__restrict__ plans, const uint32_t *__restrict__ pf,
-                          uint32_t nrot, uint32_t *__restrict__ flags,
+                          const RotPlan *__restrict__ plans, const uint32_t *__restrict__ pk,
+                          const uint32_t *__restrict__ sec, uint32_t nrot,
+                          uint32_t *__restrict__ flags,
                           uint32_t *__restrict__ join, uint32_t tag, uint32_t ctr_index,
                           uint32_t holders, StatusBlock *sb) {
     using C = XCfg<K, KV>;
@@ -574,7 +667,7 @@ __global__ void __launch_bounds__(512, 1)
     XParams prm = C::params();
     prm.max_holders = holders;
     const uint32_t tid = threadIdx.x;
-    const uint32_t total = pf[nrot];
+    const uint32_t total = sec[kSections];
     uint32_t *ctr = &sb->counters[ctr_index];
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -585,12 +678,12 @@ __global__ void __launch_bounds__(512, 1)
     }
     __syncthreads();
     uint32_t parity0 = 0, parity1 = 0;
-    uint32_t rot = 0;
+    uint32_t rot = 0, sech = 0;
     int cs = 0;  // stage of the current item
     Item cur;
     bool cur_loaded = false;
     uint32_t cur_t = sh.ticket[0];
-    if (cur_t < total && !decode_item(prm, cur_t, rot, pf, plans, nrot, n, cur)) {
+    if (cur_t < total && !decode_item(prm, cur_t, rot, sech, pk, sec, plans, nrot, n, cur)) {
         if (tid == 0) set_status(sb, IPM_ERR_DEVICE);
         return;
     }
@@ -625,7 +718,7 @@ __global__ void __launch_bounds__(512, 1)
             if (tid == 0) sh.ticket[(it_no + 1) & 1] = atomicAdd(ctr, 1u);
             __syncthreads();
             nxt_t = sh.ticket[(it_no + 1) & 1];
-            if (nxt_t < total && !decode_item(prm, nxt_t, rot, pf, plans, nrot, n, nxt)) {
+            if (nxt_t < total && !decode_item(prm, nxt_t, rot, sech, pk, sec, plans, nrot, n, nxt)) {
                 if (tid == 0) set_status(sb, IPM_ERR_DEVICE);
                 break;
             }
@@ -682,7 +775,7 @@ __global__ void __launch_bounds__(512, 1)
             if (tid == 0) sh.ticket[(it_no + 1) & 1] = atomicAdd(ctr, 1u);
             __syncthreads();
             nxt_t = sh.ticket[(it_no + 1) & 1];
-            if (nxt_t < total && !decode_item(prm, nxt_t, rot, pf, plans, nrot, n, nxt)) {
+            if (nxt_t < total && !decode_item(prm, nxt_t, rot, sech, pk, sec, plans, nrot, n, nxt)) {
                 if (tid == 0) set_status(sb, IPM_ERR_DEVICE);
                 break;
             }
@@ -718,15 +811,26 @@ constexpr uint32_t kWsConsumers = 480;  // threads 32..511
 
 // Warp version of decode_item: the exchange holding ticket t by a 32-wide probe of the
 // next exchanges, then a 33-way bracket search for longer jumps.
+// sec_lane: lane q holds the level's section start q (q <= kSections), kept in registers
+// so that finding the section costs one ballot.
 __device__ __forceinline__ bool decode_item_warp(const XParams &prm, uint32_t t,
-                                                 uint32_t &rot_hint, const uint32_t *pf,
+                                                 uint32_t &rot_hint, uint32_t &sec_hint,
+                                                 const uint32_t *pk, uint32_t sec_lane,
                                                  const RotPlan *plans, uint32_t nrot,
                                                  uint64_t n, Item &it) {
     const uint32_t lane = threadIdx.x & 31u;
-    if (pf[rot_hint + 1] <= t) {
-        uint32_t lo = rot_hint + 1;  // pf[lo] <= t; pf[nrot] = total > t
+    const uint32_t k =
+        uint32_t(__popc(__ballot_sync(0xffffffffu, lane < kSections && sec_lane <= t))) - 1u;
+    if (k != sec_hint) {
+        sec_hint = k;
+        rot_hint = 0;
+    }
+    const uint32_t ts = t - __shfl_sync(0xffffffffu, sec_lane, k);
+    const uint32_t *pf = pk + size_t(k) * (nrot + 1);
+    if (pf[rot_hint + 1] <= ts) {
+        uint32_t lo = rot_hint + 1;  // pf[lo] <= ts; pf[nrot] = section total > ts
         const uint32_t cand = lo + lane;
-        const bool p = cand <= nrot && pf[cand] <= t;
+        const bool p = cand <= nrot && pf[cand] <= ts;
         const int c = __popc(__ballot_sync(0xffffffffu, p));
         if (c < 32) {
             rot_hint = lo + uint32_t(c) - 1;
@@ -736,7 +840,7 @@ __device__ __forceinline__ bool decode_item_warp(const XParams &prm, uint32_t t,
             while (hi - lo > 1) {
                 const uint32_t R = hi - lo;
                 const uint32_t m = lo + uint32_t((uint64_t(R) * (lane + 1)) / 33);
-                const bool q = pf[m] <= t;
+                const bool q = pf[m] <= ts;
                 const int cc = __popc(__ballot_sync(0xffffffffu, q));
                 const uint32_t m_lo = __shfl_sync(0xffffffffu, m, cc > 0 ? cc - 1 : 0);
                 const uint32_t m_hi = __shfl_sync(0xffffffffu, m, cc < 32 ? cc : 31);
@@ -747,25 +851,7 @@ __device__ __forceinline__ bool decode_item_warp(const XParams &prm, uint32_t t,
         }
     }
     const uint32_t r = rot_hint;
-    const uint32_t j = t - pf[r];
-    const RotPlan q = plans[r];
-    XPhase ph;
-    uint64_t s = q.s, a = q.a, b = q.b;
-    uint32_t before = 0;
-    bool found = false;
-    while (x_phase(prm, s, a, b, ph)) {
-        if (j < before + ph.items()) {
-            found = true;
-            break;
-        }
-        before += ph.items();
-        if (ph.final_phase) break;
-        x_after_step(ph, s, a, b);
-    }
-    const uint64_t m = ph.a + ph.b;
-    if (!found || ph.s > n || m > n - ph.s) return false;
-    decode_phase_item(prm, ph, t, r, j, before, pf[r] + before, it);
-    return true;
+    return decode_in_exchange(prm, t, r, ts - pf[r], k, plans[r], n, it);
 }
 
 // Producer warp: stage the item's source blocks, then arrive on the stage's "full"
@@ -916,8 +1002,9 @@ __device__ bool ws_wait_deps(const uint32_t *flags, uint32_t lo, uint32_t hi, ui
 template <typename K, bool KV, typename V>
 __global__ void __launch_bounds__(512, 1)
     exchange_level_ws_kernel(K *__restrict__ buf, V *__restrict__ vals, uint64_t n,
-                             const RotPlan *__restrict__ plans, const uint32_t *__restrict__ pf,
-                             uint32_t nrot, uint32_t *__restrict__ flags,
+                             const RotPlan *__restrict__ plans, const uint32_t *__restrict__ pk,
+                             const uint32_t *__restrict__ sec, uint32_t nrot,
+                             uint32_t *__restrict__ flags,
                              uint32_t *__restrict__ join, uint32_t tag, uint32_t ctr_index,
                              uint32_t holders, StatusBlock *sb) {
     using C = XCfg<K, KV, V>;
@@ -928,7 +1015,7 @@ __global__ void __launch_bounds__(512, 1)
     if (call_finished(sb)) return;
     const unsigned long long lim = wait_limit(sb);
     const uint32_t tid = threadIdx.x;
-    const uint32_t total = pf[nrot];
+    const uint32_t total = sec[kSections];
     if (tid == 0) {
         mbar_init(&full[0], 1);
         mbar_init(&full[1], 1);
@@ -948,7 +1035,8 @@ __global__ void __launch_bounds__(512, 1)
         uint32_t *ctr = &sb->counters[ctr_index];
         uint32_t issued[2] = {0, 0}, drained[2] = {0, 0};
         uint32_t arrivals[2] = {0, 0};  // phases of full[q] the producer has started
-        uint32_t rot = 0;
+        uint32_t rot = 0, sech = 0;
+        const uint32_t sec_lane = lane <= kSections ? sec[lane] : ~0u;
         uint32_t st = 0;
         // "reads done" of the items staged last, published (lane 0) as soon as their
         // data has landed, while the producer waits for a stage: the flags never wait
@@ -998,7 +1086,7 @@ __global__ void __launch_bounds__(512, 1)
             t = 0;
             if (lane == 0) t = atomicAdd(ctr, 1u);
             t = __shfl_sync(0xffffffffu, t, 0);
-            if (t < total && !decode_item_warp(prm, t, rot, pf, plans, nrot, n, it)) {
+            if (t < total && !decode_item_warp(prm, t, rot, sech, pk, sec_lane, plans, nrot, n, it)) {
                 if (lane == 0) set_status(sb, IPM_ERR_DEVICE);
                 return false;
             }
@@ -1151,9 +1239,9 @@ ipm_status exchange_level_t(void *buf, void *vals, uint64_t n, uint32_t l,
                             XPlanArea pa, StatusBlock *sb, cudaStream_t stream) {
     static_assert(WS || sizeof(V) == 4, "the single-role executor moves 4-byte payloads");
     using C = XCfg<E, KV, V>;
-    using Kern = void (*)(E *, V *, uint64_t, const RotPlan *, const uint32_t *, uint32_t,
-                          uint32_t *, uint32_t *, uint32_t, uint32_t, uint32_t,
-                          StatusBlock *);
+    using Kern = void (*)(E *, V *, uint64_t, const RotPlan *, const uint32_t *,
+                          const uint32_t *, uint32_t, uint32_t *, uint32_t *, uint32_t, uint32_t,
+                          uint32_t, StatusBlock *);
     Kern kern;
     if constexpr (WS)
         kern = exchange_level_ws_kernel<E, KV, V>;
@@ -1179,8 +1267,10 @@ ipm_status exchange_level_t(void *buf, void *vals, uint64_t n, uint32_t l,
     }
     const uint64_t R = 1ull << l;
     const RotPlan *plans = reinterpret_cast<const RotPlan *>(pa.plans) + (R - 1);
-    const uint32_t *pf = pa.item_pf + (R - 1) + l;
-    kern<<<grid, C::kThreads, C::kSmem, stream>>>((E *)buf, (V *)vals, n, plans, pf, uint32_t(R),
+    const uint32_t *pk = pa.item_pf + level_prefix_offset(l);
+    const uint32_t *sec = pa.sec_start + level_section_offset(l);
+    kern<<<grid, C::kThreads, C::kSmem, stream>>>((E *)buf, (V *)vals, n, plans, pk, sec,
+                                                  uint32_t(R),
                                                   pa.flags, pa.join + (R - 1), l + 1,
                                                   kTicketCounter0 + l,
                                                   level_holders(l, holder_cap()), sb);
@@ -1215,7 +1305,8 @@ size_t xplan_area_bytes(uint32_t G, uint64_t n, ipm_dtype key, uint32_t vb) {
     const XParams prm = exchange_params(key, vb);
     size_t b = 0;
     b += align_up(sizeof(RotPlan) * P, 256);                  // plans of all levels
-    b += align_up(sizeof(uint32_t) * (P + G + 1), 256);       // item prefixes
+    b += align_up(sizeof(uint32_t) * prefix_entries(G), 256);   // item prefixes
+    b += align_up(sizeof(uint32_t) * section_entries(G), 256);  // section starts
     b += align_up(sizeof(uint32_t) * P, 256);                 // per-exchange completion
     b += align_up(sizeof(uint32_t) * max_level_items(G, n, prm), 256);  // read flags
     return b;
@@ -1240,7 +1331,9 @@ XPlanArea xplan_area_at(void *base, uint32_t G, uint64_t n, ipm_dtype key, uint3
     pa.plans = p;
     p += align_up(sizeof(RotPlan) * P, 256);
     pa.item_pf = reinterpret_cast<uint32_t *>(p);
-    p += align_up(sizeof(uint32_t) * (P + G + 1), 256);
+    p += align_up(sizeof(uint32_t) * prefix_entries(G), 256);
+    pa.sec_start = reinterpret_cast<uint32_t *>(p);
+    p += align_up(sizeof(uint32_t) * section_entries(G), 256);
     pa.join = reinterpret_cast<uint32_t *>(p);
     p += align_up(sizeof(uint32_t) * P, 256);
     pa.flags = reinterpret_cast<uint32_t *>(p);

@@ -5,10 +5,25 @@
 
 namespace ipm {
 
+// Sections of a level's ticket order (ipm_exchange.cu): section k < kSections - 1
+// holds phase k of every exchange, the last one every later phase.
+constexpr uint32_t kSections = 8;
+// Level l's per-section exchange prefixes: kSections arrays of 2^l + 1 entries.
+__host__ __device__ inline uint64_t level_prefix_offset(uint32_t l) {
+    return uint64_t(kSections) * ((1ull << l) - 1 + l);
+}
+// Level l's section starts: kSections + 1 entries.
+__host__ __device__ inline uint64_t level_section_offset(uint32_t l) {
+    return uint64_t(l) * (kSections + 1);
+}
+inline uint64_t prefix_entries(uint32_t G) { return level_prefix_offset(G); }
+inline uint64_t section_entries(uint32_t G) { return uint64_t(G) * (kSections + 1); }
+
 // Exchange plans of all levels in one workspace area (see ipm_exchange.cu).
 struct XPlanArea {
-    void *plans;        // RotPlan per exchange, level l at offset 2^l - 1
-    uint32_t *item_pf;  // item prefix per level, level l at offset 2^l - 1 + l
+    void *plans;          // RotPlan per exchange, level l at offset 2^l - 1
+    uint32_t *item_pf;    // per-section item prefixes, level l at level_prefix_offset(l)
+    uint32_t *sec_start;  // section starts, level l at level_section_offset(l)
     uint32_t *join;     // per-exchange completed-item counters, level l at 2^l - 1
     uint32_t *flags;    // per-item "reads done" flags, shared by the levels
     uint64_t nflags;

@@ -23,7 +23,8 @@ namespace {
 // Largest pair count the fixed scratch serves: P = 2^15 pairs, i.e. up to
 // 2^15 * 33,792 (~1.1e9) 4-byte keys or 2^15 * 16,896 (~5.5e8) 8-byte keys per call.
 // The workspace of such a call (sized for the fused path's split table one level
-// deeper, 2^16 + 1 entries, and the exchange plans) is ~5.2 MiB for either key width.
+// deeper, 2^16 + 1 entries, and the exchange plans with their per-section ticket
+// prefixes) is ~6.9 MiB for either key width.
 constexpr uint32_t kMaxLog2Pairs = 15;
 constexpr size_t kScratchBytes = size_t(8) << 20;  // 8 MiB
 
