@@ -85,7 +85,7 @@ FORM = {"c4-int32-batched": "batched", "c5-float32-learned": "learned"}
 # one single-pass ncu capture of that workload (dram__bytes_read.sum +
 # dram__bytes_write.sum, mean of 6 launches).  Valid for the kernel as captured; any
 # change to it voids the figure.
-EXCHANGE_TRAFFIC = {"c2-int32-uniform": 2104257323}
+EXCHANGE_TRAFFIC = {"c2-int32-uniform": 2104150869}
 # key-value workloads: the payload type per workload (payload = original buffer index)
 KV_WORKLOADS = {"c3-uint32-kv-zipf": "uint32", "f1-uint64-kv64-uniform": "uint64"}
 NP_DT = {"int32": np.int32, "uint32": np.uint32, "uint64": np.uint64, "float32": np.float32,
@@ -103,6 +103,13 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-forms", action="store_true",
                    help="skip the batched / learned side measurements")
+    p.add_argument("--batched-form", type=int, default=0, choices=[0, 1, 2],
+                   help="batched workload: launch form of the timed call (0 = default)")
+    p.add_argument("--loop-segments", type=int, default=None,
+                   help="batched workload: segments in the loop-of-plain-calls baseline "
+                        "(default all; 0 skips it)")
+    p.add_argument("--no-tune", action="store_true",
+                   help="batched workload: skip the autotuner")
     return p.parse_args()
 
 
@@ -449,20 +456,22 @@ def measure_batched(torch, ipm, workloads, dev, stream, steps, warmup, options=N
     # baseline: one ipm_merge_inplace call per segment, on the first segments
     K = la.size if loop_segments is None else min(loop_segments, la.size)
     kkeys = int((la[:K] + lb[:K]).sum())
-    wsp = ipm.workspace(ipm.ipm_merge_workspace_bytes(int(la[:K].max()), int(lb[:K].max()),
-                                                      "int32"), dev)
+    loop_ms = None
+    if K > 0:
+        wsp = ipm.workspace(ipm.ipm_merge_workspace_bytes(int(la[:K].max()),
+                                                          int(lb[:K].max()), "int32"), dev)
 
-    def loop():
-        for o, x, y in zip(offs[:K].tolist(), la[:K].tolist(), lb[:K].tolist()):
-            ipm.ipm_merge_inplace(buf[o:], x, y, "int32", wsp)
+        def loop():
+            for o, x, y in zip(offs[:K].tolist(), la[:K].tolist(), lb[:K].tolist()):
+                ipm.ipm_merge_inplace(buf[o:], x, y, "int32", wsp)
 
-    loop_ms = statistics.median(timed_steps(torch, stream, 2, prep, loop))
+        loop_ms = statistics.median(timed_steps(torch, stream, 2, prep, loop))
     peak, _ = peaks()
     min_b = 2 * n * 4
     return {
         "workload": "c4-int32-batched", "segments": int(la.size), "keys": int(n),
         "e_max": round(float(emax), 4), "max_segment": int((la + lb).max()),
-        "options": options or {"tile": 0, "order": 0, "ctas_per_sm": 0},
+        "options": options or {"tile": 0, "order": 0, "ctas_per_sm": 0, "form": 0},
         "ms_per_step": ms, "value": n / (ms * 1e-3) / 1e9, "unit": UNIT,
         "step_ms": spread(times), "autotuned": autotuned,
         "graph_ms_per_step": statistics.median(gtimes),
@@ -471,10 +480,12 @@ def measure_batched(torch, ipm, workloads, dev, stream, steps, warmup, options=N
         "merge_bytes": merge_b, "exchange_bytes": exch_b, "min_bytes": min_b,
         "method_frac": (merge_b + exch_b) / (ms * 1e-3) / 1e9 / peak,
         "min_frac": min_b / (ms * 1e-3) / 1e9 / peak,
-        "loop_baseline": {"segments": K, "keys": kkeys, "ms": loop_ms,
-                          "value": kkeys / (loop_ms * 1e-3) / 1e9,
-                          "calls": K, "note": "one ipm_merge_inplace call per segment"},
-        "speedup_vs_loop": (n / (ms * 1e-3)) / (kkeys / (loop_ms * 1e-3)),
+        "loop_baseline": None if loop_ms is None else {
+            "segments": K, "keys": kkeys, "ms": loop_ms,
+            "value": kkeys / (loop_ms * 1e-3) / 1e9,
+            "calls": K, "note": "one ipm_merge_inplace call per segment"},
+        "speedup_vs_loop": None if loop_ms is None else
+        (n / (ms * 1e-3)) / (kkeys / (loop_ms * 1e-3)),
         "sorted_check": ok_sorted, "buffer": buf, "pristine": pristine,
     }
 
@@ -789,7 +800,9 @@ def run_form(args, rank, world, torch, ipm, workloads, dev, stream, form):
     if world > 1:
         torch.distributed.barrier()
     if form == "batched":
-        m = measure_batched(torch, ipm, workloads, dev, stream, args.steps, args.warmup)
+        m = measure_batched(torch, ipm, workloads, dev, stream, args.steps, args.warmup,
+                            options={"form": args.batched_form} if args.batched_form else None,
+                            loop_segments=args.loop_segments, tune=not args.no_tune)
     else:
         m = measure_learned(torch, ipm, workloads, dev, stream, args.steps, args.warmup)
     if world > 1:
