@@ -38,10 +38,22 @@ struct PermMap {
     const uint64_t *split;  // i_0 .. i_P
     uint64_t la, n;
     uint32_t G;
+    double scale;  // 2^G / n
+
+    // The pair k with d_k <= q < d_{k+1}: an estimate in double precision, then the
+    // exact integer tests (d_k = floor(k n / 2^G), k n < 2^63) move it to the answer.
+    __device__ __forceinline__ uint64_t pair_of(uint64_t q) const {
+        const uint64_t P = 1ull << G;
+        uint64_t k = uint64_t(double(q) * scale);
+        if (k > P - 1) k = P - 1;
+        while (k > 0 && ((k * n) >> G) > q) --k;
+        while (k + 1 < P && (((k + 1) * n) >> G) <= q) ++k;
+        return k;
+    }
 
     // The position of A|B whose element belongs at q of the arranged layout.
     __device__ __forceinline__ uint64_t src(uint64_t q) const {
-        const uint64_t k = (((q + 1) << G) - 1) / n;  // d_k <= q < d_{k+1}
+        const uint64_t k = pair_of(q);  // d_k <= q < d_{k+1}
         const uint64_t dk = (k * n) >> G;
         const uint64_t ik = split[k], ak = split[k + 1] - ik;
         const uint64_t off = q - dk;
@@ -271,7 +283,7 @@ static ipm_status permute_t(void *buf_, void *vals_, uint64_t la, uint64_t lb,
     K *sk = reinterpret_cast<K *>(w + L.sk_off);
     V *sv = reinterpret_cast<V *>(w + L.sv_off);
     uint64_t *fpos = reinterpret_cast<uint64_t *>(w + L.fpos_off);
-    const PermMap m{split, la, n, G};
+    const PermMap m{split, la, n, G, double(1ull << G) / double(n)};
     const uint64_t words = (n + 31) / 32;
 
     IPM_CUDA_TRY(cudaMemsetAsync(w, 0, L.bm_off + size_t(words) * 4, st));
