@@ -214,7 +214,7 @@ ipm_status merge_core(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t 
     const uint64_t P = uint64_t(1) << Gs;
 
     {
-        PhaseScope ps(model ? 6 : 0, 2, stream);
+        PhaseScope ps(model ? 6 : 0, model ? 2u : 1u + split_launches(P), stream);
         // a0: early exit (A empty, B empty, or A[last] <= B[0]) -> later steps are no-ops
         IPM_TRY(launch_early_exit(buf, la, lb, key, sb,
                                   g_wait_limit_ns.load(std::memory_order_relaxed), stream));

@@ -48,7 +48,10 @@ ipm_status launch_early_exit(const void *buf, uint64_t la, uint64_t lb, ipm_dtyp
                              StatusBlock *sb, unsigned long long wait_limit_ns,
                              cudaStream_t stream);
 
-// Exact stable splits on d_k = floor(k*n/P), k = 0..P.  sb may be NULL.
+// Exact stable splits on d_k = floor(k*n/P), k = 0..P.  sb may be NULL.  Many diagonals
+// take two launches (split_launches): every 32nd diagonal first, then the others inside
+// the brackets their coarse neighbours give.
+uint32_t split_launches(uint64_t P);
 ipm_status launch_splits(const void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
                          uint64_t P, uint64_t *split, const StatusBlock *sb,
                          cudaStream_t stream);

@@ -23,13 +23,16 @@ __global__ void early_exit_kernel(const K *buf, uint64_t la, uint64_t lb, Status
     }
 }
 
+// The diagonals k = 0, S, 2S, ..., P (S = stride, a divisor of P): one warp each, over
+// the diagonal's whole range.
 template <typename K>
 __global__ void __launch_bounds__(256) split_kernel(const K *__restrict__ A, uint64_t la,
                                                     const K *__restrict__ B, uint64_t lb,
-                                                    uint64_t P, uint64_t *__restrict__ out,
+                                                    uint64_t P, uint64_t stride,
+                                                    uint64_t *__restrict__ out,
                                                     const StatusBlock *sb) {
     if (call_finished(sb)) return;
-    const uint64_t k = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t k = ((uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * stride;
     const unsigned lane = threadIdx.x & 31u;
     if (k > P) return;  // whole warp exits together
     const uint64_t n = la + lb;
@@ -38,14 +41,58 @@ __global__ void __launch_bounds__(256) split_kernel(const K *__restrict__ A, uin
     if (lane == 0) out[k] = i;
 }
 
+// The other diagonals, once those of split_kernel with this stride are known: both
+// i_k and j_k = d_k - i_k grow with k, so between the coarse neighbours k0 < k < k1
+//   max(i_k0, d_k - j_k1) <= i_k <= min(i_k1, d_k - j_k0),
+// a bracket of at most d_k1 - d_k0 positions instead of the diagonal's whole range.
+template <typename K>
+__global__ void __launch_bounds__(256) split_fine_kernel(const K *__restrict__ A, uint64_t la,
+                                                         const K *__restrict__ B, uint64_t lb,
+                                                         uint64_t P, uint64_t stride,
+                                                         uint64_t *__restrict__ out,
+                                                         const StatusBlock *sb) {
+    if (call_finished(sb)) return;
+    const uint64_t k = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const unsigned lane = threadIdx.x & 31u;
+    if (k > P || k % stride == 0) return;  // whole warp exits together
+    const uint64_t n = la + lb;
+    const uint64_t k0 = k / stride * stride, k1 = k0 + stride;  // k1 <= P: stride | P
+    const uint64_t d = (k * n) / P, d0 = (k0 * n) / P, d1 = (k1 * n) / P;
+    const uint64_t i0 = out[k0], i1 = out[k1];
+    const uint64_t j0 = d0 - i0, j1 = d1 - i1;
+    uint64_t lo = d > lb ? d - lb : 0, hi = d < la ? d : la;
+    if (i0 > lo) lo = i0;
+    if (d > j1 && d - j1 > lo) lo = d - j1;
+    if (i1 < hi) hi = i1;
+    if (d - j0 < hi) hi = d - j0;  // j0 <= j_k <= d
+    const uint64_t i = warp_split_bracket<true>(A, B, d, lo, hi);
+    if (lane == 0) out[k] = i;
+}
+
+// Coarse diagonals first when there are many: the fine ones then search ~32x narrower
+// brackets (about two rounds of 33 probes fewer each).
+constexpr uint64_t kSplitStride = 32;
+constexpr uint64_t kTwoPassPairs = 2048;
+
+bool two_pass(uint64_t P) { return P >= kTwoPassPairs && P % kSplitStride == 0; }
+
 template <typename K>
 ipm_status splits_t(const void *buf, uint64_t la, uint64_t lb, uint64_t P, uint64_t *split,
                     const StatusBlock *sb, cudaStream_t stream) {
     const K *A = static_cast<const K *>(buf);
-    const uint64_t warps = P + 1;
+    const bool two = two_pass(P);
+    const uint64_t stride = two ? kSplitStride : 1;
+    const uint64_t warps = P / stride + 1;
     const uint64_t blocks = (warps * 32 + 255) / 256;
-    if (blocks > 0x7fffffffull) return IPM_ERR_INVALID_ARG;
-    split_kernel<K><<<unsigned(blocks), 256, 0, stream>>>(A, la, A + la, lb, P, split, sb);
+    if (blocks > 0x7fffffffull || (P + 1) * 32 / 256 + 1 > 0x7fffffffull)
+        return IPM_ERR_INVALID_ARG;
+    split_kernel<K><<<unsigned(blocks), 256, 0, stream>>>(A, la, A + la, lb, P, stride, split,
+                                                          sb);
+    if (!two) return last_launch_status();
+    IPM_TRY(last_launch_status());
+    const uint64_t fblocks = ((P + 1) * 32 + 255) / 256;
+    split_fine_kernel<K><<<unsigned(fblocks), 256, 0, stream>>>(A, la, A + la, lb, P, stride,
+                                                                split, sb);
     return last_launch_status();
 }
 
@@ -80,6 +127,8 @@ ipm_status launch_early_exit(const void *buf, uint64_t la, uint64_t lb, ipm_dtyp
     }
     return last_launch_status();
 }
+
+uint32_t split_launches(uint64_t P) { return two_pass(P) ? 2u : 1u; }
 
 ipm_status launch_splits(const void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
                          uint64_t P, uint64_t *split, const StatusBlock *sb,

@@ -48,6 +48,29 @@ def test_splits_match_oracle(ipm, dev, orc, dt, dist):
         assert np.array_equal(got, want), (la, lb, P)
 
 
+@pytest.mark.parametrize("dt", [np.int32, np.uint64, np.float32, np.int64])
+@pytest.mark.parametrize("dist", ["uniform", "dup16", "zipf", "disjoint", "revdisjoint"])
+def test_two_pass_splits_match_oracle(ipm, dev, orc, dt, dist):
+    """Many diagonals (P >= 2048, a multiple of 32) take two passes: every 32nd diagonal
+    over its whole range, then the others inside the brackets their coarse neighbours
+    give; every entry equals the oracle's replayed split, including runs of equal keys
+    across the brackets, one-sided regions and unbalanced runs."""
+    import torch
+
+    if dist == "zipf" and dt == np.float32:
+        dist = "dup16"
+    for la, lb, P in [(1_500_007, 1_400_011, 2048), (3_000_017, 41, 4096),
+                      (37, 2_200_003, 8192), (600_001, 600_001, 16_384), (5000, 7000, 2048)]:
+        a, b = W.make_pair(dist, dt, la, lb, seed=la + 3 * lb)
+        buf = to_dev(np.concatenate([a, b]), dev)
+        out = torch.empty(P + 1, dtype=torch.int64, device=dev)
+        ipm.ipm_merge_splits(buf, la, lb, NAME[np.dtype(dt)], P, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.uint64)
+        want = orc.splits_replay(a, b, orc.diagonals(la + lb, P))
+        assert np.array_equal(got, want), (la, lb, P, dist)
+
+
 # ----------------------------------------------------------------------- step a2
 
 @pytest.mark.parametrize("elem", [4, 8])
