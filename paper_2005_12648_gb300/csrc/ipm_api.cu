@@ -214,7 +214,8 @@ ipm_status merge_core(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t 
     const uint64_t P = uint64_t(1) << Gs;
 
     {
-        PhaseScope ps(model ? 6 : 0, model ? 2u : 1u + split_launches(P), stream);
+        PhaseScope ps(model ? 6 : 0,
+                      1u + (model ? learned_split_launches(P) : split_launches(P)), stream);
         // a0: early exit (A empty, B empty, or A[last] <= B[0]) -> later steps are no-ops
         IPM_TRY(launch_early_exit(buf, la, lb, key, sb,
                                   g_wait_limit_ns.load(std::memory_order_relaxed), stream));
@@ -622,7 +623,7 @@ ipm_status ipm_merge_splits_learned(const void *d_buf, uint64_t len_a, uint64_t 
         !aligned(d_model, 4) || !aligned(d_stats, 8))
         return IPM_ERR_ALIGNMENT;
     cudaStream_t st = (cudaStream_t)stream;
-    PhaseScope ps(6, 1, st);
+    PhaseScope ps(6, learned_split_launches(num_pairs), st);
     return launch_learned_splits(d_buf, len_a, len_b, key_dtype, num_pairs, d_model, d_split_a,
                                  d_stats, nullptr, st);
 }

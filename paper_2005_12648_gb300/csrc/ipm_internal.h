@@ -52,6 +52,8 @@ ipm_status launch_early_exit(const void *buf, uint64_t la, uint64_t lb, ipm_dtyp
 // take two launches (split_launches): every 32nd diagonal first, then the others inside
 // the brackets their coarse neighbours give.
 uint32_t split_launches(uint64_t P);
+// The same for the learned splits (launch_learned_splits).
+uint32_t learned_split_launches(uint64_t P);
 ipm_status launch_splits(const void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
                          uint64_t P, uint64_t *split, const StatusBlock *sb,
                          cudaStream_t stream);

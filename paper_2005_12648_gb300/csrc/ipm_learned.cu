@@ -181,12 +181,46 @@ __global__ void reset_status_kernel(StatusBlock *sb) {
     if (threadIdx.x == 0) sb->status = 0u;
 }
 
-// Exact splits on d_k = floor(k*n/P) from the model's proposals (MODEL) or by the plain
-// bracket search; STATS accumulates probe counts and proposal errors.
+// Accumulate one diagonal's search counts and proposal error (lane 0).
+__device__ __forceinline__ void add_stats(ipm_split_stats *stats, uint32_t rounds,
+                                          uint32_t probes, uint64_t err) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(&stats->diagonals), 1ull);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&stats->rounds),
+              (unsigned long long)rounds);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&stats->probes),
+              (unsigned long long)probes);
+    atomicAdd(reinterpret_cast<unsigned long long *>(&stats->abs_err_sum),
+              (unsigned long long)err);
+    atomicMax(reinterpret_cast<unsigned long long *>(&stats->abs_err_max),
+              (unsigned long long)err);
+}
+
+// One galloping round from `guess` inside [lo, hi): the lanes probe the offsets
+// -2^15 .. -1 (lanes 0..15), 0, 1, 3, .., 2^15 - 1 around it (clamped to the range) at
+// once, and the ballot narrows [lo, hi] to the bracket that holds the split.
+template <typename K>
+__device__ __forceinline__ void gallop_round(const K *A, const K *B, uint64_t d, uint64_t guess,
+                                             uint64_t &lo, uint64_t &hi) {
+    const unsigned lane = threadIdx.x & 31u;
+    const int64_t off = lane < 16 ? -(int64_t(1) << (15 - lane)) : (int64_t(1) << (lane - 16)) - 1;
+    int64_t m = int64_t(guess) + off;
+    const int64_t mlo = int64_t(lo), mhi = int64_t(hi) - 1;
+    m = m < mlo ? mlo : m > mhi ? mhi : m;
+    const bool p = key_le(A[m], B[d - 1 - uint64_t(m)]);
+    const int c = __popc(__ballot_sync(0xffffffffu, p));
+    const int64_t m_lo = __shfl_sync(0xffffffffu, m, c > 0 ? c - 1 : 0);
+    const int64_t m_hi = __shfl_sync(0xffffffffu, m, c < 32 ? c : 31);
+    if (c > 0) lo = uint64_t(m_lo) + 1;
+    if (c < 32) hi = uint64_t(m_hi);
+}
+
+// Exact splits on d_k = floor(k*n/P) for k = 0, S, 2S, ..., P (S = stride) from the
+// model's proposals (MODEL) or by the plain bracket search; STATS accumulates probe
+// counts and proposal errors.
 template <typename K, bool MODEL, bool STATS>
 __global__ void __launch_bounds__(256)
     learned_split_kernel(const K *__restrict__ A, uint64_t la, const K *__restrict__ B,
-                         uint64_t lb, uint64_t P, const ipm_split_model *model,
+                         uint64_t lb, uint64_t P, uint64_t stride, const ipm_split_model *model,
                          uint64_t *__restrict__ out, ipm_split_stats *stats,
                          const StatusBlock *sb) {
     __shared__ float prm[kNP];
@@ -195,7 +229,7 @@ __global__ void __launch_bounds__(256)
         __syncthreads();
     }
     if (call_finished(sb)) return;
-    const uint64_t k = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t k = ((uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * stride;
     const unsigned lane = threadIdx.x & 31u;
     if (k > P) return;  // whole warp exits together
     const uint64_t n = la + lb;
@@ -209,18 +243,7 @@ __global__ void __launch_bounds__(256)
         const double g = rint(double(y) * double(la));
         // clamp to the diagonal's range (a NaN proposal becomes lo)
         guess = g > double(lo) ? (g < double(hi) ? uint64_t(g) : hi) : lo;
-        // one galloping round: offsets -2^15 .. -1 (lanes 0..15), 0, 1, 3, .., 2^15-1
-        const int64_t off = lane < 16 ? -(int64_t(1) << (15 - lane))
-                                      : (int64_t(1) << (lane - 16)) - 1;
-        int64_t m = int64_t(guess) + off;
-        const int64_t mlo = int64_t(lo), mhi = int64_t(hi) - 1;
-        m = m < mlo ? mlo : m > mhi ? mhi : m;
-        const bool p = key_le(A[m], B[d - 1 - uint64_t(m)]);
-        const int c = __popc(__ballot_sync(0xffffffffu, p));
-        const int64_t m_lo = __shfl_sync(0xffffffffu, m, c > 0 ? c - 1 : 0);
-        const int64_t m_hi = __shfl_sync(0xffffffffu, m, c < 32 ? c : 31);
-        if (c > 0) lo = uint64_t(m_lo) + 1;
-        if (c < 32) hi = uint64_t(m_hi);
+        gallop_round(A, B, d, guess, lo, hi);
         rounds = 1;
         probes = 32;
     }
@@ -228,19 +251,79 @@ __global__ void __launch_bounds__(256)
     const uint64_t i = warp_split_bracket<true, STATS>(A, B, d, lo, hi, &r2, &p2);
     if (lane == 0) {
         out[k] = i;
-        if (STATS) {
-            const uint64_t err = MODEL ? (guess > i ? guess - i : i - guess) : 0;
-            atomicAdd(reinterpret_cast<unsigned long long *>(&stats->diagonals), 1ull);
-            atomicAdd(reinterpret_cast<unsigned long long *>(&stats->rounds),
-                      (unsigned long long)(rounds + r2));
-            atomicAdd(reinterpret_cast<unsigned long long *>(&stats->probes),
-                      (unsigned long long)(probes + p2));
-            atomicAdd(reinterpret_cast<unsigned long long *>(&stats->abs_err_sum),
-                      (unsigned long long)err);
-            atomicMax(reinterpret_cast<unsigned long long *>(&stats->abs_err_max),
-                      (unsigned long long)err);
-        }
+        if (STATS) add_stats(stats, rounds + r2, probes + p2,
+                             MODEL ? (guess > i ? guess - i : i - guess) : 0);
     }
+}
+
+// The other diagonals, once those of learned_split_kernel with this stride are known:
+// the split lies in the bracket of its coarse neighbours k0 < k < k1 (both i_k and
+// j_k = d_k - i_k grow with k).  With PROPOSE the search starts at the piecewise-linear
+// model through the exact coarse splits (i_k0 + (i_k1 - i_k0) (d_k - d_k0) / (d_k1 -
+// d_k0), clamped to the bracket) with one galloping round; without, the plain bracket
+// search.
+template <typename K, bool PROPOSE, bool STATS>
+__global__ void __launch_bounds__(256)
+    learned_fine_kernel(const K *__restrict__ A, uint64_t la, const K *__restrict__ B,
+                        uint64_t lb, uint64_t P, uint64_t stride, uint64_t *__restrict__ out,
+                        ipm_split_stats *stats, const StatusBlock *sb) {
+    if (call_finished(sb)) return;
+    const uint64_t k = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const unsigned lane = threadIdx.x & 31u;
+    if (k > P || k % stride == 0) return;  // whole warp exits together
+    const uint64_t n = la + lb;
+    const uint64_t k0 = k / stride * stride, k1 = k0 + stride;  // k1 <= P: stride | P
+    const uint64_t d = (k * n) / P, d0 = (k0 * n) / P, d1 = (k1 * n) / P;
+    const uint64_t i0 = out[k0], i1 = out[k1];
+    const uint64_t j0 = d0 - i0, j1 = d1 - i1;
+    uint64_t lo = d > lb ? d - lb : 0, hi = d < la ? d : la;
+    if (i0 > lo) lo = i0;
+    if (d > j1 && d - j1 > lo) lo = d - j1;
+    if (i1 < hi) hi = i1;
+    if (d - j0 < hi) hi = d - j0;
+    uint64_t guess = lo;
+    uint32_t rounds = 0, probes = 0;
+    if (PROPOSE && hi > lo) {
+        const double g = double(i0) + rint(double(i1 - i0) * (double(d - d0) / double(d1 - d0)));
+        guess = g > double(lo) ? (g < double(hi) ? uint64_t(g) : hi) : lo;
+        gallop_round(A, B, d, guess, lo, hi);
+        rounds = 1;
+        probes = 32;
+    }
+    uint32_t r2 = 0, p2 = 0;
+    const uint64_t i = warp_split_bracket<true, STATS>(A, B, d, lo, hi, &r2, &p2);
+    if (lane == 0) {
+        out[k] = i;
+        if (STATS) add_stats(stats, rounds + r2, probes + p2,
+                             PROPOSE ? (guess > i ? guess - i : i - guess) : 0);
+    }
+}
+
+// Every 32nd diagonal first when there are 2,048 or more (a multiple of 32), then the
+// others inside the brackets of their coarse neighbours; with a model, the coarse
+// diagonals start at the model's proposals and the fine ones at the piecewise-linear
+// model through the coarse splits.  Without a model, the plain searches of
+// ipm_merge_splits.
+constexpr uint64_t kLearnedStride = 32;
+constexpr uint64_t kLearnedTwoPass = 2048;
+
+template <typename K, bool MODEL, bool STATS>
+ipm_status learned_splits_v(const K *A, uint64_t la, uint64_t lb, uint64_t P,
+                            const ipm_split_model *model, uint64_t *split,
+                            ipm_split_stats *stats, const StatusBlock *sb,
+                            cudaStream_t stream) {
+    const bool two = P >= kLearnedTwoPass && P % kLearnedStride == 0;
+    const uint64_t stride = two ? kLearnedStride : 1;
+    const uint64_t blocks = ((P / stride + 1) * 32 + 255) / 256;
+    const uint64_t fblocks = ((P + 1) * 32 + 255) / 256;
+    if (fblocks > 0x7fffffffull) return IPM_ERR_INVALID_ARG;
+    learned_split_kernel<K, MODEL, STATS><<<unsigned(blocks), 256, 0, stream>>>(
+        A, la, A + la, lb, P, stride, model, split, stats, sb);
+    if (!two) return last_launch_status();
+    IPM_TRY(last_launch_status());
+    learned_fine_kernel<K, MODEL, STATS><<<unsigned(fblocks), 256, 0, stream>>>(
+        A, la, A + la, lb, P, stride, split, stats, sb);
+    return last_launch_status();
 }
 
 template <typename K>
@@ -249,25 +332,15 @@ ipm_status learned_splits_t(const void *buf, uint64_t la, uint64_t lb, uint64_t 
                             ipm_split_stats *stats, const StatusBlock *sb,
                             cudaStream_t stream) {
     const K *A = static_cast<const K *>(buf);
-    const uint64_t blocks = ((P + 1) * 32 + 255) / 256;
-    if (blocks > 0x7fffffffull) return IPM_ERR_INVALID_ARG;
-    const unsigned g = unsigned(blocks);
-    if (model != nullptr) {
-        if (stats != nullptr)
-            learned_split_kernel<K, true, true><<<g, 256, 0, stream>>>(A, la, A + la, lb, P,
-                                                                     model, split, stats, sb);
-        else
-            learned_split_kernel<K, true, false><<<g, 256, 0, stream>>>(
-                A, la, A + la, lb, P, model, split, nullptr, sb);
-    } else {
-        if (stats != nullptr)
-            learned_split_kernel<K, false, true><<<g, 256, 0, stream>>>(
-                A, la, A + la, lb, P, nullptr, split, stats, sb);
-        else
-            learned_split_kernel<K, false, false><<<g, 256, 0, stream>>>(
-                A, la, A + la, lb, P, nullptr, split, nullptr, sb);
-    }
-    return last_launch_status();
+    if (model != nullptr)
+        return stats != nullptr
+                   ? learned_splits_v<K, true, true>(A, la, lb, P, model, split, stats, sb, stream)
+                   : learned_splits_v<K, true, false>(A, la, lb, P, model, split, nullptr, sb,
+                                                      stream);
+    return stats != nullptr
+               ? learned_splits_v<K, false, true>(A, la, lb, P, nullptr, split, stats, sb, stream)
+               : learned_splits_v<K, false, false>(A, la, lb, P, nullptr, split, nullptr, sb,
+                                                   stream);
 }
 
 template <typename K>
@@ -280,6 +353,10 @@ ipm_status targets_t(const void *buf, uint64_t la, uint64_t lb, const uint64_t *
 }
 
 }  // namespace
+
+uint32_t learned_split_launches(uint64_t P) {
+    return P >= kLearnedTwoPass && P % kLearnedStride == 0 ? 2u : 1u;
+}
 
 ipm_status launch_learned_splits(const void *buf, uint64_t la, uint64_t lb, ipm_dtype key,
                                  uint64_t P, const ipm_split_model *model, uint64_t *split,
