@@ -859,21 +859,19 @@ def run_e2e_batched(torch, ipm, workloads, m, steps, stream, dev):
     offs = np.concatenate([[0], np.cumsum(la + lb)[:-1]]).astype(np.int64)
     segs = ipm.segment_table(offs, la, lb, dev)
     n = pristine.numel()
-    wss = [ipm.workspace(ipm.ipm_merge_batched_workspace_bytes(n, la.size, "int32"), dev)
-           for _ in range(2)]
+    ws = ipm.workspace(ipm.ipm_merge_batched_workspace_bytes(n, la.size, "int32"), dev)
     return run_e2e(torch, [pristine], steps,
                    lambda d, k, st: ipm.ipm_merge_batched(d[0], None, n, segs, la.size, "int32",
-                                                          wss[k], stream=st))
+                                                          ws, stream=st))
 
 
 def run_e2e_learned(torch, ipm, m, steps, stream, model):
     pristine = m["pristine"]
     la = lb = pristine.numel() // 2
-    wss = [ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, "float32"), pristine.device)
-           for _ in range(2)]
+    ws = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, "float32"), pristine.device)
     return run_e2e(torch, [pristine], steps,
                    lambda d, k, st: ipm.ipm_merge_inplace_learned(d[0], la, lb, "float32", model,
-                                                                  wss[k], stream=st))
+                                                                  ws, stream=st))
 
 
 def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
@@ -977,9 +975,8 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
 
     e2e = None
     if not args.no_e2e:
-        ws2 = ipm.workspace(ipm.ipm_merge_workspace_bytes(la, lb, dt, with_values=vbytes), dev)
         e2e = run_e2e(torch, [pristine, vpristine] if kv else [pristine], args.steps,
-                      lambda d, k, st: merge(d[0], d[1] if kv else None, (ws, ws2)[k], st))
+                      lambda d, k, st: merge(d[0], d[1] if kv else None, ws, st))
         e2e = e2e_over_ranks(torch, e2e, world, dev)
     del buf, pristine, vbuf, vpristine
 
@@ -1027,52 +1024,60 @@ def run_plain(args, rank, world, torch, ipm, workloads, dev, stream):
     }
 
 
-def run_e2e(torch, pristines, steps, merge):
+def run_e2e(torch, pristines, steps, merge, slots=3):
     """The merge through the public API with host buffers, as a caller merging a stream
     of inputs runs it: every step copies its input (keys, and payloads for key-value)
-    from pinned host memory, merges it and copies the result back to pinned host memory;
-    consecutive steps alternate between two streams, each with its own device buffers
-    and workspace (merge(device buffers, slot, stream)), so one step's copy back overlaps
-    the next step's copy in (the link carries both directions at once).  Timed from
-    before the first copy in to after the last copy back."""
+    from pinned host memory, merges it and copies the result back to pinned host memory.
+    Three streams carry the copies in, the merges and the copies back; `slots` sets of
+    device buffers rotate between them (a buffer's next copy in waits for its last copy
+    back), so one step's copy in, another's merge and a third's copy back run at once
+    and the link carries both directions together.  The merges run one after another on
+    their stream, so one workspace serves them (merge(device buffers, slot, stream)).
+    Timed from before the first copy in to after the last copy back."""
     host_in = [p.cpu().pin_memory() for p in pristines]
-    host_out = [[torch.empty_like(h).pin_memory() for h in host_in] for _ in range(2)]
-    dbuf = [[torch.empty_like(p) for p in pristines] for _ in range(2)]
-    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-    merged = [torch.cuda.Event(), torch.cuda.Event()]
+    host_out = [[torch.empty_like(h).pin_memory() for h in host_in] for _ in range(slots)]
+    dbuf = [[torch.empty_like(p) for p in pristines] for _ in range(slots)]
+    s_in, s_merge, s_out = (torch.cuda.Stream() for _ in range(3))
+    ev_in = [torch.cuda.Event() for _ in range(slots)]
+    ev_merged = [torch.cuda.Event() for _ in range(slots)]
+    ev_out = [torch.cuda.Event() for _ in range(slots)]
+    used = [False] * slots
 
     def step(k):
-        st = streams[k % 2]
-        with torch.cuda.stream(st):
-            for d, h in zip(dbuf[k % 2], host_in):
+        q = k % slots
+        if used[q]:
+            s_in.wait_event(ev_out[q])  # the buffers' previous result has been read back
+        with torch.cuda.stream(s_in):
+            for d, h in zip(dbuf[q], host_in):
                 d.copy_(h, non_blocking=True)
-            # merges never overlap each other (their persistent kernels each take the
-            # whole GPU); only the copies overlap
-            if k > 0:
-                st.wait_event(merged[(k - 1) % 2])
-            merge(dbuf[k % 2], k % 2, st)
-            merged[k % 2].record(st)
-            for h, d in zip(host_out[k % 2], dbuf[k % 2]):
+            ev_in[q].record(s_in)
+        s_merge.wait_event(ev_in[q])
+        merge(dbuf[q], q, s_merge)
+        ev_merged[q].record(s_merge)
+        s_out.wait_event(ev_merged[q])
+        with torch.cuda.stream(s_out):
+            for h, d in zip(host_out[q], dbuf[q]):
                 h.copy_(d, non_blocking=True)
+            ev_out[q].record(s_out)
+        used[q] = True
 
-    for k in range(2):
+    for k in range(slots):
         step(k)
     torch.cuda.synchronize()
-    start, mid, end = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    start.record(streams[0])
-    streams[1].wait_event(start)
+    start, end = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    start.record(s_in)
+    s_merge.wait_event(start)
+    s_out.wait_event(start)
     for k in range(steps):
         step(k)
-    mid.record(streams[1])
-    streams[0].wait_event(mid)
-    end.record(streams[0])
+    end.record(s_out)
     torch.cuda.synchronize()
     ms = start.elapsed_time(end) / steps
     nbytes = sum(p.numel() * p.element_size() for p in pristines)
     return {"value": pristines[0].numel() / (ms * 1e-3) / 1e9, "unit": UNIT,
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "ms_per_step": ms,
             "keys_per_step": pristines[0].numel(),
-            "pipelined": "steps alternate between two streams (copy in / copy back overlap)"}
+            "pipelined": f"{slots} buffer sets over three streams (copy in, merge, copy back)"}
 
 
 def main():
