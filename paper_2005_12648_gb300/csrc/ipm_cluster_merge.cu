@@ -292,7 +292,11 @@ __global__ void __launch_bounds__(THREADS, 2)
 // pair is stored from shared memory and the first brought back from TMEM (each thread
 // its own lane and columns) and stored the same way.  Tickets cover pairs 2t and 2t+1
 // (one group: groups are aligned to 2^F >= 2 pairs); the ticket-order argument of the
-// one-pair kernel holds with 2^(F-1) claims per group.  Exactly two CTAs fit an SM
+// one-pair kernel holds with 2^(F-1) claims per group.  The barrier is per pair: a pair,
+// once staged, counts its slices in at the pairs whose outputs overwrite them
+// (count_in_slice), and a pair stores once its own count covers its output, that is
+// once the few members that read its destination have their data on chip, not the
+// whole group.  Exactly two CTAs fit an SM
 // (each CTA takes at least kGroup2Smem of shared memory), so the two allocations never
 // wait.
 // ---------------------------------------------------------------------------------
@@ -335,7 +339,6 @@ __global__ void __launch_bounds__(THREADS, 2)
     if (sb == nullptr || call_finished(sb)) return;
     const uint32_t tid = threadIdx.x, warp = tid >> 5;
     const uint64_t claims = (1ull << G) >> 1;
-    const uint32_t gsize = 1u << (F - 1);  // claims per group
     if (warp == 0) {
         tmem_alloc<kGroup2Cols>(&s_taddr);
         tmem_relinquish();
@@ -402,6 +405,10 @@ __global__ void __launch_bounds__(THREADS, 2)
         // ---- first pair: stage, merge into registers, park in TMEM
         stage(g0);
         __syncthreads();  // every thread's head / tail loads have landed too
+        if (tid == 0 && !abort_flag) {  // its slices are on chip
+            count_in_slice(gctr, la + lb, G, uint64_t(g0.gA - buf), g0.a);
+            count_in_slice(gctr, la + lb, G, uint64_t(g0.gB - buf), g0.b);
+        }
         {
             K ok[E] = {};  // outputs past the pair's end are parked but never read back
             V ov[KV ? E : 1] = {};
@@ -439,21 +446,24 @@ __global__ void __launch_bounds__(THREADS, 2)
         // ---- second pair: stage, count in, merge on chip into the output's phase
         stage(g1);
         __syncthreads();
-        if (tid == 0)  // both pairs' slices have been read
-            atomicAdd(gctr + (*((volatile uint32_t *)&s_t[cur]) >> (F - 1)), 1u);
+        if (tid == 0 && !abort_flag) {
+            count_in_slice(gctr, la + lb, G, uint64_t(g1.gA - buf), g1.a);
+            count_in_slice(gctr, la + lb, G, uint64_t(g1.gB - buf), g1.b);
+        }
         if (!abort_flag && g1.a + g1.b > 0)
             merge_two<K, KV, THREADS, E, true, V>(R + g1.offA, RV + g1.offAV, g1.a,
                                                   g1.offB - g1.offA, g1.offBV - g1.offAV, g1.b,
                                                   R + g1.oo, RV + g1.ooV);
         fence_proxy_async_smem();
 
-        // ---- group barrier: the group's region may be written once every member has
-        // its slices on chip
+        // ---- barrier: each pair's output range may be written once every element it
+        // overwrites is on chip (its count reaches its length)
         if (tid == 0 && !abort_flag) {
-            const uint32_t *ctr = gctr + (*((volatile uint32_t *)&s_t[cur]) >> (F - 1));
+            const uint64_t p0 = 2ull * *((volatile uint32_t *)&s_t[cur]);
+            const uint32_t c0 = g0.a + g0.b, c1 = g1.a + g1.b;
             DepTimer tm(wait_limit(sb));
-            while (ld_acquire_u32(ctr) < gsize)
-                if (tm.expired()) {
+            while (ld_acquire_u32(gctr + p0) < c0 || ld_acquire_u32(gctr + p0 + 1) < c1)
+                if (tm.expired() || *((volatile unsigned *)&sb->status) != 0) {
                     abort_flag = 1;
                     break;
                 }
@@ -840,7 +850,8 @@ uint32_t usable_group2_levels(ipm_dtype key, uint32_t vb, uint32_t wanted) {
 ipm_status launch_group2_merge(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t lb,
                                ipm_dtype key, const uint64_t *split, uint32_t G, uint32_t F,
                                uint32_t *gctr, StatusBlock *sb, cudaStream_t stream) {
-    IPM_CUDA_TRY(cudaMemsetAsync(gctr, 0, sizeof(uint32_t) * size_t((1ull << G) >> F), stream));
+    // one count per pair (the per-pair barrier)
+    IPM_CUDA_TRY(cudaMemsetAsync(gctr, 0, sizeof(uint32_t) * size_t(1ull << G), stream));
     switch (key) {
     case IPM_INT32:
         return group2_dispatch<int32_t>(buf, vals, vb, la, lb, split, G, F, gctr, sb, stream);

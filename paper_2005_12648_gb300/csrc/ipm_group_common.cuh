@@ -84,6 +84,23 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
     return v;
 }
 
+// Thread 0 of a CTA that has a slice [s, s + len) of the buffer on chip: count it in at
+// the pairs whose output ranges [d_k, d_k+1) (d_k = floor(k n / 2^G)) it overlaps, one
+// count per element.  Within a group the members' slices tile the group's region
+// exactly, so pair k's counter reaches d_k+1 - d_k once every element its output
+// overwrites is on chip.  (k n and (x + 1) 2^G stay below 2^64: a plan has n < 2^38.)
+__device__ __forceinline__ void count_in_slice(uint32_t *cnt, uint64_t n, uint32_t G,
+                                               uint64_t s, uint64_t len) {
+    const uint64_t e = s + len;
+    for (uint64_t x = s; x < e;) {
+        const uint64_t k = (((x + 1) << G) - 1) / n;  // the last k with d_k <= x
+        const uint64_t dk1 = ((k + 1) * n) >> G;       // > x
+        const uint64_t y = dk1 < e ? dk1 : e;
+        atomicAdd(cnt + k, uint32_t(y - x));
+        x = y;
+    }
+}
+
 // The geometry of pair k within its group of 2^F pairs (the group's region holds A's
 // slices of the group, then B's): where its two slices are, where its output goes, and
 // their phases in the staging buffer.
