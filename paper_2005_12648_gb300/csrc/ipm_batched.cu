@@ -178,6 +178,141 @@ __global__ void __launch_bounds__(kPrepThreads)
     if (tid == 0) sb->counters[kMultiCount] = nmulti;
 }
 
+constexpr uint32_t kPrepChunk = 2048;  // descriptors per chunk of the many-CTA preparation
+
+// Chunk c's length-bucket counts into s_cnt (the block; s_cnt zeroed here).
+__device__ __forceinline__ void chunk_counts(const ipm_segment *__restrict__ segs,
+                                             uint32_t nseg, uint32_t c, uint32_t *s_cnt) {
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t q = tid; q < kOrderBuckets; q += kPrepThreads) s_cnt[q] = 0u;
+    __syncthreads();
+    const uint32_t i0 = c * kPrepChunk;
+    const uint32_t i1 = nseg - i0 < kPrepChunk ? nseg : i0 + kPrepChunk;
+    for (uint32_t i = i0 + tid; i < i1; i += kPrepThreads) {
+        const uint64_t n = segs[i].len_a + segs[i].len_b;
+        atomicAdd(&s_cnt[n ? size_bucket(n) : 0u], 1u);
+    }
+    __syncthreads();
+}
+
+// The size-ordered preparation by many CTAs (the grid is at most one CTA per SM, so all
+// are resident and the waits on each other end).  The launcher has zeroed the status
+// block, its counters and the global bucket counts and cursors.  Each CTA takes chunks
+// blockIdx.x, blockIdx.x + gridDim.x, ... of kPrepChunk descriptors: it adds a chunk's
+// bucket counts to the global ones; once every chunk is counted, it takes the chunk's
+// slots in every bucket (bucket starts from the global counts, largest bucket first)
+// and scatters the chunk's descriptors there, checking each segment.  CTA 0 then waits
+// for every chunk to be scattered and lists the multi-tile segments, which lead the
+// queue, as the one-CTA preparation does.  Waits are bounded (IPM_ERR_TIMEOUT).
+__global__ void __launch_bounds__(kPrepThreads)
+    batched_prep_multi_kernel(const ipm_segment *__restrict__ segs, uint32_t nseg,
+                              uint64_t buf_len, uint64_t tile, uint64_t max_seg, QueueArea qa,
+                              StatusBlock *sb) {
+    __shared__ uint32_t s_cnt[kOrderBuckets], s_base[kOrderBuckets], s_slot[kOrderBuckets];
+    __shared__ int s_ok;
+    __shared__ uint32_t nmulti;
+    const uint32_t tid = threadIdx.x;
+    const uint32_t C = (nseg + kPrepChunk - 1) / kPrepChunk;
+    const unsigned long long lim = wait_limit(sb);
+    for (uint32_t c = blockIdx.x; c < C; c += gridDim.x) {
+        chunk_counts(segs, nseg, c, s_cnt);
+        for (uint32_t q = tid; q < kOrderBuckets; q += kPrepThreads)
+            if (s_cnt[q]) atomicAdd(&qa.hist[q], s_cnt[q]);
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicAdd(&sb->counters[kHistDone], 1u);
+    }
+    if (tid == 0) s_ok = wait_at_least(&sb->counters[kHistDone], C, lim);
+    __syncthreads();
+    if (!s_ok) {
+        if (tid == 0) set_status(sb, IPM_ERR_TIMEOUT);
+        return;
+    }
+    // bucket starts: exclusive scan of the totals from the largest bucket down
+    if (tid < 32) {
+        uint32_t carry = 0;
+        for (int base = int(kOrderBuckets) - 32; base >= 0; base -= 32) {
+            const uint32_t q = uint32_t(base) + 31u - tid;  // descending in the chunk
+            const uint32_t v = __ldcg(&qa.hist[q]);
+            uint32_t x = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (int(tid) >= o) x += y;
+            }
+            s_base[q] = carry + x - v;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+    __syncthreads();
+    for (uint32_t c = blockIdx.x; c < C; c += gridDim.x) {
+        chunk_counts(segs, nseg, c, s_cnt);
+        // this chunk's slots in every bucket
+        for (uint32_t q = tid; q < kOrderBuckets; q += kPrepThreads)
+            s_slot[q] = s_cnt[q] ? s_base[q] + atomicAdd(&qa.cursor[q], s_cnt[q]) : 0u;
+        __syncthreads();
+        const uint32_t i0 = c * kPrepChunk;
+        const uint32_t i1 = nseg - i0 < kPrepChunk ? nseg : i0 + kPrepChunk;
+        for (uint32_t i = i0 + tid; i < i1; i += kPrepThreads) {
+            const ipm_segment sg = segs[i];
+            const uint64_t n = sg.len_a + sg.len_b;
+            qa.queue[atomicAdd(&s_slot[n ? size_bucket(n) : 0u], 1u)] = sg;
+            if (seg_class(sg, buf_len, tile, max_seg) == kSegInvalid)
+                set_status(sb, IPM_ERR_INVALID_ARG);  // left untouched
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicAdd(&sb->counters[kScatterDone], 1u);
+    }
+    if (blockIdx.x != 0) return;
+    if (tid == 0) {
+        s_ok = wait_at_least(&sb->counters[kScatterDone], C, lim);
+        nmulti = 0;
+    }
+    __syncthreads();
+    if (!s_ok) {
+        if (tid == 0) set_status(sb, IPM_ERR_TIMEOUT);
+        return;
+    }
+    // the multi-tile segments lead the queue (descending buckets): read it back, through
+    // L2 (other CTAs wrote it), until a bucket entirely below the tile shows
+    __shared__ uint32_t done;
+    if (tid == 0) done = 0;
+    __syncthreads();
+    const uint32_t first_multi_bucket = size_bucket(tile + 1);
+    constexpr uint32_t kStride = kPrepThreads * kPrepBatch;
+    for (uint32_t t0 = 0; t0 < nseg && !done; t0 += kStride) {
+        ipm_segment sg[kPrepBatch];
+#pragma unroll
+        for (uint32_t j = 0; j < kPrepBatch; ++j) {
+            const uint32_t q = t0 + j * kPrepThreads + tid;
+            if (q < nseg) {
+                const unsigned long long *e =
+                    reinterpret_cast<const unsigned long long *>(&qa.queue[q]);
+                sg[j].offset = __ldcg(e);
+                sg[j].len_a = __ldcg(e + 1);
+                sg[j].len_b = __ldcg(e + 2);
+            }
+        }
+        uint32_t below = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < kPrepBatch; ++j) {
+            const uint32_t q = t0 + j * kPrepThreads + tid;
+            uint32_t cls = kSegTrivial;
+            if (q < nseg) {
+                cls = seg_class(sg[j], buf_len, tile, max_seg);
+                const uint64_t n = sg[j].len_a + sg[j].len_b;
+                below |= (n == 0 || size_bucket(n) < first_multi_bucket) ? 1u : 0u;
+            }
+            warp_append(&nmulti, qa.multi, q, cls == kSegMulti);
+        }
+        if (__syncthreads_or(below) && tid == 0) done = 1;
+        __syncthreads();
+    }
+    __syncthreads();
+    if (tid == 0) sb->counters[kMultiCount] = nmulti;
+}
+
 }  // namespace
 
 uint64_t batched_tile(ipm_dtype key, bool with_values, uint32_t variant) {
@@ -233,6 +368,15 @@ ipm_status launch_batched(void *buf, uint32_t *vals, uint64_t buf_len, ipm_dtype
         // the status block, its counters and the bucket counts start at zero; every other
         // area is written before it is read
         IPM_CUDA_TRY(cudaMemsetAsync(w, 0, L.queue_off, stream));
+    } else if (by_size && nseg > 0) {
+        // the size order prepared by up to one CTA per SM (the same zeroed start)
+        IPM_CUDA_TRY(cudaMemsetAsync(w, 0, L.queue_off, stream));
+        const uint32_t chunks = (nseg + kPrepChunk - 1) / kPrepChunk;
+        const uint32_t sms = uint32_t(num_sms());
+        batched_prep_multi_kernel<<<chunks < sms ? chunks : sms, kPrepThreads, 0, stream>>>(
+            segs, nseg, buf_len, tile, batched_max_segment(key, vals != nullptr, variant), qa,
+            sb);
+        IPM_TRY(last_launch_status());
     } else {
         batched_prep_kernel<<<1, kPrepThreads, 0, stream>>>(
             segs, nseg, by_size, buf_len, tile,
