@@ -1032,10 +1032,11 @@ def run_e2e(torch, pristines, steps, merge, slots=3):
     device buffers rotate between them (a buffer's next copy in waits for its last copy
     back), so one step's copy in, another's merge and a third's copy back run at once
     and the link carries both directions together.  The merges run one after another on
-    their stream, so one workspace serves them (merge(device buffers, slot, stream)).
+    their stream, so one workspace serves them (merge(device buffers, slot, stream)); the
+    copies back run in order on theirs, so one set of pinned output buffers serves them.
     Timed from before the first copy in to after the last copy back."""
     host_in = [p.cpu().pin_memory() for p in pristines]
-    host_out = [[torch.empty_like(h).pin_memory() for h in host_in] for _ in range(slots)]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
     dbuf = [[torch.empty_like(p) for p in pristines] for _ in range(slots)]
     s_in, s_merge, s_out = (torch.cuda.Stream() for _ in range(3))
     ev_in = [torch.cuda.Event() for _ in range(slots)]
@@ -1056,7 +1057,7 @@ def run_e2e(torch, pristines, steps, merge, slots=3):
         ev_merged[q].record(s_merge)
         s_out.wait_event(ev_merged[q])
         with torch.cuda.stream(s_out):
-            for h, d in zip(host_out[q], dbuf[q]):
+            for h, d in zip(host_out, dbuf[q]):
                 h.copy_(d, non_blocking=True)
             ev_out[q].record(s_out)
         used[q] = True
