@@ -257,3 +257,41 @@ def test_autotuned_options_match_oracle(ipm, dev, orc, kv, tmp_path):
                                        scratch_vals=svals, reps=3, cache_path=cache)
     assert again["from_cache"] and again["best"] == res["best"]
     assert again["signature"] == res["signature"]
+
+
+@pytest.mark.parametrize("form", [0, 2])
+def test_batched_many_segments_prepare_in_many_chunks(ipm, dev, orc, form):
+    """400,040 segments: the size-ordered queue is prepared in more chunks (of 2,048
+    descriptors) than there are SMs, so every preparation CTA takes several chunks
+    (bucket counts, then scatter), and the multi-tile segments scattered among them
+    must still lead the queue.  Small segments with many equal keys, 40 segments of
+    two to four tiles at random places in the table; every segment against the
+    oracle."""
+    import torch
+
+    rng = np.random.default_rng(11)
+    nsmall, nbig = 400_000, 40
+    _, tile = ipm.ipm_merge_plan(1, 1, "int32")
+    la = rng.integers(0, 49, nsmall + nbig)
+    lb = rng.integers(0, 49, nsmall + nbig)
+    big = rng.choice(nsmall + nbig, nbig, replace=False)
+    la[big] = rng.integers(tile // 2, 2 * tile, nbig)
+    lb[big] = rng.integers(tile // 2, 2 * tile, nbig)
+    runs = np.stack([la, lb], 1).ravel()
+    run_id = np.repeat(np.arange(runs.size), runs)
+    keys = rng.integers(-1000, 1000, run_id.size).astype(np.int32)
+    host = keys[np.lexsort((keys, run_id))]  # every run sorted, runs in table order
+    offs = np.concatenate([[0], np.cumsum(la + lb)[:-1]]).astype(np.int64)
+    d = to_dev(host, dev)
+    opts = OPTIONS[5] if form == 2 else None
+    st = ipm.segment_table(offs, la, lb, dev)
+    ws = ipm.workspace(ipm.ipm_merge_batched_workspace_bytes(host.size, la.size, "int32",
+                                                             False, opts), dev)
+    ipm.ipm_merge_batched(d, None, host.size, st, la.size, "int32", ws, options=opts)
+    torch.cuda.synchronize()
+    assert ipm.ipm_read_device_status(ws) == 0
+    got = from_dev(d, np.int32)
+    for s in range(la.size):
+        o, x, y = int(offs[s]), int(la[s]), int(lb[s])
+        want = orc.merge(host[o:o + x], host[o + x:o + x + y])
+        assert first_diff(got[o:o + x + y], want) is None, s
