@@ -273,9 +273,11 @@ ipm_status ipm_read_exchange_bytes(const void *d_ws, ipm_stream_t stream, uint64
  *
  * ipm_set_fused_engine selects how a group synchronises: 0 = one thread-block cluster
  * per group (cluster barrier; F <= 4), 1 = CTAs taken from a ticket in order and a
- * group barrier in global memory, 2 = the same with two pairs per CTA, the first
- * merged pair parked in tensor memory (TMEM) until the group barrier, which fuses one
- * level more (the default, for every key type with or without payload).
+ * group barrier in global memory, 2 = two pairs per CTA, the first merged pair parked
+ * in tensor memory (TMEM), each pair written once the pairs that read its destination
+ * have their slices on chip (a per-pair count in global memory instead of the whole
+ * group), which fuses one level more (the default, for every key type with or without
+ * payload).
  * ipm_merge_fused_plan reports what a merge will use.
  */
 /*

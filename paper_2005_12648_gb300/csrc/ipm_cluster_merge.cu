@@ -284,21 +284,19 @@ __global__ void __launch_bounds__(THREADS, 2)
 }
 
 // ---------------------------------------------------------------------------------
-// The group barrier with two pairs per CTA (keys, with or without payload): the first
-// pair is merged on chip and its output parked in tensor memory (TMEM, 256 columns of the
-// SM's 512 per CTA), then the second is staged and merged in shared memory, so a CTA
-// holds two merged pairs and a group of 2^F pairs needs 2^(F-1) resident CTAs: one
-// more level is fused than with one pair per CTA.  After the group barrier the second
-// pair is stored from shared memory and the first brought back from TMEM (each thread
+// Two pairs per CTA (keys, with or without payload): the first pair is merged on chip
+// and its output parked in tensor memory (TMEM, 256 columns of the SM's 512 per CTA),
+// then the second is staged and merged in shared memory, so a CTA holds two merged
+// pairs and a group of 2^F pairs needs 2^(F-1) resident CTAs: one more level is fused
+// than with one pair per CTA.  After the barrier below the second pair is stored from shared memory and the first brought back from TMEM (each thread
 // its own lane and columns) and stored the same way.  Tickets cover pairs 2t and 2t+1
 // (one group: groups are aligned to 2^F >= 2 pairs); the ticket-order argument of the
 // one-pair kernel holds with 2^(F-1) claims per group.  The barrier is per pair: a pair,
 // once staged, counts its slices in at the pairs whose outputs overwrite them
 // (count_in_slice), and a pair stores once its own count covers its output, that is
 // once the few members that read its destination have their data on chip, not the
-// whole group.  Exactly two CTAs fit an SM
-// (each CTA takes at least kGroup2Smem of shared memory), so the two allocations never
-// wait.
+// whole group.  Exactly two CTAs fit an SM (each CTA takes at least kGroup2Smem of
+// shared memory), so the two allocations never wait.
 // ---------------------------------------------------------------------------------
 constexpr uint32_t kGroup2Cols = 256;
 // more than a third of the SM's 228 KB (no third CTA fits), less than half with each

@@ -95,9 +95,10 @@ ipm_status launch_group_merge(void *buf, void *vals, uint32_t vb, uint64_t la, u
 // The largest F <= wanted with at least 2^F resident CTAs of the group kernel.
 uint32_t usable_group_levels(ipm_dtype key, uint32_t vb, uint32_t wanted);
 
-// The group barrier with two pairs per CTA, the first merged pair parked in TMEM
-// (every key type, with or without payload): groups of 2^F pairs need 2^(F-1) resident
-// CTAs.
+// Two pairs per CTA, the first merged pair parked in TMEM (every key type, with or
+// without payload), each pair written once the pairs reading its destination have
+// counted their slices in (gctr: one count per pair, zeroed here): groups of 2^F pairs
+// need 2^(F-1) resident CTAs.
 ipm_status launch_group2_merge(void *buf, void *vals, uint32_t vb, uint64_t la, uint64_t lb,
                                ipm_dtype key, const uint64_t *split, uint32_t G, uint32_t F,
                                uint32_t *gctr, StatusBlock *sb, cudaStream_t stream);
