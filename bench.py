@@ -84,8 +84,9 @@ FORM = {"c4-int32-batched": "batched", "c5-float32-learned": "learned"}
 # DRAM bytes (read + write) per launch of exchange_level_ws_kernel on a workload, from
 # one single-pass ncu capture of that workload (dram__bytes_read.sum +
 # dram__bytes_write.sum, mean of 6 launches).  Valid for the kernel as captured; any
-# change to it voids the figure.
-EXCHANGE_TRAFFIC = {"c2-int32-uniform": 2104150869}
+# change to it voids the figure (the last capture, 2,104,150,869 B on c2-int32-uniform,
+# was of the kernel with 104 KB stages; the stages are 112 KB now, so none is stored).
+EXCHANGE_TRAFFIC = {}
 # key-value workloads: the payload type per workload (payload = original buffer index)
 KV_WORKLOADS = {"c3-uint32-kv-zipf": "uint32", "f1-uint64-kv64-uniform": "uint64"}
 NP_DT = {"int32": np.int32, "uint32": np.uint32, "uint64": np.uint64, "float32": np.float32,

@@ -237,7 +237,7 @@ __device__ bool wait_count(const uint32_t *ctr, uint32_t target, unsigned long l
 template <typename K, bool KV, typename V = uint32_t>
 struct XCfg {
     static constexpr int kThreads = 512;
-    static constexpr uint32_t kStageBytes = 104u * 1024u;
+    static constexpr uint32_t kStageBytes = 112u * 1024u;
     static constexpr uint32_t kElemBytes = uint32_t(sizeof(K)) + (KV ? uint32_t(sizeof(V)) : 0u);
     static constexpr uint32_t kKPad = 16u / uint32_t(sizeof(K));  // phase slack, keys
     static constexpr uint32_t kVPad = 16u / uint32_t(sizeof(V));  // phase slack, values
